@@ -1,0 +1,250 @@
+/*
+ * inim.h -- C ABI of the GB300 integral-image (InIm) cartogram library.
+ *
+ * The library computes contiguous cartograms by the iterative
+ * density-equalising transformation of "Fast Time-Varying Contiguous
+ * Cartograms Using Integral Images" (Molchanov, Rave, Linsen):
+ *   per iteration (Sec. 4.1, steps 2-7)
+ *     rasterise the region polygons into a label texture and count o(v)
+ *     build the density texture d = s(v)/o(v), background = bdv_scale * d0
+ *     build the integral images (Sec. 3.1)
+ *     evaluate t(x,y;d) - t(x,y;d0) (Eq. 2, Eq. 3) at the pixels around each
+ *     vertex, interpolate bilinearly, blend with the shape parameter, move
+ *     compute shoelace areas, cartographic errors (Sec. 3.3), stop rule
+ *   per time step, in direct or cumulative mode (Sec. 4.2).
+ *
+ * Conventions shared by every entry point
+ *   - Coordinates are in the unit square, x to the right, y downward
+ *     (Sec. 3.2).  Vertex arrays are interleaved float pairs (x, y).
+ *   - The texture is N x N with N = 2^log2_res, 8 <= log2_res <= 12
+ *     (Sec. 3.1: textures of size 2^k x 2^k).  Textures are row-major:
+ *     element (i, j) (column i = x, row j = y) is at offset j*N + i.
+ *   - Pointers: the caller owns every pointer it passes.  Entry points whose
+ *     comment says "host or device" accept either kind of memory (the kind
+ *     is queried with cudaPointerGetAttributes); "device" means device memory
+ *     of the current CUDA device.  The library copies what it keeps.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Work is enqueued on it; entry points that return
+ *     results through host memory synchronise that stream before returning.
+ *   - Return value: INIM_OK (0) on success, a negative INIM_E_* error code,
+ *     or a positive INIM_W_* soft status (results are still written).
+ *     Errors leave outputs unspecified; the message of the last error on the
+ *     calling thread is available from inim_last_error().
+ */
+#ifndef INIM_H
+#define INIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define INIM_OK                0
+#define INIM_E_ARG            -1   /* bad size, index, resolution or pointer */
+#define INIM_E_VALUE          -2   /* non-finite or negative region value */
+#define INIM_E_CUDA           -3   /* a CUDA runtime call failed */
+#define INIM_E_TIMEOUT        -4   /* a device-side wait hit its iteration cap */
+#define INIM_E_CAPACITY       -5   /* an internal or caller buffer is too small */
+#define INIM_E_STATE          -6   /* call not valid in the current state */
+#define INIM_W_NOT_CONVERGED   1   /* stopped by max_iters before xi_stop */
+#define INIM_W_FOLDOVER        2   /* a region changed orientation or overlapped */
+
+/* inim_params.mode (Sec. 4.2) */
+#define INIM_DIRECT            0   /* every time step starts from the original map */
+#define INIM_CUMULATIVE        1   /* every time step starts from the previous result */
+
+/* inim_params.precision of the integral images */
+#define INIM_FP32              0   /* float prefix sums */
+#define INIM_FIX64             1   /* 64-bit fixed-point prefix sums (exact) */
+#define INIM_KAHAN             2   /* compensated (double-float) prefix sums */
+
+/* inim_params.form */
+#define INIM_FORM_FUSED        0   /* fused kernels, batched, CUDA graph, device stop */
+#define INIM_FORM_PLAIN        1   /* one unfused kernel per step, host stop test */
+
+/* inim_map_create flags */
+#define INIM_MAP_DEVICE_PTRS   1   /* all input arrays are device pointers */
+
+typedef struct inim_map inim_map;   /* opaque: device copy of a region map */
+
+/* Parameters of one solve.  Fill with inim_params_default() first. */
+typedef struct {
+    int32_t log2_res;     /* k, N = 2^k (Sec. 3.1); 8..12; default 10 (Sec. 4.1) */
+    float   shape;        /* shape parameter in [0, 1): vertices move by
+                             (1 - shape) * displacement per iteration */
+    float   bdv_scale;    /* background density = bdv_scale * d0 (Sec. 4.1); default 1 */
+    int32_t max_iters;    /* iteration cap per time step; default 512 (Sec. 4.1) */
+    float   xi_stop;      /* stop when max error xi < xi_stop; default 0.01; <= 0 off */
+    int32_t stall_window; /* stop when xi has not improved for this many
+                             iterations; default 32; 0 off */
+    float   eps_stop;     /* stop when average error eps < eps_stop; default 0 (off) */
+    int32_t mode;         /* INIM_DIRECT or INIM_CUMULATIVE */
+    int32_t precision;    /* INIM_FP32, INIM_FIX64 or INIM_KAHAN */
+    int32_t form;         /* INIM_FORM_FUSED or INIM_FORM_PLAIN */
+    int32_t warm_start;   /* 1: move vertices by the learned field first (needs
+                             inim_warmstart_load); default 0 */
+    int32_t reserved;
+} inim_params;
+
+/* Per time-step statistics. */
+typedef struct {
+    int32_t iters;        /* iterations performed */
+    float   eps;          /* average cartographic error after the last iteration */
+    float   xi;           /* maximum cartographic error after the last iteration */
+    int32_t foldover;     /* 1 if a region changed the sign of its area */
+    int32_t overlap;      /* 1 if some pixel was inside two regions */
+    int32_t status;       /* INIM_OK / INIM_W_* of this step */
+} inim_step_stats;
+
+/* One independent solve for inim_run_batch. */
+typedef struct {
+    const inim_map* map;
+    const float*    values;    /* [n_regions] s(v) >= 0; host or device */
+    const float*    init_xy;   /* [n_verts*2] start vertices, NULL = the map's own; host or device */
+    float*          out_xy;    /* [n_verts*2] result; host or device */
+    inim_params     params;    /* mode is ignored: every job is one time step */
+    inim_step_stats* stats;    /* NULL or one host struct */
+} inim_job;
+
+/* Defaults of Sec. 4.1: 1024^2, stop at xi < 0.01 / 32-iteration stall / 512 iterations. */
+void inim_params_default(inim_params* p);
+
+/* Text of a status code; static storage. */
+const char* inim_status_string(int status);
+
+/* Message of the last error reported on the calling thread ("" if none). */
+const char* inim_last_error(void);
+
+/*
+ * Create a map (Sec. 4.1 step 0: regions described by polygons; the
+ * background is the complement of the regions in the unit square).
+ *   xy          [n_verts*2] unique vertex positions.
+ *   ring_off    [n_rings+1] CSR offsets into ring_idx (ring_off[0] = 0).
+ *   ring_idx    [ring_off[n_rings]] vertex ids; each ring closes implicitly.
+ *   ring_region [n_rings] region id of each ring, 0 <= id < n_regions.
+ *   n_regions   1 .. 65534.
+ * Membership is even-odd over all rings of a region, so holes are rings of
+ * the same region.  Shared boundaries must use the same vertex ids in both
+ * regions so that they move together.  Arrays are host memory unless
+ * flags has INIM_MAP_DEVICE_PTRS.  Errors: INIM_E_ARG for sizes out of
+ * range or a vertex id outside [0, n_verts).
+ */
+int inim_map_create(const float* xy, int32_t n_verts,
+                    const int32_t* ring_off, int32_t n_rings,
+                    const int32_t* ring_idx, const int32_t* ring_region,
+                    int32_t n_regions, int32_t flags, inim_map** out);
+
+int inim_map_destroy(inim_map* map);
+
+/* Sizes of a map (any pointer may be NULL). */
+int inim_map_info(const inim_map* map, int32_t* n_verts, int32_t* n_regions,
+                  int32_t* n_rings, int32_t* n_edges);
+
+/*
+ * Time-varying cartogram (Sec. 4.1 algorithm per step; Sec. 4.2 modes).
+ *   values  [T*n_regions] s_t(v) for t = 0..T-1; host or device.
+ *   init_xy [n_verts*2] start vertices or NULL (the map's own); host or device.
+ *   out_xy  [T*n_verts*2] vertices after each step; host or device.
+ *   stats   [T] host array or NULL.
+ * Direct mode runs all T steps as one batch; cumulative mode runs them in
+ * order.  Returns the worst per-step status.
+ */
+int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* params,
+             const float* init_xy, float* out_xy, inim_step_stats* stats, void* stream);
+
+/*
+ * Many independent single-step solves of possibly different maps and
+ * resolutions in one batched launch sequence captured in a CUDA graph
+ * (params.form must be INIM_FORM_FUSED).  Jobs run together until each one's
+ * stop rule fires.
+ */
+int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream);
+
+/* ---------------- single steps of the iteration (device memory) -------- */
+
+/*
+ * Step 2 of Sec. 4.1: rasterise the map at vertex positions xy.
+ *   xy      [n_verts*2] device.
+ *   labels  [N*N] device uint16: region id, or n_regions for background.
+ *   counts  [n_regions+1] device int32: o(v) in pixels; counts[n_regions]
+ *           is the background pixel count.
+ *   overlap NULL or host int32: 1 if some pixel lay inside two regions.
+ * Rule: vertices snap to X = rint(x*2^(k+8)); pixel (i,j) has centre
+ * (256i+128, 256j+128); an edge with Y0 < Y1 counts for the centre iff
+ * Y0 <= Yc < Y1 and the centre is on or right of the edge (exact integer
+ * test); a pixel is inside a region iff its count over the region's rings is
+ * odd; inside several regions -> the smallest id.
+ */
+int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t* labels,
+                int32_t* counts, int32_t* overlap, void* stream);
+
+/*
+ * Step 4 of Sec. 4.1 on a given texture: the integral images of Sec. 3.1.
+ *   density [N*N] device float, d >= 0.
+ *   S       [N*N] device: alpha(i,j) = sum_{i'<=i, j'<=j} d   (2-D prefix)
+ *   T       [N*N] device: alpha_t(i,j) = top-wedge sum, the pixels
+ *           (i',j') with j'<j and i-(j-j') < i' <= i+(j-j')
+ *   A       [2N-1] device: A(s) = sum_{i'+j'<=s} d
+ *   B       [2N-1] device: B(w+N-1) = sum_{i'-j'<=w} d
+ * Element type of S and T: float for INIM_FP32; int64 fixed point with
+ * 2^frac_bits units for INIM_FIX64 (d is quantised to llrint(d*2^frac_bits);
+ * A, B are then int64 as well); float pairs (hi, lo) for INIM_KAHAN (A, B
+ * float pairs).  frac_bits is ignored unless precision is INIM_FIX64 and
+ * must keep every sum below 2^62.  The other six InIms follow from these by
+ * Eq. (1) (see inim_displacement).
+ */
+int inim_inims(const float* density, int32_t log2_res, int32_t precision, int32_t frac_bits,
+               void* S, void* T, void* A, void* B, void* stream);
+
+/*
+ * Steps 5-6 of Sec. 4.1 on a given texture: Eq. (3) displacement
+ * t(p;d) - t(p;d0) interpolated bilinearly at n points.
+ *   density [N*N] device float; xy [n*2] device; delta [n*2] device out.
+ * Samples are pixel centres; bilinear weights use f = x*N - 1/2,
+ * i0 = clamp(floor f, 0, N-2), a = clamp(f - i0, 0, 1).
+ */
+int inim_displacement(const float* density, int32_t log2_res, int32_t precision,
+                      const float* xy, int32_t n, float* delta, void* stream);
+
+/*
+ * Run n_iters full iterations in place on device vertices (Sec. 4.1 steps
+ * 2-6 plus the areas and errors of Sec. 3.3).  values [n_regions] device.
+ * stats: NULL or host struct, filled after the last iteration.  The stop
+ * rule is NOT applied (exactly n_iters iterations).
+ */
+int inim_iterate(const inim_map* map, float* xy, const float* values,
+                 const inim_params* params, int32_t n_iters, inim_step_stats* stats,
+                 void* stream);
+
+/*
+ * Signed shoelace area per region (sum over its rings), accumulated in
+ * double (Sec. 3.3).  xy [n_verts*2] device; areas [n_regions] device double.
+ */
+int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream);
+
+/* ---------------- profiling ------------------------------------------- */
+
+/*
+ * Average device time of every kernel stage of one fused iteration of the
+ * batch used most recently by inim_run / inim_run_batch / inim_iterate: each
+ * stage is launched `reps` times back to back between two CUDA events on the
+ * library's stream (ms[i] = elapsed / reps).  Stages, in iteration order:
+ * raster, density_table, scan_phase1, scan_carry, scan_phase3, gather_move,
+ * areas_errors (names from inim_stage_name).  The batch's vertices move while
+ * it runs; the next run resets them.  ms must hold >= 7 floats; *n_stages
+ * receives 7.  INIM_E_STATE if no map batch ran yet.
+ */
+int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_stages);
+const char* inim_stage_name(int32_t i);
+
+/* Number of kernel launches issued by this library so far (graph replays count
+ * every kernel node they run). */
+long long inim_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INIM_H */

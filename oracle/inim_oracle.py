@@ -223,9 +223,9 @@ def left_wedge_sweep(d):
     wedge grows by exactly those rays from column i-1 to column i.
     """
     N = d.shape[0]
-    L = np.zeros((N, N))
-    D1 = np.zeros((N, N))
-    D2 = np.zeros((N, N))
+    L = np.zeros_like(d)
+    D1 = np.zeros_like(d)
+    D2 = np.zeros_like(d)
     for i in range(N):
         if i == 0:
             D1[:, 0] = d[:, 0]
@@ -247,7 +247,8 @@ def inims(d):
     gamma from Eq. (1).  beta_t = left wedge L (column sweep); with
     A(s) = sum_{i'+j'<=s} d and B(w) = sum_{i'-j'<=w} d:
     alpha_t = A(i+j) - L, gamma_t = B(i-j) - L, delta_t from Eq. (1).
-    Returns a dict with the eight [N, N] tables and the total C.
+    Returns a dict with the eight [N, N] tables and the total C.  Sums are
+    accumulated in d's dtype, so an integer texture gives exact sums.
     """
     N = d.shape[0]
     S = np.cumsum(np.cumsum(d, axis=1), axis=0)
@@ -258,14 +259,16 @@ def inims(d):
     gamma = C - alpha - beta - delta
     L = left_wedge_sweep(d)
     jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
-    anti = np.bincount((ii + jj).ravel(), weights=d.ravel(), minlength=2 * N - 1)
-    diag = np.bincount((ii - jj + N - 1).ravel(), weights=d.ravel(), minlength=2 * N - 1)
+    anti = np.zeros(2 * N - 1, dtype=d.dtype)
+    diag = np.zeros(2 * N - 1, dtype=d.dtype)
+    np.add.at(anti, (ii + jj).ravel(), d.ravel())
+    np.add.at(diag, (ii - jj + N - 1).ravel(), d.ravel())
     A = np.cumsum(anti)
     B = np.cumsum(diag)
     at = A[ii + jj] - L
     gt = B[ii - jj + N - 1] - L
     dt = C - L - at - gt
-    return dict(a=alpha, b=beta, g=gamma, d=delta, at=at, bt=L, gt=gt, dt=dt, C=C)
+    return dict(a=alpha, b=beta, g=gamma, d=delta, at=at, bt=L, gt=gt, dt=dt, C=C, A=A, B=B)
 
 
 # ----------------------------------------------------------------------------

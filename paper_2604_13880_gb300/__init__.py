@@ -1,0 +1,197 @@
+"""GB300 integral-image (InIm) contiguous cartograms.
+
+Python binding of the C ABI in ``include/inim.h`` (same function names).  The
+functions take numpy arrays (host memory) or torch tensors (host or CUDA) and
+only marshal arguments; the cartogram iteration itself (rasterisation,
+density, integral images, Eq. (2)-(3) displacement, blend, move, areas and
+errors) runs in the CUDA kernels of ``libinim.so``.  Nothing here falls back
+to a CPU implementation: a missing library raises.
+
+Typical use::
+
+    from paper_2604_13880_gb300 import synth, inim_map_create, inim_run, params
+    mesh = synth.voronoi_map(200, 50_000, seed=2, jitter=0.3)
+    m = inim_map_create(mesh)
+    out, stats = inim_run(m, values_T_by_R, params(log2_res=10, shape=0.5))
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_FIX64, INIM_FORM_FUSED, INIM_FORM_PLAIN,  # noqa: F401
+                   INIM_FP32, INIM_KAHAN, InimError, inim_job, inim_params, inim_step_stats)
+
+__all__ = [
+    "params", "inim_params_default", "inim_status_string", "inim_map_create", "inim_map_destroy",
+    "inim_map_info", "inim_run", "inim_run_batch", "inim_raster", "inim_inims", "inim_displacement",
+    "inim_iterate", "inim_areas", "Map",
+]
+
+
+def inim_params_default() -> inim_params:
+    p = inim_params()
+    _lib.load().inim_params_default(ctypes.byref(p))
+    return p
+
+
+def params(**kw) -> inim_params:
+    """Defaults of Sec. 4.1 with keyword overrides (log2_res, shape, ...)."""
+    p = inim_params_default()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def inim_status_string(status: int) -> str:
+    return _lib.load().inim_status_string(status).decode()
+
+
+class Map:
+    """Owner of an ``inim_map*`` handle."""
+
+    def __init__(self, handle, n_verts, n_regions):
+        self.handle = handle
+        self.n_verts = n_verts
+        self.n_regions = n_regions
+
+    def close(self):
+        if self.handle:
+            _lib.load().inim_map_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def inim_map_create(mesh=None, *, xy=None, ring_off=None, ring_idx=None, ring_region=None,
+                    n_regions=None) -> Map:
+    """Create a map from a ``synth.Mesh`` or from the raw arrays."""
+    if mesh is not None:
+        xy, ring_off, ring_idx, ring_region, n_regions = (
+            mesh.verts, mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
+    xy = np.ascontiguousarray(xy, dtype=np.float32)
+    ring_off = np.ascontiguousarray(ring_off, dtype=np.int32)
+    ring_idx = np.ascontiguousarray(ring_idx, dtype=np.int32)
+    ring_region = np.ascontiguousarray(ring_region, dtype=np.int32)
+    h = ctypes.c_void_p()
+    lib = _lib.load()
+    _lib.check(lib.inim_map_create(xy.ctypes.data, xy.shape[0], ring_off.ctypes.data, ring_region.shape[0],
+                                   ring_idx.ctypes.data, ring_region.ctypes.data, int(n_regions), 0,
+                                   ctypes.byref(h)), "inim_map_create")
+    return Map(h.value, xy.shape[0], int(n_regions))
+
+
+def inim_map_destroy(m: Map) -> None:
+    m.close()
+
+
+def inim_map_info(m: Map):
+    a = [ctypes.c_int32() for _ in range(4)]
+    _lib.check(_lib.load().inim_map_info(m.handle, *[ctypes.byref(x) for x in a]), "inim_map_info")
+    return dict(n_verts=a[0].value, n_regions=a[1].value, n_rings=a[2].value, n_edges=a[3].value)
+
+
+def _stats_array(T):
+    return (inim_step_stats * T)()
+
+
+def inim_run(m: Map, values, p: inim_params, init_xy=None, out_xy=None, stream=None):
+    """Time-varying run (values [T, R]); returns (out_xy [T, V, 2], stats list)."""
+    lib = _lib.load()
+    if isinstance(values, np.ndarray) or not hasattr(values, "data_ptr"):
+        values = np.ascontiguousarray(np.atleast_2d(values), dtype=np.float32)
+    T = int(values.shape[0]) if values.ndim == 2 else 1
+    if init_xy is not None and isinstance(init_xy, np.ndarray):
+        init_xy = np.ascontiguousarray(init_xy, dtype=np.float32)
+    if out_xy is None:
+        out_xy = np.empty((T, m.n_verts, 2), np.float32)
+    st = _stats_array(T)
+    s = stream if stream is not None else _lib.stream_of(values, init_xy, out_xy)
+    status = _lib.check(lib.inim_run(m.handle, _lib.ptr(values), T, ctypes.byref(p), _lib.ptr(init_xy),
+                                     _lib.ptr(out_xy), st, s), "inim_run")
+    return out_xy, [x.as_dict() for x in st], status
+
+
+def inim_run_batch(jobs, stream=None):
+    """jobs: list of dicts(map=Map, values, params, init_xy=None, out_xy=None)."""
+    lib = _lib.load()
+    n = len(jobs)
+    arr = (inim_job * n)()
+    stats = _stats_array(n)
+    keep = []
+    outs = []
+    for k, j in enumerate(jobs):
+        vals = j["values"]
+        if isinstance(vals, np.ndarray) or not hasattr(vals, "data_ptr"):
+            vals = np.ascontiguousarray(vals, dtype=np.float32).ravel()
+        init = j.get("init_xy")
+        if init is not None and isinstance(init, np.ndarray):
+            init = np.ascontiguousarray(init, dtype=np.float32)
+        out = j.get("out_xy")
+        if out is None:
+            out = np.empty((j["map"].n_verts, 2), np.float32)
+        keep += [vals, init]
+        outs.append(out)
+        arr[k].map = j["map"].handle
+        arr[k].values = _lib.ptr(vals)
+        arr[k].init_xy = _lib.ptr(init)
+        arr[k].out_xy = _lib.ptr(out)
+        arr[k].params = j["params"]
+        arr[k].stats = ctypes.pointer(stats[k])
+    status = _lib.check(lib.inim_run_batch(arr, n, stream), "inim_run_batch")
+    return outs, [s.as_dict() for s in stats], status
+
+
+def inim_raster(m: Map, xy, log2_res: int, labels, counts, stream=None) -> int:
+    """Device buffers: xy [V,2] f32, labels [N,N] u16 (int16 tensor), counts [R+1] i32."""
+    ov = ctypes.c_int32(0)
+    _lib.check(_lib.load().inim_raster(m.handle, _lib.ptr(xy), log2_res, _lib.ptr(labels), _lib.ptr(counts),
+                                       ctypes.byref(ov), stream or _lib.stream_of(xy)), "inim_raster")
+    return ov.value
+
+
+def inim_inims(density, log2_res: int, precision: int, frac_bits: int, S, T, A, B, stream=None) -> None:
+    _lib.check(_lib.load().inim_inims(_lib.ptr(density), log2_res, precision, frac_bits, _lib.ptr(S),
+                                      _lib.ptr(T), _lib.ptr(A), _lib.ptr(B), stream or _lib.stream_of(density)),
+               "inim_inims")
+
+
+def inim_displacement(density, log2_res: int, precision: int, xy, delta, stream=None) -> None:
+    n = int(xy.shape[0])
+    _lib.check(_lib.load().inim_displacement(_lib.ptr(density), log2_res, precision, _lib.ptr(xy), n,
+                                             _lib.ptr(delta), stream or _lib.stream_of(density)),
+               "inim_displacement")
+
+
+def inim_iterate(m: Map, xy, values, p: inim_params, n_iters: int, stream=None):
+    st = inim_step_stats()
+    status = _lib.check(_lib.load().inim_iterate(m.handle, _lib.ptr(xy), _lib.ptr(values), ctypes.byref(p),
+                                                 n_iters, ctypes.byref(st), stream or _lib.stream_of(xy)),
+                        "inim_iterate")
+    return st.as_dict(), status
+
+
+def inim_areas(m: Map, xy, areas, stream=None) -> None:
+    _lib.check(_lib.load().inim_areas(m.handle, _lib.ptr(xy), _lib.ptr(areas), stream or _lib.stream_of(xy)),
+               "inim_areas")
+
+
+def inim_profile_stages(reps: int = 20):
+    """{stage name: average ms per launch} for the most recent batch."""
+    lib = _lib.load()
+    ms = (ctypes.c_float * 16)()
+    n = ctypes.c_int32(0)
+    _lib.check(lib.inim_profile_stages(reps, ms, 16, ctypes.byref(n)), "inim_profile_stages")
+    return {lib.inim_stage_name(i).decode(): ms[i] for i in range(n.value)}
+
+
+def inim_launch_count() -> int:
+    return int(_lib.load().inim_launch_count())

@@ -1,0 +1,940 @@
+// C ABI of the InIm cartogram library: maps, batches of jobs, the fused and
+// the plain iteration drivers, the direct / cumulative time loop (Sec. 4.2),
+// and the single-step entry points.  See include/inim.h for the contract.
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <list>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "inim_internal.cuh"
+
+using namespace inim;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(INIM_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// map
+// ---------------------------------------------------------------------------
+struct inim_map {
+    int n_verts = 0, n_regions = 0, n_rings = 0, n_edges = 0;
+    int2* edges = nullptr;
+    int* edge_region = nullptr;
+    int* reg_ring_off = nullptr;
+    int* reg_rings = nullptr;
+    int* ring_off = nullptr;
+    int* ring_idx = nullptr;
+    float* sign0 = nullptr;
+    float2* xy0 = nullptr;
+    std::vector<float> h_xy0;
+    std::vector<int> h_edge_a, h_edge_b;   // for capacity estimates
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// per-job device buffers
+// ---------------------------------------------------------------------------
+size_t elem_size(int precision) { return precision == INIM_FP32 ? 4 : 8; }
+
+struct Buffers {
+    int n = 0, precision = 0, R = 0, key_cap = 0, nb = 0, V = 0;
+    uint16_t* labels = nullptr;
+    int* row_cnt = nullptr;
+    int* row_off = nullptr;
+    uint32_t* keys = nullptr;
+    int* counts = nullptr;
+    float* dens = nullptr;
+    float* values = nullptr;
+    void* S = nullptr;
+    void* T = nullptr;
+    void* A = nullptr;
+    void* B = nullptr;
+    void* rowcum = nullptr;
+    void* agg = nullptr;
+    void* carry = nullptr;
+    double* areas = nullptr;
+    float2* xy = nullptr;
+
+    cudaError_t alloc(int n_, int prec, int R_, int V_, int key_cap_, int nb_) {
+        n = n_; precision = prec; R = R_; V = V_; key_cap = key_cap_; nb = nb_;
+        const size_t np = (size_t)n * n, es = elem_size(prec);
+        cudaError_t e = cudaSuccess;
+        auto A_ = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes < 16 ? 16 : bytes); };
+        A_((void**)&labels, np * 2);
+        A_((void**)&row_cnt, (size_t)n * 4);
+        A_((void**)&row_off, (size_t)(n + 1) * 4);
+        A_((void**)&keys, (size_t)key_cap * 4);
+        A_((void**)&counts, (size_t)(R + 1) * 4);
+        A_((void**)&dens, (size_t)(R + 1) * 4);
+        A_((void**)&values, (size_t)R * 4);
+        A_(&S, np * es);
+        A_(&T, np * es);
+        A_(&A, (size_t)(2 * n) * es);
+        A_(&B, (size_t)(2 * n) * es);
+        A_(&rowcum, (size_t)n * es);
+        A_(&agg, (size_t)3 * nb * n * es);
+        A_(&carry, (size_t)3 * nb * n * es);
+        A_((void**)&areas, (size_t)R * 8);
+        A_((void**)&xy, (size_t)V * 8);
+        if (e == cudaSuccess) e = cudaMemset(row_cnt, 0, (size_t)n * 4);
+        return e;
+    }
+    void release() {
+        dfree(labels); dfree(row_cnt); dfree(row_off); dfree(keys); dfree(counts); dfree(dens);
+        dfree(values); dfree(S); dfree(T); dfree(A); dfree(B); dfree(rowcum); dfree(agg);
+        dfree(carry); dfree(areas); dfree(xy);
+    }
+};
+
+// default scan tiles per resolution (band height, columns per thread, threads)
+ScanTile g_tiles[kMaxLog2 + 1] = {};
+
+ScanTile default_tile(int log2n) {
+    switch (log2n) {
+        case 8: return {8, 2, 128};
+        case 9: return {8, 4, 128};
+        case 10: return {16, 8, 128};
+        case 11: return {16, 8, 256};
+        default: return {32, 8, 512};
+    }
+}
+
+ScanTile tile_for(int log2n) {
+    ScanTile t = g_tiles[log2n];
+    if (t.H <= 0) t = default_tile(log2n);
+    return t;
+}
+
+int estimate_key_cap(const inim_map* m, const float* xy_host, int n) {
+    // crossings of every edge with the rows, from the start positions, with
+    // a generous margin for stretching during the iteration
+    double rows = 0.0;
+    for (int e = 0; e < m->n_edges; ++e) {
+        const int a = m->h_edge_a[e], b = m->h_edge_b[e];
+        rows += std::fabs((double)xy_host[2 * a + 1] - (double)xy_host[2 * b + 1]) * n + 1.0;
+    }
+    double cap = 4.0 * rows + 4.0 * n + 1024.0;
+    if (cap > 2.0e9) cap = 2.0e9;
+    return (int)cap;
+}
+
+// ---------------------------------------------------------------------------
+// batch: jobs + buffers + block maps (+ a captured CUDA graph)
+// ---------------------------------------------------------------------------
+struct JobSpec {
+    const inim_map* map;
+    int log2n;
+    int precision;
+    bool operator==(const JobSpec& o) const {
+        return map == o.map && log2n == o.log2n && precision == o.precision;
+    }
+};
+
+struct Group {
+    int log2n;
+    ScanTile tile;
+    BlockMap band, carry;
+};
+
+struct Batch {
+    std::vector<JobSpec> spec;
+    std::vector<Job> h_jobs;
+    std::vector<JobState> h_states;
+    std::vector<Buffers> bufs;
+    Job* d_jobs = nullptr;
+    JobState* d_states = nullptr;
+    BlockMap edge_blocks, job_blocks, row_blocks, vert_blocks, region_blocks;
+    std::vector<Group> groups;
+    int precision = INIM_FP32;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    std::vector<PlainWork> plain;   // per job (plain form only)
+
+    ~Batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (auto& b : bufs) b.release();
+        for (auto& p : plain) plain_free(p);
+        dfree(d_jobs); dfree(d_states);
+        BlockMap* maps[] = {&edge_blocks, &job_blocks, &row_blocks, &vert_blocks, &region_blocks};
+        for (BlockMap* m : maps) dfree(m->d_map);
+        for (auto& g : groups) { dfree(g.band.d_map); dfree(g.carry.d_map); }
+        if (ev) cudaEventDestroy(ev);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+cudaError_t make_map(BlockMap& bm, const std::vector<int2>& entries) {
+    bm.n_blocks = (int)entries.size();
+    if (entries.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&bm.d_map, entries.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMemcpy(bm.d_map, entries.data(), entries.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    return e;
+}
+
+int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<const float*>& start_xy_host) {
+    B.spec = spec;
+    const int nj = (int)spec.size();
+    B.precision = spec[0].precision;
+    CUDA_TRY(cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaMalloc(&B.d_jobs, nj * sizeof(Job)));
+    CUDA_TRY(cudaMalloc(&B.d_states, nj * sizeof(JobState)));
+    B.h_jobs.resize(nj);
+    B.h_states.assign(nj, JobState{});
+    B.bufs.resize(nj);
+    std::vector<int2> eb, jb, rb, vb, gb;
+    for (int k = 0; k < nj; ++k) {
+        const JobSpec& s = spec[k];
+        const inim_map* m = s.map;
+        const int n = 1 << s.log2n;
+        const ScanTile tile = tile_for(s.log2n);
+        const int nb = (n + tile.H - 1) / tile.H;
+        const int cap = m ? estimate_key_cap(m, start_xy_host[k] ? start_xy_host[k] : m->h_xy0.data(), n) : 16;
+        Buffers& b = B.bufs[k];
+        CUDA_TRY(b.alloc(n, s.precision, m ? m->n_regions : 1, m ? m->n_verts : 1, cap, nb));
+        Job J{};
+        J.n = n; J.log2n = s.log2n;
+        if (m) {
+            J.n_verts = m->n_verts; J.n_regions = m->n_regions; J.n_edges = m->n_edges; J.n_rings = m->n_rings;
+            J.edges = m->edges; J.edge_region = m->edge_region; J.reg_ring_off = m->reg_ring_off;
+            J.reg_rings = m->reg_rings; J.ring_off = m->ring_off; J.ring_idx = m->ring_idx; J.sign0 = m->sign0;
+        }
+        J.xy = b.xy; J.values = b.values; J.lam = 1.0f; J.bdv_scale = 1.0f; J.precision = s.precision;
+        J.labels = b.labels; J.row_cnt = b.row_cnt; J.row_off = b.row_off; J.keys = b.keys; J.key_cap = cap;
+        J.counts = b.counts; J.dens = b.dens;
+        J.S = b.S; J.T = b.T; J.A = b.A; J.B = b.B; J.rowcum = b.rowcum;
+        J.H = tile.H; J.nb = nb; J.agg = b.agg; J.carry = b.carry;
+        J.areas = b.areas; J.st = B.d_states + k;
+        B.h_jobs[k] = J;
+        if (m) {
+            for (int q = 0; q < (m->n_edges + 255) / 256; ++q) eb.push_back(make_int2(k, q));
+            for (int q = 0; q < (m->n_verts + 255) / 256; ++q) vb.push_back(make_int2(k, q));
+            for (int q = 0; q < (m->n_regions + 7) / 8; ++q) gb.push_back(make_int2(k, q));
+        }
+        jb.push_back(make_int2(k, 0));
+        for (int j = 0; j < n; ++j) rb.push_back(make_int2(k, j));
+    }
+    CUDA_TRY(make_map(B.edge_blocks, eb));
+    CUDA_TRY(make_map(B.job_blocks, jb));
+    CUDA_TRY(make_map(B.row_blocks, rb));
+    CUDA_TRY(make_map(B.vert_blocks, vb));
+    CUDA_TRY(make_map(B.region_blocks, gb));
+    // scan groups by resolution
+    for (int l = kMinLog2; l <= kMaxLog2; ++l) {
+        std::vector<int2> band, carry;
+        for (int k = 0; k < nj; ++k) {
+            if (spec[k].log2n != l) continue;
+            const Job& J = B.h_jobs[k];
+            for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
+            const int span = J.n + (J.nb - 1) * J.H;
+            const int len = J.n + 2 * span;
+            for (int q = 0; q < (len + 255) / 256; ++q) carry.push_back(make_int2(k, q));
+        }
+        if (band.empty()) continue;
+        Group g;
+        g.log2n = l;
+        g.tile = tile_for(l);
+        CUDA_TRY(make_map(g.band, band));
+        CUDA_TRY(make_map(g.carry, carry));
+        B.groups.push_back(g);
+    }
+    CUDA_TRY(cudaMemcpy(B.d_jobs, B.h_jobs.data(), nj * sizeof(Job), cudaMemcpyHostToDevice));
+    return INIM_OK;
+}
+
+// batch cache (same job specs -> same buffers, block maps and graph)
+std::mutex g_cache_mu;
+std::list<std::unique_ptr<Batch>> g_cache;
+constexpr size_t kCacheMax = 6;
+
+Batch* get_batch(const std::vector<JobSpec>& spec, const std::vector<const float*>& start_xy_host, int* status) {
+    for (auto it = g_cache.begin(); it != g_cache.end(); ++it) {
+        if ((*it)->spec == spec) {
+            g_cache.splice(g_cache.begin(), g_cache, it);
+            *status = INIM_OK;
+            return g_cache.front().get();
+        }
+    }
+    auto b = std::make_unique<Batch>();
+    *status = build_batch(*b, spec, start_xy_host);
+    if (*status != INIM_OK) return nullptr;
+    g_cache.push_front(std::move(b));
+    while (g_cache.size() > kCacheMax) g_cache.pop_back();
+    return g_cache.front().get();
+}
+
+void purge_map(const inim_map* m) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto it = g_cache.begin(); it != g_cache.end();) {
+        bool uses = false;
+        for (auto& s : (*it)->spec) uses |= (s.map == m);
+        if (uses) it = g_cache.erase(it);
+        else ++it;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// iteration drivers
+// ---------------------------------------------------------------------------
+cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s) {
+    cudaError_t e = launch_raster(B.d_jobs, B.edge_blocks, B.job_blocks, B.row_blocks, s);
+    if (e == cudaSuccess) e = launch_density_table(B.d_jobs, (int)B.spec.size(), s);
+    for (auto& g : B.groups) {
+        if (e != cudaSuccess) break;
+        if (B.precision == INIM_FIX64) e = launch_scan_fix64(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
+        else if (B.precision == INIM_KAHAN) e = launch_scan_kahan(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
+        else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
+    }
+    if (e == cudaSuccess) e = launch_gather(B.d_jobs, B.vert_blocks, B.precision, s);
+    if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, (int)B.spec.size(), B.region_blocks, 1, s);
+    return e;
+}
+
+constexpr int kGraphIters = 8;
+
+std::atomic<long long> g_launches{0};
+
+int kernels_per_fused_iteration(const Batch& B) {
+    int k = 2 + (B.edge_blocks.n_blocks ? 2 : 0);          // raster
+    k += 1;                                                  // density table
+    k += 3 * (int)B.groups.size();                           // scan phases 1-3
+    k += B.vert_blocks.n_blocks ? 1 : 0;                     // gather / move
+    k += (B.region_blocks.n_blocks ? 1 : 0) + 1;             // areas, errors
+    return k;
+}
+constexpr int kKernelsPerPlainIteration = 17;
+
+int ensure_graph(Batch& B) {
+    if (B.graph) return INIM_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = enqueue_fused_iteration(B, B.stream);
+    cudaError_t e2 = cudaStreamEndCapture(B.stream, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail(INIM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e)); }
+    if (e2 != cudaSuccess) return fail(INIM_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+    e = cudaGraphInstantiate(&B.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { B.graph = nullptr; return fail(INIM_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+    B.graph_iters = kGraphIters;
+    return INIM_OK;
+}
+
+JobState initial_state(const inim_params& p, int stop_on_rule, int max_iters) {
+    JobState st{};
+    st.active = 1;
+    st.iters = 0;
+    st.max_iters = max_iters;
+    st.stall_window = p.stall_window;
+    st.xi_stop = p.xi_stop;
+    st.eps_stop = p.eps_stop;
+    st.best_xi = 1e300;
+    st.since = 0;
+    st.stop_on_rule = stop_on_rule;
+    return st;
+}
+
+bool needs_poll(const inim_params& p) {
+    return p.xi_stop > 0.0f || p.eps_stop > 0.0f || p.stall_window > 0;
+}
+
+// run the fused form until every job stopped; states must be uploaded
+int run_fused(Batch& B, int max_iters, bool poll) {
+    const int nj = (int)B.spec.size();
+    int st = ensure_graph(B);
+    if (st != INIM_OK) return st;
+    int done = 0;
+    while (done < max_iters) {
+        CUDA_TRY(cudaGraphLaunch(B.graph, B.stream));
+        g_launches += (long long)B.graph_iters * kernels_per_fused_iteration(B);
+        done += B.graph_iters;
+        if (poll && done < max_iters) {
+            CUDA_TRY(cudaMemcpyAsync(B.h_states.data(), B.d_states, nj * sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
+            CUDA_TRY(cudaStreamSynchronize(B.stream));
+            bool any = false;
+            for (auto& s : B.h_states) any |= (s.active != 0);
+            if (!any) break;
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(B.h_states.data(), B.d_states, nj * sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
+    CUDA_TRY(cudaStreamSynchronize(B.stream));
+    return INIM_OK;
+}
+
+// the plain form: one job at a time, host stop test after every iteration
+int run_plain(Batch& B, int max_iters) {
+    const int nj = (int)B.spec.size();
+    if ((int)B.plain.size() != nj) {
+        B.plain.resize(nj);
+        for (int k = 0; k < nj; ++k) CUDA_TRY(plain_alloc(B.plain[k], B.h_jobs[k].n));
+    }
+    if (nj != 1) return fail(INIM_E_ARG, "the plain form runs one job at a time");
+    for (int k = 0; k < nj; ++k) {
+        const Job* dj = B.d_jobs + k;
+        for (int it = 0; it < max_iters; ++it) {
+            CUDA_TRY(launch_raster(B.d_jobs, B.edge_blocks, B.job_blocks, B.row_blocks, B.stream));
+            CUDA_TRY(launch_density_table(dj, 1, B.stream));
+            CUDA_TRY(plain_iteration(dj, B.h_jobs[k], B.plain[k], B.stream));
+            CUDA_TRY(launch_areas_errors(B.d_jobs, nj, B.region_blocks, 1, B.stream));
+            g_launches += kKernelsPerPlainIteration;
+            CUDA_TRY(cudaMemcpyAsync(&B.h_states[k], B.d_states + k, sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
+            CUDA_TRY(cudaStreamSynchronize(B.stream));
+            if (!B.h_states[k].active) break;
+        }
+    }
+    return INIM_OK;
+}
+
+int check_params(const inim_params* p) {
+    if (!p) return fail(INIM_E_ARG, "params is NULL");
+    if (p->log2_res < kMinLog2 || p->log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
+    if (!(p->shape >= 0.0f && p->shape < 1.0f)) return fail(INIM_E_ARG, "shape must be in [0, 1)");
+    if (!(p->bdv_scale > 0.0f) || !std::isfinite(p->bdv_scale)) return fail(INIM_E_ARG, "bdv_scale must be > 0");
+    if (p->max_iters < 1) return fail(INIM_E_ARG, "max_iters must be >= 1");
+    if (p->precision < INIM_FP32 || p->precision > INIM_KAHAN) return fail(INIM_E_ARG, "bad precision");
+    if (p->form != INIM_FORM_FUSED && p->form != INIM_FORM_PLAIN) return fail(INIM_E_ARG, "bad form");
+    if (p->mode != INIM_DIRECT && p->mode != INIM_CUMULATIVE) return fail(INIM_E_ARG, "bad mode");
+    if (p->warm_start) return fail(INIM_E_STATE, "no warm-start network loaded");
+    return INIM_OK;
+}
+
+int check_values(const float* v, size_t n) {
+    for (size_t k = 0; k < n; ++k)
+        if (!(v[k] >= 0.0f) || !std::isfinite(v[k])) return fail(INIM_E_VALUE, "region values must be finite and >= 0");
+    return INIM_OK;
+}
+
+std::vector<float> to_host(const float* p, size_t n) {
+    std::vector<float> h(n);
+    if (is_device_ptr(p)) cudaMemcpy(h.data(), p, n * sizeof(float), cudaMemcpyDeviceToHost);
+    else std::memcpy(h.data(), p, n * sizeof(float));
+    return h;
+}
+
+int fill_stats(const JobState& s, inim_step_stats* out) {
+    int status = INIM_OK;
+    if (s.error) status = s.error;
+    else if (s.foldover || s.overlap) status = INIM_W_FOLDOVER;
+    else if (s.stop_on_rule && s.xi_stop > 0.0f && s.iters >= s.max_iters && !(s.xi < s.xi_stop))
+        status = INIM_W_NOT_CONVERGED;
+    if (out) {
+        out->iters = s.iters;
+        out->eps = (float)s.eps;
+        out->xi = (float)s.xi;
+        out->foldover = s.foldover;
+        out->overlap = s.overlap;
+        out->status = status;
+    }
+    return status;
+}
+
+int worst(int a, int b) {
+    if (a < 0 || b < 0) return std::min(a, b);
+    return std::max(a, b);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void inim_params_default(inim_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->log2_res = 10;
+    p->shape = 0.0f;
+    p->bdv_scale = 1.0f;
+    p->max_iters = 512;
+    p->xi_stop = 0.01f;
+    p->stall_window = 32;
+    p->eps_stop = 0.0f;
+    p->mode = INIM_DIRECT;
+    p->precision = INIM_FP32;
+    p->form = INIM_FORM_FUSED;
+    p->warm_start = 0;
+}
+
+const char* inim_status_string(int s) {
+    switch (s) {
+        case INIM_OK: return "ok";
+        case INIM_E_ARG: return "invalid argument";
+        case INIM_E_VALUE: return "invalid region value";
+        case INIM_E_CUDA: return "CUDA error";
+        case INIM_E_TIMEOUT: return "device wait timed out";
+        case INIM_E_CAPACITY: return "buffer capacity exceeded";
+        case INIM_E_STATE: return "invalid state";
+        case INIM_W_NOT_CONVERGED: return "not converged";
+        case INIM_W_FOLDOVER: return "fold-over detected";
+        default: return "unknown status";
+    }
+}
+
+const char* inim_last_error(void) { return g_last_error.c_str(); }
+
+int inim_map_create(const float* xy, int32_t n_verts, const int32_t* ring_off, int32_t n_rings,
+                    const int32_t* ring_idx, const int32_t* ring_region, int32_t n_regions, int32_t flags,
+                    inim_map** out) {
+    if (!out) return fail(INIM_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!xy || !ring_off || !ring_idx || !ring_region) return fail(INIM_E_ARG, "NULL input array");
+    if (n_verts < 1 || n_rings < 1) return fail(INIM_E_ARG, "n_verts and n_rings must be >= 1");
+    if (n_regions < 1 || n_regions > 65534) return fail(INIM_E_ARG, "n_regions must be in [1, 65534]");
+    const bool dev = (flags & INIM_MAP_DEVICE_PTRS) != 0;
+    auto fetch = [&](const void* src, void* dst, size_t bytes) {
+        if (dev) return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+        std::memcpy(dst, src, bytes);
+        return cudaSuccess;
+    };
+    std::vector<float> hxy((size_t)n_verts * 2);
+    std::vector<int> hoff(n_rings + 1), hreg(n_rings);
+    CUDA_TRY(fetch(xy, hxy.data(), hxy.size() * 4));
+    CUDA_TRY(fetch(ring_off, hoff.data(), hoff.size() * 4));
+    CUDA_TRY(fetch(ring_region, hreg.data(), hreg.size() * 4));
+    if (hoff[0] != 0) return fail(INIM_E_ARG, "ring_off[0] must be 0");
+    for (int r = 0; r < n_rings; ++r) {
+        if (hoff[r + 1] < hoff[r]) return fail(INIM_E_ARG, "ring_off must be non-decreasing");
+        if (hreg[r] < 0 || hreg[r] >= n_regions) return fail(INIM_E_ARG, "ring_region out of range");
+    }
+    const int total = hoff[n_rings];
+    std::vector<int> hidx(std::max(total, 1));
+    if (total > 0) CUDA_TRY(fetch(ring_idx, hidx.data(), (size_t)total * 4));
+    for (int k = 0; k < total; ++k)
+        if (hidx[k] < 0 || hidx[k] >= n_verts) return fail(INIM_E_ARG, "ring_idx out of range");
+    for (float v : hxy)
+        if (!std::isfinite(v) || v < -1.0f || v > 2.0f) return fail(INIM_E_ARG, "vertex coordinates must lie in [-1, 2]");
+
+    auto m = std::make_unique<inim_map>();
+    m->n_verts = n_verts; m->n_regions = n_regions; m->n_rings = n_rings;
+    // rings grouped by region, edges grouped by region (ring order kept)
+    std::vector<int> reg_ring_off(n_regions + 1, 0), reg_rings(n_rings);
+    for (int r = 0; r < n_rings; ++r) reg_ring_off[hreg[r] + 1]++;
+    for (int v = 0; v < n_regions; ++v) reg_ring_off[v + 1] += reg_ring_off[v];
+    {
+        std::vector<int> fill(reg_ring_off.begin(), reg_ring_off.end() - 1);
+        for (int r = 0; r < n_rings; ++r) reg_rings[fill[hreg[r]]++] = r;
+    }
+    std::vector<int2> edges;
+    std::vector<int> edge_region;
+    std::vector<float> sign0(n_regions, 0.0f);
+    edges.reserve(total);
+    for (int v = 0; v < n_regions; ++v) {
+        double area2 = 0.0;
+        for (int q = reg_ring_off[v]; q < reg_ring_off[v + 1]; ++q) {
+            const int r = reg_rings[q];
+            const int b = hoff[r], e = hoff[r + 1];
+            for (int k = b; k < e; ++k) {
+                const int a = hidx[k], c = hidx[k + 1 == e ? b : k + 1];
+                edges.push_back(make_int2(a, c));
+                edge_region.push_back(v);
+                m->h_edge_a.push_back(a);
+                m->h_edge_b.push_back(c);
+                area2 += (double)hxy[2 * a] * hxy[2 * c + 1] - (double)hxy[2 * c] * hxy[2 * a + 1];
+            }
+        }
+        sign0[v] = area2 > 0.0 ? 1.0f : (area2 < 0.0 ? -1.0f : 0.0f);
+    }
+    m->n_edges = (int)edges.size();
+    m->h_xy0 = hxy;
+    auto up = [&](void** dst, const void* src, size_t bytes) {
+        cudaError_t e = cudaMalloc(dst, bytes < 16 ? 16 : bytes);
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = up((void**)&m->edges, edges.data(), edges.size() * sizeof(int2));
+    if (e == cudaSuccess) e = up((void**)&m->edge_region, edge_region.data(), edge_region.size() * 4);
+    if (e == cudaSuccess) e = up((void**)&m->reg_ring_off, reg_ring_off.data(), reg_ring_off.size() * 4);
+    if (e == cudaSuccess) e = up((void**)&m->reg_rings, reg_rings.data(), reg_rings.size() * 4);
+    if (e == cudaSuccess) e = up((void**)&m->ring_off, hoff.data(), hoff.size() * 4);
+    if (e == cudaSuccess) e = up((void**)&m->ring_idx, hidx.data(), (size_t)total * 4);
+    if (e == cudaSuccess) e = up((void**)&m->sign0, sign0.data(), sign0.size() * 4);
+    if (e == cudaSuccess) e = up((void**)&m->xy0, hxy.data(), hxy.size() * 4);
+    if (e != cudaSuccess) {
+        inim_map_destroy(m.release());
+        return fail(INIM_E_CUDA, std::string("map upload: ") + cudaGetErrorString(e));
+    }
+    *out = m.release();
+    return INIM_OK;
+}
+
+int inim_map_destroy(inim_map* m) {
+    if (!m) return INIM_OK;
+    purge_map(m);
+    dfree(m->edges); dfree(m->edge_region); dfree(m->reg_ring_off); dfree(m->reg_rings);
+    dfree(m->ring_off); dfree(m->ring_idx); dfree(m->sign0); dfree(m->xy0);
+    delete m;
+    return INIM_OK;
+}
+
+int inim_map_info(const inim_map* m, int32_t* nv, int32_t* nr, int32_t* nrings, int32_t* ne) {
+    if (!m) return fail(INIM_E_ARG, "map is NULL");
+    if (nv) *nv = m->n_verts;
+    if (nr) *nr = m->n_regions;
+    if (nrings) *nrings = m->n_rings;
+    if (ne) *ne = m->n_edges;
+    return INIM_OK;
+}
+
+int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream);
+
+int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* params, const float* init_xy,
+             float* out_xy, inim_step_stats* stats, void* stream) {
+    if (!map || !values || !out_xy || T < 1) return fail(INIM_E_ARG, "bad arguments to inim_run");
+    int st = check_params(params);
+    if (st != INIM_OK) return st;
+    const int R = map->n_regions, V = map->n_verts;
+    // host values are checked here, device values by the density kernel
+    const bool val_dev = is_device_ptr(values);
+    if (!val_dev) {
+        st = check_values(values, (size_t)T * R);
+        if (st != INIM_OK) return st;
+    }
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    const bool out_dev = is_device_ptr(out_xy);
+    const float* start = init_xy ? init_xy : map->h_xy0.data();   // host or device
+
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    const bool direct = params->mode == INIM_DIRECT;
+    const bool plain = params->form == INIM_FORM_PLAIN;
+    const int nj = (direct && !plain) ? T : 1;
+    std::vector<JobSpec> spec(nj, JobSpec{map, params->log2_res, params->precision});
+    std::vector<const float*> starts(nj, map->h_xy0.data());
+    Batch* B = get_batch(spec, starts, &st);
+    if (!B) return st;
+    int result = INIM_OK;
+    const int rounds = (nj == T) ? 1 : T;
+    for (int t = 0; t < rounds; ++t) {
+        // values, vertices and state of the jobs of this round
+        for (int k = 0; k < nj; ++k) {
+            const int step = (nj == T) ? k : t;
+            Job& J = B->h_jobs[k];
+            J.lam = 1.0f - params->shape;
+            J.bdv_scale = params->bdv_scale;
+            CUDA_TRY(cudaMemcpyAsync(B->bufs[k].values, values + (size_t)step * R, R * 4, cudaMemcpyDefault, B->stream));
+            const bool reset = direct || t == 0;
+            if (reset) CUDA_TRY(cudaMemcpyAsync(B->bufs[k].xy, start, (size_t)V * 8, cudaMemcpyDefault, B->stream));
+            B->h_states[k] = initial_state(*params, 1, params->max_iters);
+        }
+        CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), nj * sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+        CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), nj * sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+        st = plain ? run_plain(*B, params->max_iters) : run_fused(*B, params->max_iters, needs_poll(*params));
+        if (st != INIM_OK) return st;
+        for (int k = 0; k < nj; ++k) {
+            const int step = (nj == T) ? k : t;
+            float* dst = out_xy + (size_t)step * V * 2;
+            CUDA_TRY(cudaMemcpyAsync(dst, B->bufs[k].xy, (size_t)V * 8,
+                                     out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, B->stream));
+            result = worst(result, fill_stats(B->h_states[k], stats ? stats + step : nullptr));
+        }
+        CUDA_TRY(cudaStreamSynchronize(B->stream));
+    }
+    return result;
+}
+
+int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
+    if (!jobs || n_jobs < 1) return fail(INIM_E_ARG, "no jobs");
+    std::vector<JobSpec> spec(n_jobs);
+    std::vector<const float*> cap_ptr(n_jobs), start_ptr(n_jobs);
+    bool poll = false;
+    for (int k = 0; k < n_jobs; ++k) {
+        const inim_job& j = jobs[k];
+        if (!j.map || !j.values || !j.out_xy) return fail(INIM_E_ARG, "job with NULL map, values or out_xy");
+        int st = check_params(&j.params);
+        if (st != INIM_OK) return st;
+        if (j.params.form != INIM_FORM_FUSED) return fail(INIM_E_ARG, "inim_run_batch needs the fused form");
+        if (j.params.precision != jobs[0].params.precision) return fail(INIM_E_ARG, "all jobs need one precision");
+        if (!is_device_ptr(j.values)) {     // device values are checked by the density kernel
+            st = check_values(j.values, j.map->n_regions);
+            if (st != INIM_OK) return st;
+        }
+        cap_ptr[k] = j.map->h_xy0.data();   // capacity estimate from the map (4x margin)
+        start_ptr[k] = j.init_xy ? j.init_xy : j.map->h_xy0.data();
+        spec[k] = JobSpec{j.map, j.params.log2_res, j.params.precision};
+        poll |= needs_poll(j.params);
+    }
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    int st = INIM_OK;
+    Batch* B = get_batch(spec, cap_ptr, &st);
+    if (!B) return st;
+    int max_it = 1;
+    for (int k = 0; k < n_jobs; ++k) {
+        const inim_job& j = jobs[k];
+        Job& J = B->h_jobs[k];
+        J.lam = 1.0f - j.params.shape;
+        J.bdv_scale = j.params.bdv_scale;
+        CUDA_TRY(cudaMemcpyAsync(B->bufs[k].values, j.values, (size_t)j.map->n_regions * 4, cudaMemcpyDefault, B->stream));
+        CUDA_TRY(cudaMemcpyAsync(B->bufs[k].xy, start_ptr[k], (size_t)j.map->n_verts * 8, cudaMemcpyDefault, B->stream));
+        B->h_states[k] = initial_state(j.params, 1, j.params.max_iters);
+        max_it = std::max(max_it, j.params.max_iters);
+    }
+    CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), n_jobs * sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), n_jobs * sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+    st = run_fused(*B, max_it, poll);
+    if (st != INIM_OK) return st;
+    int result = INIM_OK;
+    for (int k = 0; k < n_jobs; ++k) {
+        const inim_job& j = jobs[k];
+        CUDA_TRY(cudaMemcpyAsync(j.out_xy, B->bufs[k].xy, (size_t)j.map->n_verts * 8, cudaMemcpyDefault, B->stream));
+        result = worst(result, fill_stats(B->h_states[k], j.stats));
+    }
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    return result;
+}
+
+int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t* labels, int32_t* counts,
+                int32_t* overlap, void* stream) {
+    if (!map || !xy || !labels || !counts) return fail(INIM_E_ARG, "NULL argument");
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<float> hxy = to_host(xy, (size_t)map->n_verts * 2);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    int st = INIM_OK;
+    std::vector<JobSpec> spec{JobSpec{map, log2_res, INIM_FP32}};
+    std::vector<const float*> starts{hxy.data()};
+    Batch* B = get_batch(spec, starts, &st);
+    if (!B) return st;
+    inim_params p;
+    inim_params_default(&p);
+    B->h_states[0] = initial_state(p, 0, 1);
+    B->h_jobs[0].lam = 1.0f;
+    B->h_jobs[0].bdv_scale = 1.0f;
+    const int R = map->n_regions;
+    const int n = 1 << log2_res;
+    std::vector<float> ones(R, 1.0f);
+    CUDA_TRY(cudaMemcpyAsync(B->bufs[0].values, ones.data(), R * 4, cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, xy, (size_t)map->n_verts * 8, cudaMemcpyDefault, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(launch_raster(B->d_jobs, B->edge_blocks, B->job_blocks, B->row_blocks, B->stream));
+    CUDA_TRY(launch_density_table(B->d_jobs, 1, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(labels, B->bufs[0].labels, (size_t)n * n * 2, cudaMemcpyDeviceToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(counts, B->bufs[0].counts, (size_t)(R + 1) * 4, cudaMemcpyDeviceToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->h_states.data(), B->d_states, sizeof(JobState), cudaMemcpyDeviceToHost, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    if (overlap) *overlap = B->h_states[0].overlap;
+    if (B->h_states[0].error) return fail(B->h_states[0].error, "raster capacity exceeded");
+    return INIM_OK;
+}
+
+static int texture_batch(int log2_res, int precision, int frac_bits, const float* density, Batch** out) {
+    int st = INIM_OK;
+    std::vector<JobSpec> spec{JobSpec{nullptr, log2_res, precision}};
+    std::vector<const float*> starts{nullptr};
+    Batch* B = get_batch(spec, starts, &st);
+    if (!B) return st;
+    inim_params p;
+    inim_params_default(&p);
+    B->h_states[0] = initial_state(p, 0, 1);
+    B->h_states[0].fix_bits = frac_bits;
+    CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+    const Group& g = B->groups[0];
+    if (precision == INIM_FIX64) CUDA_TRY(launch_scan_fix64(B->d_jobs, g.band, g.carry, g.tile, density, B->stream));
+    else if (precision == INIM_KAHAN) CUDA_TRY(launch_scan_kahan(B->d_jobs, g.band, g.carry, g.tile, density, B->stream));
+    else CUDA_TRY(launch_scan_fp32(B->d_jobs, g.band, g.carry, g.tile, density, B->stream));
+    *out = B;
+    return INIM_OK;
+}
+
+int inim_inims(const float* density, int32_t log2_res, int32_t precision, int32_t frac_bits, void* S, void* T,
+               void* A, void* Bv, void* stream) {
+    if (!density || !S || !T || !A || !Bv) return fail(INIM_E_ARG, "NULL argument");
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
+    if (precision < INIM_FP32 || precision > INIM_KAHAN) return fail(INIM_E_ARG, "bad precision");
+    if (precision == INIM_FIX64 && (frac_bits < 0 || frac_bits > 62)) return fail(INIM_E_ARG, "bad frac_bits");
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    Batch* B = nullptr;
+    int st = texture_batch(log2_res, precision, frac_bits, density, &B);
+    if (st != INIM_OK) return st;
+    CUDA_TRY(launch_finalize_B(B->d_jobs, precision, B->stream));
+    const size_t n = (size_t)1 << log2_res, es = elem_size(precision);
+    CUDA_TRY(cudaMemcpyAsync(S, B->bufs[0].S, n * n * es, cudaMemcpyDeviceToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(T, B->bufs[0].T, n * n * es, cudaMemcpyDeviceToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(A, B->bufs[0].A, (2 * n - 1) * es, cudaMemcpyDeviceToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(Bv, B->bufs[0].B, (2 * n - 1) * es, cudaMemcpyDeviceToDevice, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    return INIM_OK;
+}
+
+int inim_displacement(const float* density, int32_t log2_res, int32_t precision, const float* xy, int32_t n,
+                      float* delta, void* stream) {
+    if (!density || !xy || !delta || n < 0) return fail(INIM_E_ARG, "bad arguments");
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
+    if (precision < INIM_FP32 || precision > INIM_KAHAN) return fail(INIM_E_ARG, "bad precision");
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    // fixed point: 2^30 units per unit density keeps 4096^2 textures of
+    // densities up to 2^6 below 2^62
+    Batch* B = nullptr;
+    int st = texture_batch(log2_res, precision, 30, density, &B);
+    if (st != INIM_OK) return st;
+    CUDA_TRY(launch_displacement(B->d_jobs, xy, n, delta, precision, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    return INIM_OK;
+}
+
+int inim_iterate(const inim_map* map, float* xy, const float* values, const inim_params* params, int32_t n_iters,
+                 inim_step_stats* stats, void* stream) {
+    if (!map || !xy || !values || n_iters < 0) return fail(INIM_E_ARG, "bad arguments");
+    int st = check_params(params);
+    if (st != INIM_OK) return st;
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<float> hv = to_host(values, map->n_regions);
+    st = check_values(hv.data(), hv.size());
+    if (st != INIM_OK) return st;
+    std::vector<float> hxy = to_host(xy, (size_t)map->n_verts * 2);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    std::vector<JobSpec> spec{JobSpec{map, params->log2_res, params->precision}};
+    std::vector<const float*> starts{hxy.data()};
+    Batch* B = get_batch(spec, starts, &st);
+    if (!B) return st;
+    Job& J = B->h_jobs[0];
+    J.lam = 1.0f - params->shape;
+    J.bdv_scale = params->bdv_scale;
+    B->h_states[0] = initial_state(*params, 0, std::max(n_iters, 1));
+    CUDA_TRY(cudaMemcpyAsync(B->bufs[0].values, hv.data(), hv.size() * 4, cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, hxy.data(), hxy.size() * 4, cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+    if (n_iters > 0) {
+        if (params->form == INIM_FORM_PLAIN) st = run_plain(*B, n_iters);
+        else {
+            for (int k = 0; k < n_iters; ++k) CUDA_TRY(enqueue_fused_iteration(*B, B->stream));
+            g_launches += (long long)n_iters * kernels_per_fused_iteration(*B);
+            CUDA_TRY(cudaMemcpyAsync(B->h_states.data(), B->d_states, sizeof(JobState), cudaMemcpyDeviceToHost, B->stream));
+            CUDA_TRY(cudaStreamSynchronize(B->stream));
+        }
+        if (st != INIM_OK) return st;
+    }
+    CUDA_TRY(cudaMemcpyAsync(xy, B->bufs[0].xy, (size_t)map->n_verts * 8, cudaMemcpyDefault, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    return fill_stats(B->h_states[0], stats);
+}
+
+int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream) {
+    if (!map || !xy || !areas) return fail(INIM_E_ARG, "NULL argument");
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<float> hxy = to_host(xy, (size_t)map->n_verts * 2);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    int st = INIM_OK;
+    std::vector<JobSpec> spec{JobSpec{map, kMinLog2, INIM_FP32}};
+    std::vector<const float*> starts{hxy.data()};
+    Batch* B = get_batch(spec, starts, &st);
+    if (!B) return st;
+    inim_params p;
+    inim_params_default(&p);
+    B->h_states[0] = initial_state(p, 0, 1);
+    CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, hxy.data(), hxy.size() * 4, cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(launch_areas_errors(B->d_jobs, 1, B->region_blocks, -1, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(areas, B->bufs[0].areas, (size_t)map->n_regions * 8, cudaMemcpyDefault, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    return INIM_OK;
+}
+
+static const char* kStageNames[] = {"raster", "density_table", "scan_phase1", "scan_carry", "scan_phase3",
+                                     "gather_move", "areas_errors"};
+constexpr int kNumStages = 7;
+
+const char* inim_stage_name(int32_t i) {
+    return (i >= 0 && i < kNumStages) ? kStageNames[i] : "";
+}
+
+long long inim_launch_count(void) { return g_launches.load(); }
+
+int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_stages) {
+    if (reps < 1 || !ms || max_stages < kNumStages) return fail(INIM_E_ARG, "bad arguments");
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (g_cache.empty() || !g_cache.front()->spec[0].map) return fail(INIM_E_STATE, "no map batch has run yet");
+    Batch& B = *g_cache.front();
+    const int nj = (int)B.spec.size();
+    for (int k = 0; k < nj; ++k) {
+        JobState& s = B.h_states[k];
+        s.active = 1; s.stop_on_rule = 0; s.max_iters = INT_MAX; s.error = 0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(B.d_states, B.h_states.data(), nj * sizeof(JobState), cudaMemcpyHostToDevice, B.stream));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    auto stage = [&](int i) -> cudaError_t {
+        switch (i) {
+            case 0: return launch_raster(B.d_jobs, B.edge_blocks, B.job_blocks, B.row_blocks, B.stream);
+            case 1: return launch_density_table(B.d_jobs, nj, B.stream);
+            case 2: case 3: case 4: {
+                cudaError_t e = cudaSuccess;
+                for (auto& g : B.groups) {
+                    if (B.precision == INIM_FIX64) e = launch_scan_fix64(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 1);
+                    else if (B.precision == INIM_KAHAN) e = launch_scan_kahan(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 1);
+                    else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 1);
+                    if (e != cudaSuccess) break;
+                }
+                return e;
+            }
+            case 5: return launch_gather(B.d_jobs, B.vert_blocks, B.precision, B.stream);
+            default: return launch_areas_errors(B.d_jobs, nj, B.region_blocks, 0, B.stream);
+        }
+    };
+    int rc = INIM_OK;
+    for (int i = 0; i < kNumStages && rc == INIM_OK; ++i) {
+        cudaError_t e = stage(i);                       // warm
+        if (e == cudaSuccess) e = cudaEventRecord(e0, B.stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = stage(i);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, B.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) rc = fail(INIM_E_CUDA, std::string("profile: ") + cudaGetErrorString(e));
+        ms[i] = t / (float)reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_stages) *n_stages = kNumStages;
+    return rc;
+}
+
+}  // extern "C"

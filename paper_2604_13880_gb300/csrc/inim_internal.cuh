@@ -1,0 +1,214 @@
+// Internal declarations shared by the CUDA translation units of the InIm
+// cartogram library: the device-resident job descriptor, per-job state, and
+// small device helpers (fixed-point snap, Eq. (2), uniform-density counts).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/inim.h"
+
+namespace inim {
+
+constexpr int kSubBits = 8;          // sub-pixel bits of the fixed-point raster
+constexpr int kMaxLog2 = 12;         // N <= 4096
+constexpr int kMinLog2 = 8;          // N >= 256
+
+// Per-solve state living in device memory: the stop rule (Sec. 4.1 defaults)
+// and the statistics of the last iteration.
+struct JobState {
+    int   active;        // 1 while iterating; kernels skip inactive jobs
+    int   iters;         // iterations done
+    int   max_iters;
+    int   stall_window;
+    float xi_stop;
+    float eps_stop;
+    double best_xi;      // best max error so far (stall rule)
+    int   since;         // iterations since best_xi improved
+    int   pad0;
+    double eps, xi;      // errors after the last iteration
+    int   foldover;      // a region changed the sign of its area
+    int   overlap;       // a pixel lay inside two regions
+    int   error;         // INIM_E_* raised on the device (capacity, ...)
+    int   fix_bits;      // fraction bits of the fixed-point InIms
+    double d0;           // area-weighted mean density of the regions
+    double mass;         // total mass in the texture (w(v) = s(v) / mass)
+    double bdv_abs;      // background density in value units
+    int   stop_on_rule;  // 0: run exactly max_iters (no early stop)
+    int   pad;
+};
+
+// Everything a kernel needs to work on one job.  Lives in device memory; one
+// entry per job of a batch.  Texture element (i, j) is at j*n + i.
+struct Job {
+    // texture
+    int n, log2n;
+    // map topology (shared by all jobs of one map)
+    int n_verts, n_regions, n_edges, n_rings;
+    const int2* edges;         // [n_edges] vertex ids, grouped by region
+    const int*  edge_region;   // [n_edges]
+    const int*  reg_ring_off;  // [n_regions+1] into reg_rings
+    const int*  reg_rings;     // ring ids grouped by region
+    const int*  ring_off;      // [n_rings+1]
+    const int*  ring_idx;
+    const float* sign0;        // [n_regions] sign of the initial area (0 = none)
+    // solve
+    float2*      xy;           // [n_verts] vertices, moved in place
+    const float* values;       // [n_regions] s(v)
+    float lam;                 // blend weight = 1 - shape
+    float bdv_scale;
+    int   precision;           // INIM_FP32 / INIM_FIX64 / INIM_KAHAN
+    // raster workspace
+    uint16_t* labels;          // [n*n]
+    int*      row_cnt;         // [n]   crossings per row (zero between uses)
+    int*      row_off;         // [n+1] exclusive prefix of row_cnt
+    uint32_t* keys;            // [key_cap] (region << 16 | column)
+    int       key_cap;
+    int*      counts;          // [n_regions+1] pixel areas o(v); last = background
+    float*    dens;            // [n_regions+1] density relative to d0
+    // integral images (element type by precision)
+    void*  S;                  // [n*n] 2-D inclusive prefix (alpha)
+    void*  T;                  // [n*n] top wedge (alpha_t)
+    void*  A;                  // [2n-1] A(s) = sum_{i+j<=s} d
+    void*  B;                  // [2n-1] w<=0: sum_{i-j<=w} d ; w>0: sum_{i-j>w} d
+    void*  rowcum;             // [n] S(n-1, j)
+    // band scan workspace
+    int    H, nb;              // band height, number of bands
+    void*  agg;                // [3][nb][n] band aggregates
+    void*  carry;              // [3][nb][n] band carries
+    // areas and errors
+    double*   areas;           // [n_regions] signed shoelace areas
+    JobState* st;
+};
+
+// ---------------------------------------------------------------------------
+// integer helpers (exact rasterisation rule, Sec. 4.1 step 2 reading)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ long long floor_div(long long a, long long b) {
+    // b > 0
+    long long q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+__host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) {
+    return -floor_div(-a, b);
+}
+
+// X = rint(x * 2^(k+8)) with ties to even (the scale is a power of two, so the
+// product is exact).
+__device__ __forceinline__ long long snap_coord(float x, float scale) {
+    return __float2ll_rn(x * scale);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (2): t = (1/2C)(alpha q1 + beta q2 + gamma q3 + delta q4
+//                     + alpha_t (x,1) + beta_t (1,y) + gamma_t (x,0) + delta_t (0,y))
+// with the anchors q1..q4 of Sec. 3.2 (y downward).  Inputs are the eight
+// sums at one pixel and the pixel centre (x, y).
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ void eq2(F a, F b, F g, F d, F at, F bt, F gt, F dt, F C,
+                                    F x, F y, F& tx, F& ty) {
+    F q1x, q1y, q3x, q3y, q2x, q2y, q4x, q4y;
+    if (y < x) { q1x = F(1); q1y = F(1) + y - x; q3x = x - y; q3y = F(0); }
+    else       { q1x = F(1) - y + x; q1y = F(1); q3x = F(0); q3y = y - x; }
+    F s = x + y;
+    if (s < F(1)) { q2x = s; q2y = F(0); q4x = F(0); q4y = s; }
+    else          { q2x = F(1); q2y = s - F(1); q4x = s - F(1); q4y = F(1); }
+    F inv = F(1) / (F(2) * C);
+    tx = (a * q1x + b * q2x + g * q3x + d * q4x + at * x + bt + gt * x) * inv;
+    ty = (a * q1y + b * q2y + g * q3y + d * q4y + at + bt * y + dt * y) * inv;
+}
+
+// Pixel counts of the eight regions for a constant texture (exact integers):
+// the InIms of t(.; d0) (Sec. 4.1 step 1) in closed form.
+struct Counts8 { long long a, b, g, d, at, bt, gt, dt, C; };
+
+__host__ __device__ __forceinline__ long long anti_prefix_count(long long s, long long n) {
+    // #{(i', j') in [0,n)^2 : i' + j' <= s}; the complement of s' = 2n-2-s-1
+    if (s < 0) return 0;
+    if (s >= 2 * n - 2) return n * n;
+    if (s <= n - 1) return (s + 1) * (s + 2) / 2;
+    long long m = 2 * n - 3 - s;          // i'+j' > s  <=>  (n-1-i')+(n-1-j') <= m
+    return n * n - (m + 1) * (m + 2) / 2;
+}
+
+__host__ __device__ __forceinline__ Counts8 uniform_counts(int i, int j, int n) {
+    Counts8 c;
+    long long I = i, J = j, N = n;
+    c.C = N * N;
+    c.a = (I + 1) * (J + 1);
+    c.b = (I + 1) * (N - 1 - J);
+    c.g = (N - 1 - I) * (N - 1 - J);
+    c.d = (N - 1 - I) * (J + 1);
+    // left wedge: row j' holds max(0, i + 1 - |j' - j|) pixels
+    long long m = I + 1;
+    long long k1 = I < J ? I : J;
+    long long k2 = I < (N - 1 - J) ? I : (N - 1 - J);
+    long long L = m + (k1 * m - k1 * (k1 + 1) / 2) + (k2 * m - k2 * (k2 + 1) / 2);
+    long long A = anti_prefix_count(I + J, N);
+    long long B = anti_prefix_count(I - J + N - 1, N);   // i'-j' <= w  <=>  i'+(n-1-j') <= w+n-1
+    c.bt = L;
+    c.at = A - L;
+    c.gt = B - L;
+    c.dt = c.C - c.bt - c.at - c.gt;
+    return c;
+}
+
+// t(x, y; d0) at pixel (i, j) in float, from the exact counts.
+__device__ __forceinline__ float2 t_uniform(int i, int j, int n) {
+    Counts8 c = uniform_counts(i, j, n);
+    float inv_n = 1.0f / (float)n;
+    float x = ((float)i + 0.5f) * inv_n, y = ((float)j + 0.5f) * inv_n;
+    float tx, ty;
+    eq2<float>((float)c.a, (float)c.b, (float)c.g, (float)c.d, (float)c.at, (float)c.bt,
+               (float)c.gt, (float)c.dt, (float)c.C, x, y, tx, ty);
+    return make_float2(tx, ty);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct BlockMap {            // block -> (job, first item) tables for one kernel
+    int2* d_map = nullptr;   // device [n_blocks]
+    int   n_blocks = 0;
+};
+
+struct ScanTile { int H; int cpt; int nt; };   // band height, columns/thread, threads
+
+cudaError_t launch_raster(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& job_blocks,
+                          const BlockMap& row_blocks, cudaStream_t s);
+cudaError_t launch_density_table(const Job* d_jobs, int n_jobs, cudaStream_t s);
+cudaError_t launch_scan_fp32(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
+                             ScanTile tile, const float* dtex, cudaStream_t s, int phase = 0);
+cudaError_t launch_scan_fix64(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
+                              ScanTile tile, const float* dtex, cudaStream_t s, int phase = 0);
+cudaError_t launch_scan_kahan(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
+                              ScanTile tile, const float* dtex, cudaStream_t s, int phase = 0);
+cudaError_t launch_gather(const Job* d_jobs, const BlockMap& vert_blocks, int precision,
+                          cudaStream_t s);
+// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only
+cudaError_t launch_areas_errors(const Job* d_jobs, int n_jobs, const BlockMap& region_blocks,
+                                int update_state, cudaStream_t s);
+cudaError_t launch_displacement(const Job* d_job, const float* xy, int n, float* delta,
+                                int precision, cudaStream_t s);
+cudaError_t launch_finalize_B(const Job* d_job, int precision, cudaStream_t s);
+
+// plain (unfused) form: extra full textures of one job
+struct PlainWork {
+    float*  d   = nullptr;   // [n*n] density
+    float*  R   = nullptr;   // [n*n] row prefix
+    float*  S   = nullptr;   // [n*n] 2-D prefix
+    float*  D1  = nullptr;   // [n*n] diagonal ray sums
+    float*  D2  = nullptr;   // [n*n] anti-diagonal ray sums
+    float*  L   = nullptr;   // [n*n] left wedge
+    float*  ad  = nullptr;   // [2n-1] anti-diagonal sums -> A
+    float*  dd  = nullptr;   // [2n-1] diagonal sums -> B
+    float2* t0  = nullptr;   // [n*n] t(.; d0), computed once
+    float2* fld = nullptr;   // [n*n] displacement field
+    int     n   = 0;
+};
+cudaError_t plain_alloc(PlainWork& w, int n);
+void plain_free(PlainWork& w);
+cudaError_t plain_iteration(const Job* d_job, const Job& h_job, PlainWork& w, cudaStream_t s);
+
+}  // namespace inim

@@ -1,0 +1,390 @@
+// Steps 3-4 of the static algorithm (Sec. 4.1): density texture and integral
+// images (Sec. 3.1), fused into one reduce-then-scan over full-width row bands.
+//
+// Stored per pixel: S = alpha (2-D inclusive prefix) and T = alpha_t (top
+// wedge: the pixels (i', j') with j' < j and i - (j - j') < i' <= i + (j - j')).
+// The other six InIms follow from S, T and the 1-D arrays A, B, rowcum through
+// Eq. (1):  beta = S(i, N-1) - S, delta = S(N-1, j) - S, gamma = C - the rest;
+// beta_t = A(i+j) - T, gamma_t = B(i-j) - beta_t, delta_t = C - the rest.
+//
+// Both S and T are causal from the top, so one top-down sweep over rows gives
+// them.  With R(i, j) the row prefix of d:
+//   S(i, j)  = S(i, j-1) + R(i, j)
+//   E1(x, j) = R(x, j) + E1(x+1, j-1)     (R(x >= N) = row total)
+//   E2(x, j) = R(x, j) + E2(x-1, j-1)     (R(x < 0) = 0)
+//   T(i, j)  = E1(i+1, j-1) - E2(i-1, j-1)
+// E1 / E2 sum R along the two upward diagonal rays; their difference is the
+// mass of the wedge.  Special values: A(s) = E1(0, s) for s < N and
+// A(s) = E1(s-N+1, N-1) beyond; B(w) = E2(w+N-1, N-1) for w <= 0, and for
+// w > 0 the complement sum_{i'-j' > w} d = S(N-1, r) - E2(N-1, r), r = N-1-w.
+//
+// Parallel form (reduce-then-scan over bands of H rows, no inter-block waits):
+//   phase 1  per band: band-local S, E1, E2 of the band's last row (zero carry)
+//   phase 2  per column / diagonal: carries into every band
+//            Sc_b(i) = sum of earlier bands' S aggregates
+//            E1c_{b+1}(x) = E1loc_b(x) + E1c_b(x+H)   (x+H >= N: rowcum)
+//            E2c_{b+1}(x) = E2loc_b(x) + E2c_b(x-H)   (x-H < 0: 0)
+//   phase 3  per band: recompute the rows, add the carries, write S, T, A, B.
+// Each thread owns CPT contiguous columns of the full-width band; the row
+// prefix is a thread-serial scan plus one warp scan plus a block exclusive
+// offset (one __syncthreads per row, double-buffered).
+#pragma once
+
+#include "inim_internal.cuh"
+
+namespace inim {
+
+// ---------------------------------------------------------------------------
+// accumulator types of the three precisions
+// ---------------------------------------------------------------------------
+struct AccF32 {
+    using T = float;
+    static __device__ __forceinline__ T zero() { return 0.0f; }
+    static __device__ __forceinline__ T from(float d, float) { return d; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ float ratio(T a, T c) { return a / c; }
+};
+
+struct AccFix {   // 64-bit fixed point, exact sums
+    using T = long long;
+    static __device__ __forceinline__ T zero() { return 0; }
+    static __device__ __forceinline__ T from(float d, float scale) { return __float2ll_rn(d * scale); }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ float ratio(T a, T c) { return (float)((double)a / (double)c); }
+};
+
+struct AccKahan {   // compensated float pairs: value = hi + lo
+    using T = float2;
+    static __device__ __forceinline__ T zero() { return make_float2(0.0f, 0.0f); }
+    static __device__ __forceinline__ T from(float d, float) { return make_float2(d, 0.0f); }
+    static __device__ __forceinline__ T add(T a, T b) {
+        // two-sum of the high parts, then fold in the low parts and renormalise
+        float s = __fadd_rn(a.x, b.x);
+        float bb = __fsub_rn(s, a.x);
+        float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+        e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+        float hi = __fadd_rn(s, e);
+        float lo = __fsub_rn(e, __fsub_rn(hi, s));
+        return make_float2(hi, lo);
+    }
+    static __device__ __forceinline__ T sub(T a, T b) { return add(a, make_float2(-b.x, -b.y)); }
+    static __device__ __forceinline__ T shfl_up(T v, int o) {
+        return make_float2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
+    }
+    static __device__ __forceinline__ float ratio(T a, T c) {
+        return (float)(((double)a.x + (double)a.y) / ((double)c.x + (double)c.y));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// density source: labels + per-region table, or a given float texture
+// ---------------------------------------------------------------------------
+template <int CPT>
+__device__ __forceinline__ void load_density(const Job& J, const float* __restrict__ dtex, int j,
+                                             int i0, float (&d)[CPT]) {
+    const size_t base = (size_t)j * J.n + i0;
+    if (dtex) {
+        if constexpr (CPT % 4 == 0) {
+#pragma unroll
+            for (int k = 0; k < CPT; k += 4) {
+                float4 v = *reinterpret_cast<const float4*>(dtex + base + k);
+                d[k] = v.x; d[k + 1] = v.y; d[k + 2] = v.z; d[k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) d[k] = dtex[base + k];
+        }
+        return;
+    }
+    uint16_t lab[CPT];
+    const uint16_t* src = J.labels + base;
+    if constexpr (CPT == 8) {
+        uint4 v = *reinterpret_cast<const uint4*>(src);
+        unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { lab[2 * k] = w[k] & 0xffffu; lab[2 * k + 1] = w[k] >> 16; }
+    } else if constexpr (CPT == 4) {
+        uint2 v = *reinterpret_cast<const uint2*>(src);
+        lab[0] = v.x & 0xffffu; lab[1] = v.x >> 16; lab[2] = v.y & 0xffffu; lab[3] = v.y >> 16;
+    } else if constexpr (CPT == 2) {
+        unsigned v = *reinterpret_cast<const unsigned*>(src);
+        lab[0] = v & 0xffffu; lab[1] = v >> 16;
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) lab[k] = src[k];
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) d[k] = __ldg(J.dens + lab[k]);
+}
+
+template <class Acc, int CPT>
+__device__ __forceinline__ void store_row(typename Acc::T* dst, const typename Acc::T (&v)[CPT]) {
+    using T = typename Acc::T;
+    if constexpr (sizeof(T) == 4 && CPT % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < CPT; k += 4)
+            reinterpret_cast<float4*>(dst)[k / 4] = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    } else if constexpr (sizeof(T) == 8 && CPT % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < CPT; k += 2) {
+            T pair[2] = {v[k], v[k + 1]};
+            reinterpret_cast<uint4*>(dst)[k / 2] = *reinterpret_cast<const uint4*>(pair);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) dst[k] = v[k];
+    }
+}
+
+template <class Acc, int NT>
+struct ScanShared {
+    typename Acc::T wtot[2][NT / 32];
+    typename Acc::T e1first[2][NT];
+    typename Acc::T e2last[2][NT];
+};
+
+// phase 1 (PHASE == 1) or phase 3 (PHASE == 3) of one band
+template <class Acc, int CPT, int NT, int PHASE>
+__global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
+                                                  const int2* __restrict__ bmap,
+                                                  const float* __restrict__ dtex) {
+    using T = typename Acc::T;
+    __shared__ ScanShared<Acc, NT> sh;
+    const int2 m = bmap[blockIdx.x];
+    const Job& J = jobs[m.x];
+    if (!J.st->active) return;
+    const int n = J.n, H = J.H, nb = J.nb;
+    const int band = m.y;
+    const int j0 = band * H;
+    const int rows = min(H, n - j0);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int i0 = tid * CPT;
+    const float qscale = ldexpf(1.0f, J.st->fix_bits);   // fixed-point unit (FIX64 only)
+
+    T Sacc[CPT], E1[CPT], E2[CPT];
+    T e1edge = Acc::zero();             // band-local E1 beyond the right edge
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) { Sacc[k] = Acc::zero(); E1[k] = Acc::zero(); E2[k] = Acc::zero(); }
+
+    // phase 3 carries
+    const T* cS = nullptr;
+    const T* c1 = nullptr;
+    const T* c2 = nullptr;
+    T w1[CPT], w2[CPT];
+    T rc_above = Acc::zero();           // rowcum(j0 - 1) = E1 beyond the edge at row j0-1
+    if constexpr (PHASE == 3) {
+        const T* carry = reinterpret_cast<const T*>(J.carry);
+        cS = carry + (size_t)band * n;
+        c1 = carry + (size_t)(nb + band) * n;
+        c2 = carry + (size_t)(2 * nb + band) * n;
+        rc_above = cS[n - 1];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            Sacc[k] = cS[i0 + k];
+            const int x1 = i0 + k + 1;              // E1c at i + r + 1, r = 0
+            w1[k] = x1 < n ? c1[x1] : rc_above;
+            const int x2 = i0 + k - 1;              // E2c at i - r - 1, r = 0
+            w2[k] = x2 >= 0 ? c2[x2] : Acc::zero();
+        }
+    }
+
+    T* Sout = reinterpret_cast<T*>(J.S);
+    T* Tout = reinterpret_cast<T*>(J.T);
+    T* Aout = reinterpret_cast<T*>(J.A);
+    T* Bout = reinterpret_cast<T*>(J.B);
+    T* RCout = reinterpret_cast<T*>(J.rowcum);
+
+    float dn[CPT];
+    load_density<CPT>(J, dtex, j0, i0, dn);
+    for (int r = 0; r < rows; ++r) {
+        const int j = j0 + r;
+        float d[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) d[k] = dn[k];
+        if (r + 1 < rows) load_density<CPT>(J, dtex, j + 1, i0, dn);   // prefetch
+
+        // thread-local inclusive prefix
+        T p[CPT];
+        T run = Acc::zero();
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) { run = Acc::add(run, Acc::from(d[k], qscale)); p[k] = run; }
+        // warp inclusive scan of the thread totals
+        T incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T t = Acc::shfl_up(incl, o);
+            if (lane >= o) incl = Acc::add(incl, t);
+        }
+        const int buf = r & 1;
+        if (lane == 31) sh.wtot[buf][wid] = incl;
+        sh.e1first[buf][tid] = E1[0];
+        sh.e2last[buf][tid] = E2[CPT - 1];
+        __syncthreads();
+        T off = Acc::sub(incl, run);          // exclusive within the warp
+        T rowtot = Acc::zero();
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) {
+            const T t = sh.wtot[buf][w];
+            if (w < wid) off = Acc::add(off, t);
+            rowtot = Acc::add(rowtot, t);
+        }
+        const T nbr1 = (tid + 1 < NT) ? sh.e1first[buf][tid + 1] : e1edge;     // E1(i0+CPT, j-1) local
+        const T nbr2 = (tid > 0) ? sh.e2last[buf][tid - 1] : Acc::zero();      // E2(i0-1, j-1) local
+
+        T Tv[CPT];
+        T R[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) R[k] = Acc::add(off, p[k]);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const T e1p = (k + 1 < CPT) ? E1[k + 1] : nbr1;   // E1 local at (i+1, j-1)
+            const T e2p = (k > 0) ? E2[k - 1] : nbr2;          // E2 local at (i-1, j-1)
+            if constexpr (PHASE == 3) Tv[k] = Acc::sub(Acc::add(e1p, w1[k]), Acc::add(e2p, w2[k]));
+            Sacc[k] = Acc::add(Sacc[k], R[k]);
+            // E1 / E2 need the old neighbours: build the new rows in p and R
+            p[k] = Acc::add(R[k], e1p);       // new E1[k]
+            R[k] = Acc::add(R[k], e2p);       // new E2[k]
+        }
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) E1[k] = p[k];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) E2[k] = R[k];
+        e1edge = Acc::add(e1edge, rowtot);
+
+        if constexpr (PHASE == 3) {
+            const size_t rowbase = (size_t)j * n + i0;
+            store_row<Acc, CPT>(Sout + rowbase, Sacc);
+            store_row<Acc, CPT>(Tout + rowbase, Tv);
+            if (tid == 0) Aout[j] = Acc::add(E1[0], w1[0]);                      // A(j) = E1(0, j)
+            if (tid == NT - 1) {
+                RCout[j] = Sacc[CPT - 1];                                       // S(N-1, j)
+                if (j < n - 1)                                                  // w = N-1-j > 0
+                    Bout[2 * n - 2 - j] = Acc::sub(Sacc[CPT - 1], Acc::add(E2[CPT - 1], w2[CPT - 1]));
+            }
+            if (j == n - 1) {
+#pragma unroll
+                for (int k = 0; k < CPT; ++k) {
+                    Aout[i0 + k + n - 1] = Acc::add(E1[k], w1[k]);               // A(x+N-1) = E1(x, N-1)
+                    Bout[i0 + k] = Acc::add(E2[k], w2[k]);                       // B(x-N+1) = E2(x, N-1)
+                }
+            }
+            // slide the carry windows to row r + 1
+            const int rn = r + 1;
+#pragma unroll
+            for (int k = 0; k < CPT - 1; ++k) w1[k] = w1[k + 1];
+            {
+                const int x1 = i0 + CPT - 1 + rn + 1;
+                w1[CPT - 1] = x1 < n ? c1[x1] : rc_above;
+            }
+#pragma unroll
+            for (int k = CPT - 1; k > 0; --k) w2[k] = w2[k - 1];
+            {
+                const int x2 = i0 - rn - 1;
+                w2[0] = x2 >= 0 ? c2[x2] : Acc::zero();
+            }
+        }
+    }
+    if constexpr (PHASE == 1) {
+        T* agg = reinterpret_cast<T*>(J.agg);
+        store_row<Acc, CPT>(agg + (size_t)band * n + i0, Sacc);
+        store_row<Acc, CPT>(agg + (size_t)(nb + band) * n + i0, E1);
+        store_row<Acc, CPT>(agg + (size_t)(2 * nb + band) * n + i0, E2);
+    }
+}
+
+// phase 2: carries.  Index space per job: [0, n) S columns, then E1
+// diagonals q = x + b H in [0, n + (nb-1) H), then E2 diagonals
+// q = x - b H + (nb-1) H in [0, n + (nb-1) H).
+template <class Acc>
+__global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs,
+                                                    const int2* __restrict__ bmap) {
+    using T = typename Acc::T;
+    const int2 m = bmap[blockIdx.x];
+    const Job& J = jobs[m.x];
+    if (!J.st->active) return;
+    const int n = J.n, H = J.H, nb = J.nb;
+    const int span = n + (nb - 1) * H;
+    int q = m.y * blockDim.x + threadIdx.x;
+    const T* agg = reinterpret_cast<const T*>(J.agg);
+    T* carry = reinterpret_cast<T*>(J.carry);
+    const T* aS = agg;
+    const T* a1 = agg + (size_t)nb * n;
+    const T* a2 = agg + (size_t)2 * nb * n;
+    T* cS = carry;
+    T* c1 = carry + (size_t)nb * n;
+    T* c2 = carry + (size_t)2 * nb * n;
+    if (q < n) {
+        T acc = Acc::zero();
+        for (int b = 0; b < nb; ++b) {
+            cS[(size_t)b * n + q] = acc;
+            acc = Acc::add(acc, aS[(size_t)b * n + q]);
+        }
+        return;
+    }
+    q -= n;
+    if (q < span) {                     // E1 chain: x_b = q - b H
+        T acc = Acc::zero();
+        T rc = Acc::zero();              // rowcum at the row above band b
+        for (int b = 0; b < nb; ++b) {
+            const int x = q - b * H;
+            if (x >= n) acc = rc;
+            else c1[(size_t)b * n + x] = acc;
+            const int xn = x - H;
+            if (xn < 0) break;
+            const T bandrc = aS[(size_t)b * n + (n - 1)];
+            const T loc = xn < n ? a1[(size_t)b * n + xn] : bandrc;
+            acc = Acc::add(loc, acc);
+            rc = Acc::add(rc, bandrc);
+        }
+        return;
+    }
+    q -= span;
+    if (q < span) {                     // E2 chain: x_b = q - (nb-1) H + b H
+        const int qq = q - (nb - 1) * H;
+        T acc = Acc::zero();
+        for (int b = 0; b < nb; ++b) {
+            const int x = qq + b * H;
+            if (x < 0) acc = Acc::zero();
+            else c2[(size_t)b * n + x] = acc;
+            const int xn = x + H;
+            if (xn >= n) break;
+            const T loc = xn >= 0 ? a2[(size_t)b * n + xn] : Acc::zero();
+            acc = Acc::add(loc, acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch: one (CPT, NT) instantiation per tile shape, N = CPT * NT
+// ---------------------------------------------------------------------------
+template <class Acc, int CPT, int NT>
+cudaError_t launch_scan_tile(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
+                             const float* dtex, int phase, cudaStream_t s) {
+    if (phase == 0 || phase == 1) k_scan_band<Acc, CPT, NT, 1><<<band.n_blocks, NT, 0, s>>>(d_jobs, band.d_map, dtex);
+    if (phase == 0 || phase == 2) k_scan_carry<Acc><<<carry.n_blocks, 256, 0, s>>>(d_jobs, carry.d_map);
+    if (phase == 0 || phase == 3) k_scan_band<Acc, CPT, NT, 3><<<band.n_blocks, NT, 0, s>>>(d_jobs, band.d_map, dtex);
+    return cudaGetLastError();
+}
+
+template <class Acc>
+cudaError_t launch_scan_acc(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
+                            ScanTile tile, const float* dtex, int phase, cudaStream_t s) {
+    const int key = tile.cpt * 10000 + tile.nt;
+    switch (key) {
+        case 2 * 10000 + 128: return launch_scan_tile<Acc, 2, 128>(d_jobs, band, carry, dtex, phase, s);
+        case 4 * 10000 + 128: return launch_scan_tile<Acc, 4, 128>(d_jobs, band, carry, dtex, phase, s);
+        case 2 * 10000 + 256: return launch_scan_tile<Acc, 2, 256>(d_jobs, band, carry, dtex, phase, s);
+        case 8 * 10000 + 128: return launch_scan_tile<Acc, 8, 128>(d_jobs, band, carry, dtex, phase, s);
+        case 4 * 10000 + 256: return launch_scan_tile<Acc, 4, 256>(d_jobs, band, carry, dtex, phase, s);
+        case 8 * 10000 + 256: return launch_scan_tile<Acc, 8, 256>(d_jobs, band, carry, dtex, phase, s);
+        case 4 * 10000 + 512: return launch_scan_tile<Acc, 4, 512>(d_jobs, band, carry, dtex, phase, s);
+        case 8 * 10000 + 512: return launch_scan_tile<Acc, 8, 512>(d_jobs, band, carry, dtex, phase, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace inim

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol the
+header declares; argument checks that need no device work on CPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "inim.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_13880_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2604_13880_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|long long|const char\*)\s+(inim_\w+)\s*\(", txt, re.M)))
+
+
+def test_header_symbols_exported(lib):
+    from paper_2604_13880_gb300 import _lib
+    names = declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(_lib.declared_symbols())
+
+
+def test_struct_layout_matches_header(tmp_path):
+    # compile a C program against the header and compare sizes/offsets with ctypes
+    from paper_2604_13880_gb300 import _lib
+    src = tmp_path / "t.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "inim.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(inim_params), sizeof(inim_step_stats),'
+                   ' sizeof(inim_job), offsetof(inim_job, params), offsetof(inim_params, form));return 0;}\n')
+    exe = tmp_path / "t"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = list(map(int, subprocess.check_output([str(exe)]).split()))
+    want = [ctypes.sizeof(_lib.inim_params), ctypes.sizeof(_lib.inim_step_stats), ctypes.sizeof(_lib.inim_job),
+            _lib.inim_job.params.offset, _lib.inim_params.form.offset]
+    assert got == want
+
+
+def test_defaults_and_status(lib):
+    import paper_2604_13880_gb300 as P
+    p = P.params()
+    assert (p.log2_res, p.max_iters, p.stall_window) == (10, 512, 32)
+    assert abs(p.xi_stop - 0.01) < 1e-9 and p.bdv_scale == 1.0
+    assert P.inim_status_string(0) == "ok"
+    assert "capacity" in P.inim_status_string(-5)
+
+
+def test_map_argument_checks(lib):
+    # these fail before any device work
+    xy = np.zeros((3, 2), np.float32)
+    off = np.array([0, 3], np.int32)
+    reg = np.zeros(1, np.int32)
+    h = ctypes.c_void_p()
+    bad_idx = np.array([0, 1, 7], np.int32)
+    assert lib.inim_map_create(xy.ctypes.data, 3, off.ctypes.data, 1, bad_idx.ctypes.data, reg.ctypes.data,
+                               1, 0, ctypes.byref(h)) == -1
+    idx = np.array([0, 1, 2], np.int32)
+    assert lib.inim_map_create(xy.ctypes.data, 3, off.ctypes.data, 1, idx.ctypes.data, reg.ctypes.data,
+                               0, 0, ctypes.byref(h)) == -1
+    bad_reg = np.array([4], np.int32)
+    assert lib.inim_map_create(xy.ctypes.data, 3, off.ctypes.data, 1, idx.ctypes.data, bad_reg.ctypes.data,
+                               2, 0, ctypes.byref(h)) == -1
+    nan = np.full((3, 2), np.nan, np.float32)
+    assert lib.inim_map_create(nan.ctypes.data, 3, off.ctypes.data, 1, idx.ctypes.data, reg.ctypes.data,
+                               1, 0, ctypes.byref(h)) == -1
+    assert b"range" in lib.inim_last_error() or b"coordinates" in lib.inim_last_error()

@@ -1,0 +1,356 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, through the
+C ABI, on seeded synthetic inputs.
+
+Tolerances (derived in the design notes):
+  labels / counts       bit-exact (integer rule)
+  FIX64 integral images bit-exact (integer sums of the quantised texture)
+  FP32 integral images  |err| <= 2 * depth * 2^-24 * C, depth = N/8 + 64
+                        (a linear bound in the number of additions on any path)
+  KAHAN integral images |err| <= 1e-10 * C
+  displacement          3e-5 (FP32 sums), 1e-6 (FIX64 / KAHAN)
+  one iteration         max |dp| <= 1e-5 of the map extent
+  N iterations          max |dp| <= 1e-4 of the map extent, areas <= 1e-4 relative
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2604_13880_gb300 as P  # noqa: E402
+from paper_2604_13880_gb300 import synth  # noqa: E402
+from oracle import inim_oracle as O  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+EXTENT = 0.9
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def arrays(mesh):
+    return (mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
+
+
+def gpu_raster(m, xy32, k):
+    N = 1 << k
+    lab = torch.empty((N, N), dtype=torch.int16, device="cuda")
+    cnt = torch.empty(m.n_regions + 1, dtype=torch.int32, device="cuda")
+    ov = P.inim_raster(m, dev(xy32), k, lab, cnt)
+    return lab.cpu().numpy().view(np.uint16).astype(np.int64), cnt.cpu().numpy(), ov
+
+
+def oracle_raster(mesh, xy32, k):
+    lab, cnt, ov = O.labels_scanline(xy32.astype(np.float64), *arrays(mesh), k)
+    lab = np.where(lab < 0, mesh.n_regions, lab)
+    return lab, cnt, ov
+
+
+# ---------------------------------------------------------------------------
+# A1: rasterisation, bit-exact
+# ---------------------------------------------------------------------------
+def _raster_cases():
+    yield "voronoi32", synth.voronoi_map(32, 2000, seed=1), 8
+    yield "voronoi60_jitter", synth.voronoi_map(60, 3000, seed=7, jitter=0.3), 9
+    yield "voronoi200_jitter", synth.voronoi_map(200, 50_000, seed=2, jitter=0.3), 10
+    m = synth.voronoi_map(25, 1500, seed=11)
+    m = m.with_verts((np.floor(m.verts * 256) + 0.5) / 256)      # vertices on pixel centres
+    yield "on_centres", m, 8
+    yield "overlap", synth.square_map([(0.2, 0.2, 0.6, 0.6), (0.4, 0.4, 0.8, 0.8)]), 8
+    outer = [(0.1, 0.1), (0.1, 0.9), (0.9, 0.9), (0.9, 0.1)]
+    inner = [(0.3, 0.3), (0.3, 0.7), (0.7, 0.7), (0.7, 0.3)]
+    yield "hole", synth.Mesh(np.array(outer + inner, np.float64), np.array([0, 4, 8], np.int32),
+                             np.arange(8, dtype=np.int32), np.array([0, 0], np.int32), 1), 8
+
+
+@pytest.mark.parametrize("name,mesh,k", list(_raster_cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_raster_bit_exact(name, mesh, k):
+    m = P.inim_map_create(mesh)
+    xy = mesh.verts_f32()
+    lab, cnt, ov = gpu_raster(m, xy, k)
+    olab, ocnt, oov = oracle_raster(mesh, xy, k)
+    np.testing.assert_array_equal(lab, olab)
+    np.testing.assert_array_equal(cnt[:-1], ocnt)
+    assert cnt[-1] == (1 << (2 * k)) - ocnt.sum()
+    assert bool(ov) == oov
+
+
+def test_raster_bit_exact_4096():
+    w = synth.precision_workload()
+    mesh = w["mesh"]
+    m = P.inim_map_create(mesh)
+    xy = mesh.verts_f32()
+    lab, cnt, ov = gpu_raster(m, xy, 12)
+    olab, ocnt, oov = oracle_raster(mesh, xy, 12)
+    np.testing.assert_array_equal(lab, olab)
+    np.testing.assert_array_equal(cnt[:-1], ocnt)
+    assert not ov and not oov
+
+
+# ---------------------------------------------------------------------------
+# A3: integral images on given textures
+# ---------------------------------------------------------------------------
+def gpu_inims(d32, k, precision, frac_bits=30):
+    N = 1 << k
+    dt = torch.float32 if precision == P.INIM_FP32 else (torch.int64 if precision == P.INIM_FIX64 else torch.float64)
+    # KAHAN elements are float pairs (hi, lo): allocate as float32 [.., 2]
+    if precision == P.INIM_KAHAN:
+        S = torch.empty((N, N, 2), dtype=torch.float32, device="cuda")
+        T = torch.empty((N, N, 2), dtype=torch.float32, device="cuda")
+        A = torch.empty((2 * N - 1, 2), dtype=torch.float32, device="cuda")
+        B = torch.empty((2 * N - 1, 2), dtype=torch.float32, device="cuda")
+    else:
+        S = torch.empty((N, N), dtype=dt, device="cuda")
+        T = torch.empty((N, N), dtype=dt, device="cuda")
+        A = torch.empty(2 * N - 1, dtype=dt, device="cuda")
+        B = torch.empty(2 * N - 1, dtype=dt, device="cuda")
+    P.inim_inims(dev(d32), k, precision, frac_bits, S, T, A, B)
+    torch.cuda.synchronize()
+    out = [x.cpu().numpy() for x in (S, T, A, B)]
+    if precision == P.INIM_KAHAN:
+        out = [x[..., 0].astype(np.float64) + x[..., 1].astype(np.float64) for x in out]
+    return out
+
+
+def texture(k, seed, sigma=1.0):
+    N = 1 << k
+    rng = np.random.default_rng(seed)
+    return rng.lognormal(0.0, sigma, (N, N)).astype(np.float32)
+
+
+@pytest.mark.parametrize("k", [8, 9, 10, 11])
+def test_inims_fp32(k):
+    d = texture(k, 100 + k)
+    S, T, A, B = gpu_inims(d, k, P.INIM_FP32)
+    I = O.inims(d.astype(np.float64))
+    N = 1 << k
+    tol = 2 * (N / 8 + 64) * 2.0 ** -24 * I["C"]
+    for g, o, nm in ((S, I["a"], "S"), (T, I["at"], "T"), (A, I["A"], "A"), (B, I["B"], "B")):
+        err = np.abs(g.astype(np.float64) - o).max()
+        assert err <= tol, (nm, err / I["C"])
+
+
+@pytest.mark.parametrize("k", [8, 10, 12])
+def test_inims_fix64_bit_exact(k):
+    d = texture(k, 200 + k)
+    fb = 30
+    q = np.rint(d.astype(np.float64) * 2.0 ** fb).astype(np.int64)
+    S, T, A, B = gpu_inims(d, k, P.INIM_FIX64, fb)
+    I = O.inims(q)
+    np.testing.assert_array_equal(S, I["a"])
+    np.testing.assert_array_equal(T, I["at"])
+    np.testing.assert_array_equal(A, I["A"])
+    np.testing.assert_array_equal(B, I["B"])
+
+
+@pytest.mark.parametrize("k", [8, 10])
+def test_inims_kahan(k):
+    d = texture(k, 300 + k, sigma=2.0)
+    S, T, A, B = gpu_inims(d, k, P.INIM_KAHAN)
+    I = O.inims(d.astype(np.float64))
+    tol = 1e-10 * I["C"]
+    for g, o, nm in ((S, I["a"], "S"), (T, I["at"], "T"), (A, I["A"], "A"), (B, I["B"], "B")):
+        assert np.abs(g - o).max() <= tol, nm
+
+
+# ---------------------------------------------------------------------------
+# A4: Eq. (3) displacement at points; identity at constant density
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tol", [(P.INIM_FP32, 3e-5), (P.INIM_FIX64, 1e-6), (P.INIM_KAHAN, 1e-6)])
+def test_displacement(precision, tol):
+    k = 8
+    d = texture(k, 7)
+    pts = np.random.default_rng(8).uniform(0.01, 0.99, (5000, 2)).astype(np.float32)
+    out = torch.empty((len(pts), 2), dtype=torch.float32, device="cuda")
+    P.inim_displacement(dev(d), k, precision, dev(pts), out)
+    torch.cuda.synchronize()
+    fx, fy = O.displacement_field(d.astype(np.float64))
+    want = np.stack([O.bilinear(fx, pts), O.bilinear(fy, pts)], 1)
+    assert np.abs(out.cpu().numpy() - want).max() <= tol
+
+
+@pytest.mark.parametrize("precision", [P.INIM_FP32, P.INIM_FIX64, P.INIM_KAHAN])
+def test_identity_at_constant_density(precision):
+    k = 9
+    N = 1 << k
+    pts = np.random.default_rng(9).uniform(0.0, 1.0, (4000, 2)).astype(np.float32)
+    out = torch.empty((len(pts), 2), dtype=torch.float32, device="cuda")
+    P.inim_displacement(dev(np.ones((N, N), np.float32)), k, precision, dev(pts), out)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy()).max() == 0.0
+    P.inim_displacement(dev(np.full((N, N), 3.7, np.float32)), k, precision, dev(pts), out)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy()).max() <= 1e-6
+
+
+def test_identity_mapping_iteration():
+    mesh = synth.voronoi_map(20, 800, seed=21)
+    k = 8
+    xy = mesh.verts_f32()
+    _, cnt, _ = O.labels_scanline(xy.astype(np.float64), *arrays(mesh), k)
+    vals = (2.5 * cnt).astype(np.float32)
+    m = P.inim_map_create(mesh)
+    x = dev(xy)
+    st, _ = P.inim_iterate(m, x, dev(vals), P.params(log2_res=k, shape=0.0), 5)
+    assert np.abs(x.cpu().numpy() - xy).max() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# A5 / A6: one iteration, trajectories, areas, errors
+# ---------------------------------------------------------------------------
+def test_areas():
+    mesh = synth.voronoi_map(50, 4000, seed=5, jitter=0.3)
+    m = P.inim_map_create(mesh)
+    xy = mesh.verts_f32()
+    a = torch.empty(mesh.n_regions, dtype=torch.float64, device="cuda")
+    P.inim_areas(m, dev(xy), a)
+    want = O.signed_areas(xy.astype(np.float64), *arrays(mesh))
+    np.testing.assert_allclose(a.cpu().numpy(), want, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [0.25, 0.5, 0.75])
+def test_one_iteration(shape):
+    w = synth.single_step_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    xy = mesh.verts_f32()
+    x = dev(xy)
+    P.inim_iterate(m, x, dev(vals), P.params(log2_res=k, shape=shape), 1)
+    want, _ = O.iterate(xy.astype(np.float64), arrays(mesh), vals.astype(np.float64), k, shape)
+    assert np.abs(x.cpu().numpy() - want).max() <= 1e-5 * EXTENT
+
+
+def test_one_iteration_config_timevarying():
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    xy = mesh.verts_f32()
+    x = dev(xy)
+    P.inim_iterate(m, x, dev(vals), P.params(log2_res=k, shape=0.5), 1)
+    want, _ = O.iterate(xy.astype(np.float64), arrays(mesh), vals.astype(np.float64), k, 0.5)
+    assert np.abs(x.cpu().numpy() - want).max() <= 1e-5 * EXTENT
+
+
+def test_trajectory_single_step_config():
+    """20 iterations, shape 0.5 (the single-step workload): vertices, areas,
+    and bit-exact labels of the GPU's own vertices at every iteration."""
+    w = synth.single_step_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    xy0 = mesh.verts_f32()
+    x = dev(xy0)
+    ora = xy0.astype(np.float64)
+    t0 = O.transform_uniform(1 << k)
+    p = P.params(log2_res=k, shape=0.5)
+    for it in range(w["iters"]):
+        g = x.cpu().numpy()
+        lab, cnt, _ = gpu_raster(m, g, k)
+        olab, ocnt, _ = oracle_raster(mesh, g, k)
+        np.testing.assert_array_equal(lab, olab)
+        P.inim_iterate(m, x, dev(vals), p, 1)
+        ora, _ = O.iterate(ora, arrays(mesh), vals.astype(np.float64), k, 0.5, t0=t0)
+    g = x.cpu().numpy()
+    assert np.abs(g - ora).max() <= 1e-4 * EXTENT
+    ga = O.signed_areas(g.astype(np.float64), *arrays(mesh))
+    oa = O.signed_areas(ora, *arrays(mesh))
+    assert (np.abs(ga - oa) / np.abs(oa)).max() <= 1e-4
+
+
+@pytest.mark.parametrize("precision", [P.INIM_FIX64, P.INIM_KAHAN])
+def test_precision_variants_trajectory(precision):
+    w = synth.single_step_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    x = dev(mesh.verts_f32())
+    P.inim_iterate(m, x, dev(vals), P.params(log2_res=k, shape=0.5, precision=precision), 20)
+    ora, _ = O.run(mesh.with_verts(mesh.verts_f32().astype(np.float64)), vals[None].astype(np.float64), k,
+                   shape=0.5, max_iters=20, xi_stop=0, stall_window=0)
+    assert np.abs(x.cpu().numpy() - ora[0]).max() <= 1e-4 * EXTENT
+
+
+def test_plain_form_matches_fused():
+    w = synth.single_step_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    a = dev(mesh.verts_f32())
+    b = dev(mesh.verts_f32())
+    P.inim_iterate(m, a, dev(vals), P.params(log2_res=k, shape=0.5), 10)
+    P.inim_iterate(m, b, dev(vals), P.params(log2_res=k, shape=0.5, form=P.INIM_FORM_PLAIN), 10)
+    assert (a - b).abs().max().item() <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# A7 / A8: time loop (direct, cumulative), batches, the stop rule
+# ---------------------------------------------------------------------------
+def test_direct_steps_are_independent_solves():
+    mesh = synth.voronoi_map(30, 1500, seed=31)
+    vals = synth.random_walk_values(30, 3, seed=32).astype(np.float32)
+    m = P.inim_map_create(mesh)
+    p = P.params(log2_res=8, shape=0.5, max_iters=12, xi_stop=0.0, stall_window=0)
+    out, stats, _ = P.inim_run(m, vals, p)
+    for t in range(3):
+        one, _, _ = P.inim_run(m, vals[t:t + 1], p)
+        np.testing.assert_array_equal(out[t], one[0])
+        assert stats[t]["iters"] == 12
+
+
+def test_cumulative_matches_oracle():
+    mesh = synth.voronoi_map(30, 1500, seed=33)
+    vals = synth.random_walk_values(30, 3, seed=34).astype(np.float32)
+    m = P.inim_map_create(mesh)
+    p = P.params(log2_res=8, shape=0.25, max_iters=6, xi_stop=0.0, stall_window=0, mode=P.INIM_CUMULATIVE)
+    out, stats, _ = P.inim_run(m, vals, p)
+    ora, _ = O.run(mesh.with_verts(mesh.verts_f32().astype(np.float64)), vals.astype(np.float64), 8,
+                   shape=0.25, max_iters=6, xi_stop=0, stall_window=0, mode="cumulative")
+    assert np.abs(out - ora).max() <= 1e-4 * EXTENT
+    d, _, _ = P.inim_run(m, vals[:1], P.params(log2_res=8, shape=0.25, max_iters=6, xi_stop=0.0, stall_window=0))
+    np.testing.assert_array_equal(out[0], d[0])
+
+
+def test_batch_mixed_resolutions_equals_single_runs():
+    meshes = [synth.voronoi_map(20 + 10 * b, 1000 + 500 * b, seed=40 + b) for b in range(4)]
+    ks = [8, 9, 10, 8]
+    maps = [P.inim_map_create(mm) for mm in meshes]
+    jobs = []
+    for b, mm in enumerate(meshes):
+        vals = synth.lognormal_values(mm.n_regions, seed=50 + b).astype(np.float32)
+        jobs.append(dict(map=maps[b], values=vals,
+                         params=P.params(log2_res=ks[b], shape=0.5, max_iters=10 + 3 * b, xi_stop=0.0,
+                                         stall_window=0)))
+    outs, stats, _ = P.inim_run_batch(jobs)
+    for b, j in enumerate(jobs):
+        one, st, _ = P.inim_run(j["map"], j["values"][None], j["params"])
+        np.testing.assert_array_equal(outs[b], one[0])
+        assert stats[b]["iters"] == 10 + 3 * b
+
+
+def test_stop_rule_reports_consistent_errors():
+    w = synth.single_step_workload()
+    mesh = w["mesh"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    out, stats, status = P.inim_run(m, vals[None], P.params(log2_res=8, shape=0.0))
+    s = stats[0]
+    assert 1 <= s["iters"] <= 512
+    assert s["iters"] == 512 or s["xi"] < 0.01 or s["iters"] >= 33
+    # the reported errors are the errors of the returned vertices
+    g = out[0].astype(np.float64)
+    _, cnt, _ = O.labels_scanline(g, *arrays(mesh), 8)
+    areas = O.signed_areas(g, *arrays(mesh))
+    d0 = vals[cnt > 0].astype(np.float64).sum() / cnt.sum()
+    desired = O.desired_areas(vals.astype(np.float64), cnt, d0, 256)
+    eps, xi = O.cartographic_errors(areas, desired)
+    assert abs(eps - s["eps"]) <= 2e-3 and abs(xi - s["xi"]) <= 5e-3
+    assert s["foldover"] == 0 and s["overlap"] == 0
