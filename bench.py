@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the InIm cartogram iteration on one GB300 (or N replicas).
+
+Workload (the time-varying configuration): 200 jittered Voronoi regions,
+~50k vertices, 1024^2 texture, 24 time steps of log-normal random-walk values,
+50 iterations per step, shape parameter swept over {0.25, 0.5, 0.75}, in
+direct mode (72 independent solves, one batch) and cumulative mode (3 shape
+series, 24 rounds of a 3-solve batch).  One step = that whole sweep =
+2 * 3 * 24 * 50 = 7200 InIm iterations.
+
+Printed (one JSON line, rank 0): iterations/s with inputs resident in HBM,
+the same through host (pinned) buffers (e2e), the dominant kernel's roofline
+from CUDA events on the library's stream, SM clocks sampled during the timed
+region, the CPU oracle on a bounded sample (cpu_baseline), the plain
+unfused GPU form on a bounded sample, and time-to-epsilon plain vs fused.
+
+--impl reference times the CPU oracle (the reference arm of this build) on
+the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPES = (0.25, 0.5, 0.75)
+ITERS = 50
+T_STEPS = 24
+ITERS_PER_STEP = 2 * len(SHAPES) * T_STEPS * ITERS
+METRIC = "InIm iterations/s"
+WORKLOAD = "voronoi200_v50k_res1024_T24_it50_shapes3_direct+cumulative"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import inim_oracle as O
+    from paper_2604_13880_gb300 import synth
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    arrays = (mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
+    t0 = O.transform_uniform(1 << w["log2_res"])
+    xy = mesh.verts_f32().astype(np.float64)
+    per_step = 2
+
+    def step():
+        nonlocal xy
+        for _ in range(per_step):
+            xy, _ = O.iterate(xy, arrays, w["values"][0], w["log2_res"], 0.5, t0=t0)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    value = args.steps * per_step / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{per_step} oracle iterations per step (shape 0.5, t=0)"},
+            "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} iterations of the 1024^2 map per step"},
+            "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip plain form, time-to-eps and CPU baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import _lib, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    V, R = mesh.n_verts, mesh.n_regions
+    vals = w["values"].astype(np.float32)                     # [24, 200]
+    m = P.inim_map_create(mesh)
+
+    def prm(shape, **kw):
+        return P.params(log2_res=k, shape=shape, max_iters=ITERS, xi_stop=0.0, stall_window=0, **kw)
+
+    def job_array(entries):
+        arr = (P.inim_job * len(entries))()
+        for q, (vp, ip, op, p) in enumerate(entries):
+            arr[q].map = m.handle
+            arr[q].values = vp
+            arr[q].init_xy = ip
+            arr[q].out_xy = op
+            arr[q].params = p
+            arr[q].stats = None
+        return arr
+
+    def make_plan(vals_buf, out_direct, out_cum, stride):
+        """ctypes job arrays of one step over the given buffers (device or pinned host)."""
+        vp = lambda t: vals_buf.data_ptr() + t * R * 4                    # noqa: E731
+        op = lambda buf, q: buf.data_ptr() + q * V * 2 * 4                 # noqa: E731
+        direct = job_array([(vp(t), None, op(out_direct, s * T_STEPS + t), prm(sh))
+                            for s, sh in enumerate(SHAPES) for t in range(T_STEPS)])
+        rounds = []
+        for t in range(T_STEPS):
+            rounds.append(job_array([(vp(t), None if t == 0 else op(out_cum, s * T_STEPS + t - 1),
+                                      op(out_cum, s * T_STEPS + t), prm(sh)) for s, sh in enumerate(SHAPES)]))
+        return direct, rounds
+
+    def run_step(plan):
+        direct, rounds = plan
+        _lib.check(lib.inim_run_batch(direct, len(direct), None), "direct batch")
+        for r in rounds:
+            _lib.check(lib.inim_run_batch(r, len(r), None), "cumulative round")
+
+    # device-resident inputs and outputs
+    vals_d = torch.as_tensor(vals, device=dev).contiguous()
+    out_dir_d = torch.empty((len(SHAPES) * T_STEPS, V, 2), device=dev)
+    out_cum_d = torch.empty((len(SHAPES) * T_STEPS, V, 2), device=dev)
+    plan_d = make_plan(vals_d, out_dir_d, out_cum_d, None)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        run_step(plan_d)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    barrier()
+    clocks = ClockSampler(uuid) if rank == 0 else None
+    launches0 = P.inim_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        run_step(plan_d)
+    ev1.record()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    ms = ev0.elapsed_time(ev1)
+    launches = P.inim_launch_count() - launches0
+    clk = clocks.stop() if clocks else None
+    ms_t = torch.tensor([ms], device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    total_iters = ITERS_PER_STEP * args.steps * world
+    value = total_iters / (ms_max / 1e3)
+
+    # e2e: the same sweep through the public API with pinned host buffers
+    vals_h = torch.as_tensor(vals).pin_memory()
+    out_dir_h = torch.empty((len(SHAPES) * T_STEPS, V, 2)).pin_memory()
+    out_cum_h = torch.empty((len(SHAPES) * T_STEPS, V, 2)).pin_memory()
+    plan_h = make_plan(vals_h, out_dir_h, out_cum_h, None)
+    run_step(plan_h)
+    barrier()
+    e_steps = max(1, min(args.steps, 3))
+    t = time.perf_counter()
+    for _ in range(e_steps):
+        run_step(plan_h)
+    barrier()
+    e2e_s = time.perf_counter() - t
+    e2e_t = torch.tensor([e2e_s], device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ITERS_PER_STEP * e_steps * world / float(e2e_t.item())
+    n_sol = 2 * len(SHAPES) * T_STEPS
+    h2d = n_sol * R * 4 + len(SHAPES) * (T_STEPS - 1) * V * 8
+    d2h = n_sol * V * 8
+
+    line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "texture": "1024x1024", "regions": R, "vertices": V,
+                       "iterations_per_step": ITERS_PER_STEP,
+                       "l2": "inputs larger than L2 (72 solves x ~13 MB of textures per batched iteration)",
+                       "parallelism": f"replicas{world}"},
+            "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "host_buffers": "pinned"},
+            "gpu_launches": int(launches), "wall_s_timed": wall}
+    if clk:
+        line["clocks"] = clk
+
+    if rank == 0:
+        # roofline of the dominant stage, measured on the 72-solve batch
+        run_step(plan_d)
+        _lib.check(lib.inim_run_batch(plan_d[0], len(plan_d[0]), None), "direct batch")
+        stages = P.inim_profile_stages(reps=10)
+        N = 1 << k
+        Ppx = N * N
+        nb = N // 16
+        n_jobs = len(SHAPES) * T_STEPS
+        E = int(P.inim_map_info(m)["n_edges"])
+        algo = {   # algorithmic bytes per launch over the whole batch (design notes)
+            "raster": n_jobs * (2 * Ppx + 2 * 8 * E),
+            "density_table": n_jobs * (12 * R),
+            "scan_phase1": n_jobs * (2 * Ppx + 3 * nb * N * 4),
+            "scan_carry": n_jobs * (2 * 3 * nb * N * 4),
+            "scan_phase3": n_jobs * (2 * Ppx + 8 * Ppx + 3 * nb * N * 4),
+            "gather_move": n_jobs * 48 * V,
+            "areas_errors": n_jobs * 16 * E,
+        }
+        dom = max(stages, key=stages.get)
+        pk = peaks()
+        achieved = algo[dom] / (stages[dom] / 1e3) / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"],
+                            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                            "algorithmic_bytes_per_launch": algo[dom], "launch_ms": stages[dom],
+                            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "fallback" not in pk
+                            else "fallback"}
+        line["stages_ms"] = stages
+        line["stages_gbs"] = {s: algo[s] / (stages[s] / 1e3) / 1e9 for s in stages}
+
+    if rank == 0 and not args.no_extras:
+        # plain unfused form on a bounded sample: 2 time steps x 3 shapes, direct
+        tp = time.perf_counter()
+        for sh in SHAPES:
+            P.inim_run(m, vals[:2], prm(sh, form=P.INIM_FORM_PLAIN))
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - tp
+        plain_value = 2 * len(SHAPES) * ITERS / plain_s
+        line["plain_form"] = {"value": plain_value, "unit": "iterations/s",
+                              "sample": "3 shapes x 2 time steps x 50 iterations, one solve at a time",
+                              "fused_over_plain": value / world / plain_value}
+        # time to cartographic error eps (one solve, shape 0.5, time step 0)
+        eps_target = 0.02
+        tte = {"eps_target": eps_target}
+        for form, name in ((P.INIM_FORM_PLAIN, "plain"), (P.INIM_FORM_FUSED, "fused")):
+            p = P.params(log2_res=k, shape=0.5, max_iters=512, xi_stop=0.0, stall_window=0, eps_stop=eps_target,
+                         form=form)
+            P.inim_run(m, vals[:1], p)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, st, _ = P.inim_run(m, vals[:1], p)
+            torch.cuda.synchronize()
+            tte[f"{name}_ms"] = 1e3 * (time.perf_counter() - t)
+            tte[f"{name}_iters"] = st[0]["iters"]
+            tte[f"{name}_eps"] = st[0]["eps"]
+        # all 24 time steps of shape 0.5 to eps, batched (direct) vs one at a time (plain)
+        p = P.params(log2_res=k, shape=0.5, max_iters=512, xi_stop=0.0, stall_window=0, eps_stop=eps_target)
+        P.inim_run(m, vals, p)
+        t = time.perf_counter()
+        _, st, _ = P.inim_run(m, vals, p)
+        tte["fused_batched_24_steps_ms"] = 1e3 * (time.perf_counter() - t)
+        tte["fused_batched_24_steps_iters"] = int(sum(s["iters"] for s in st))
+        line["time_to_eps"] = tte
+        # CPU oracle on a bounded sample (this host's cores)
+        from oracle import inim_oracle as O
+        arrays = (mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
+        t0 = O.transform_uniform(1 << k)
+        xy = mesh.verts_f32().astype(np.float64)
+        n_cpu = 0
+        t = time.perf_counter()
+        while n_cpu < 40 and (n_cpu < 3 or time.perf_counter() - t < 15.0):
+            xy, _ = O.iterate(xy, arrays, w["values"][0], k, 0.5, t0=t0)
+            n_cpu += 1
+        cpu_s = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": n_cpu / cpu_s, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n_cpu} oracle iterations of the 1024^2 map (shape 0.5, t=0), "
+                                          f"{cpu_s:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
