@@ -225,6 +225,29 @@ int inim_iterate(const inim_map* map, float* xy, const float* values,
  */
 int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream);
 
+/*
+ * Allocation-free FP32 integral images (the paper has no counterpart; this is
+ * a service of this library).  Same inputs, outputs and meaning as
+ * inim_inims with precision INIM_FP32, for callers that cannot allocate
+ * device memory: code running under another framework's memory manager that
+ * owns the whole device pool, or a latency-critical loop in which cudaMalloc /
+ * cudaFree (which can synchronise the device) are not acceptable.
+ *   density [N*N], S [N*N], T [N*N], A [2N-1], B [2N-1]: device float,
+ *   all provided by the caller.  Work is enqueued on `stream`; the call does
+ *   not wait for it.
+ * The working memory (band aggregates, carries, job descriptor, block tables)
+ * is one fixed array inside the library, about 1.6 MB, held by every GPU that
+ * loads the library until the process exits.  Limit: log2_res <= 10
+ * (N <= 1024); larger textures return INIM_E_CAPACITY.  Every call reuses the
+ * same array, so calls whose kernels overlap on the GPU (e.g. on two
+ * unordered streams) race.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current): make that
+ * first call before any stream capture.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.
+ */
+int inim_inims_noalloc(const float* density, int32_t log2_res, float* S, float* T,
+                       float* A, float* B, void* stream);
+
 /* ---------------- profiling ------------------------------------------- */
 
 /*

@@ -164,6 +164,19 @@ def inim_inims(density, log2_res: int, precision: int, frac_bits: int, S, T, A, 
                "inim_inims")
 
 
+def inim_inims_noalloc(density, log2_res: int, S, T, A, B, stream=None) -> None:
+    """FP32 integral images without any device allocation (N <= 1024).
+
+    For callers that cannot allocate device memory (another framework owns
+    the device pool, or a loop that cannot afford cudaMalloc's
+    synchronisation); the library keeps its working memory in a fixed array.
+    Calls that overlap on the GPU share that array and race.
+    """
+    _lib.check(_lib.load().inim_inims_noalloc(_lib.ptr(density), log2_res, _lib.ptr(S), _lib.ptr(T), _lib.ptr(A),
+                                              _lib.ptr(B), stream or _lib.stream_of(density)),
+               "inim_inims_noalloc")
+
+
 def inim_displacement(density, log2_res: int, precision: int, xy, delta, stream=None) -> None:
     n = int(xy.shape[0])
     _lib.check(_lib.load().inim_displacement(_lib.ptr(density), log2_res, precision, _lib.ptr(xy), n,

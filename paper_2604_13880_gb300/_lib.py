@@ -89,6 +89,8 @@ _SIGS = {
     "inim_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(inim_params),
                                     ctypes.c_int32, ctypes.POINTER(inim_step_stats), ctypes.c_void_p]),
     "inim_areas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "inim_inims_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "inim_profile_stages": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]),
     "inim_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
