@@ -201,6 +201,11 @@ def main():
     out_cum_d = torch.empty((len(SHAPES) * T_STEPS, V, 2), device=dev)
     plan_d = make_plan(vals_d, out_dir_d, out_cum_d, None)
 
+    # scan tiles chosen by the autotuner on the two batch shapes of the step
+    P.inim_autotune_scan(plan_d[0], reps=5)
+    P.inim_autotune_scan(plan_d[1][0], reps=20)
+    tiles = {cls: P.inim_get_scan_tile(k, P.INIM_FP32, large) for cls, large in (("large", 1), ("small", 0))}
+
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
@@ -263,7 +268,7 @@ def main():
             "config": {"workload": WORKLOAD, "texture": "1024x1024", "regions": R, "vertices": V,
                        "iterations_per_step": ITERS_PER_STEP,
                        "l2": "inputs larger than L2 (72 solves x ~13 MB of textures per batched iteration)",
-                       "parallelism": f"replicas{world}"},
+                       "parallelism": f"replicas{world}", "scan_tiles_autotuned": tiles},
             "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "host_buffers": "pinned"},
             "gpu_launches": int(launches), "wall_s_timed": wall}
@@ -299,6 +304,9 @@ def main():
                             else "fallback"}
         line["stages_ms"] = stages
         line["stages_gbs"] = {s: algo[s] / (stages[s] / 1e3) / 1e9 for s in stages}
+        # the same stages on a 3-solve cumulative round (latency-bound sizes)
+        _lib.check(lib.inim_run_batch(plan_d[1][1], len(plan_d[1][1]), None), "cumulative round")
+        line["stages_3solve_ms"] = P.inim_profile_stages(reps=20)
 
     if rank == 0 and not args.no_extras:
         # plain unfused form on a bounded sample: 2 time steps x 3 shapes, direct

@@ -208,3 +208,21 @@ def inim_profile_stages(reps: int = 20):
 
 def inim_launch_count() -> int:
     return int(_lib.load().inim_launch_count())
+
+
+def inim_set_scan_tile(log2_res: int, precision: int, large: int, band_rows: int, cols_per_thread: int,
+                       threads: int) -> None:
+    _lib.check(_lib.load().inim_set_scan_tile(log2_res, precision, large, band_rows, cols_per_thread, threads),
+               "inim_set_scan_tile")
+
+
+def inim_get_scan_tile(log2_res: int, precision: int = 0, large: int = 1):
+    v = [ctypes.c_int32() for _ in range(3)]
+    _lib.check(_lib.load().inim_get_scan_tile(log2_res, precision, large, *[ctypes.byref(x) for x in v]),
+               "inim_get_scan_tile")
+    return dict(band_rows=v[0].value, cols_per_thread=v[1].value, threads=v[2].value)
+
+
+def inim_autotune_scan(job_array, reps: int = 5) -> None:
+    """job_array: a ctypes (inim_job * n) array (see inim_run_batch)."""
+    _lib.check(_lib.load().inim_autotune_scan(job_array, len(job_array), reps), "inim_autotune_scan")

@@ -91,6 +91,9 @@ _SIGS = {
     "inim_areas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "inim_inims_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "inim_set_scan_tile": (ctypes.c_int, [ctypes.c_int32] * 6),
+    "inim_get_scan_tile": (ctypes.c_int, [ctypes.c_int32] * 3 + [ctypes.POINTER(ctypes.c_int32)] * 3),
+    "inim_autotune_scan": (ctypes.c_int, [ctypes.POINTER(inim_job), ctypes.c_int32, ctypes.c_int32]),
     "inim_profile_stages": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]),
     "inim_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),

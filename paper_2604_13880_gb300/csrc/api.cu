@@ -12,7 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "inim_internal.cuh"
+#include "scan_impl.cuh"
 
 using namespace inim;
 
@@ -57,6 +57,7 @@ struct inim_map {
     int n_verts = 0, n_regions = 0, n_rings = 0, n_edges = 0;
     int2* edges = nullptr;
     int* edge_region = nullptr;
+    int* reg_edge_off = nullptr;
     int* reg_ring_off = nullptr;
     int* reg_rings = nullptr;
     int* ring_off = nullptr;
@@ -74,11 +75,14 @@ namespace {
 // ---------------------------------------------------------------------------
 size_t elem_size(int precision) { return precision == INIM_FP32 ? 4 : 8; }
 
+constexpr int kRowsPerBlock = 8;     // rows of one k_raster_rows block (one warp each)
+
 struct Buffers {
     int n = 0, precision = 0, R = 0, key_cap = 0, nb = 0, V = 0;
     uint16_t* labels = nullptr;
     int* row_cnt = nullptr;
     int* row_off = nullptr;
+    int* big_rows = nullptr;
     uint32_t* keys = nullptr;
     int* counts = nullptr;
     float* dens = nullptr;
@@ -93,7 +97,7 @@ struct Buffers {
     double* areas = nullptr;
     float2* xy = nullptr;
 
-    cudaError_t alloc(int n_, int prec, int R_, int V_, int key_cap_, int nb_) {
+    cudaError_t alloc(int n_, int prec, int R_, int V_, int key_cap_, int nb_, bool interleaved) {
         n = n_; precision = prec; R = R_; V = V_; key_cap = key_cap_; nb = nb_;
         const size_t np = (size_t)n * n, es = elem_size(prec);
         cudaError_t e = cudaSuccess;
@@ -101,12 +105,14 @@ struct Buffers {
         A_((void**)&labels, np * 2);
         A_((void**)&row_cnt, (size_t)n * 4);
         A_((void**)&row_off, (size_t)(n + 1) * 4);
+        A_((void**)&big_rows, (size_t)n * 4);
         A_((void**)&keys, (size_t)key_cap * 4);
         A_((void**)&counts, (size_t)(R + 1) * 4);
         A_((void**)&dens, (size_t)(R + 1) * 4);
         A_((void**)&values, (size_t)R * 4);
-        A_(&S, np * es);
-        A_(&T, np * es);
+        // map jobs store interleaved (S, T) pairs in S; texture jobs S and T apart
+        A_(&S, (interleaved ? 2 : 1) * np * es);
+        A_(&T, interleaved ? 16 : np * es);
         A_(&A, (size_t)(2 * n) * es);
         A_(&B, (size_t)(2 * n) * es);
         A_(&rowcum, (size_t)n * es);
@@ -118,14 +124,20 @@ struct Buffers {
         return e;
     }
     void release() {
-        dfree(labels); dfree(row_cnt); dfree(row_off); dfree(keys); dfree(counts); dfree(dens);
+        dfree(labels); dfree(row_cnt); dfree(row_off); dfree(big_rows); dfree(keys); dfree(counts); dfree(dens);
         dfree(values); dfree(S); dfree(T); dfree(A); dfree(B); dfree(rowcum); dfree(agg);
         dfree(carry); dfree(areas); dfree(xy);
     }
 };
 
-// default scan tiles per resolution (band height, columns per thread, threads)
-ScanTile g_tiles[kMaxLog2 + 1] = {};
+// scan tiles per (precision, resolution): band height, columns per thread,
+// threads.  Defaults below; inim_set_scan_tile / inim_autotune_scan override.
+// Separate entries for small and large groups (total pixels of the group's
+// jobs below / at least 2^23): small batches are latency-bound, large ones
+// bandwidth-bound, and they prefer different tiles.
+ScanTile g_tiles[3][2][kMaxLog2 + 1] = {};
+
+int size_class(long long group_pixels) { return group_pixels >= (1LL << 23) ? 1 : 0; }
 
 ScanTile default_tile(int log2n) {
     switch (log2n) {
@@ -137,10 +149,23 @@ ScanTile default_tile(int log2n) {
     }
 }
 
-ScanTile tile_for(int log2n) {
-    ScanTile t = g_tiles[log2n];
+ScanTile tile_for(int log2n, int precision, int cls) {
+    ScanTile t = g_tiles[precision][cls][log2n];
     if (t.H <= 0) t = default_tile(log2n);
     return t;
+}
+
+// (columns per thread, threads) pairs with a compiled band-scan kernel
+constexpr int kTilePairs[][2] = {{2, 128}, {4, 128}, {2, 256}, {8, 128}, {4, 256}, {8, 256}, {4, 512}, {8, 512}};
+constexpr int kTileHeights[] = {4, 8, 16, 32, 64};
+
+bool tile_valid(int log2n, ScanTile t) {
+    const int n = 1 << log2n;
+    bool pair = false;
+    for (auto& q : kTilePairs) pair |= (q[0] == t.cpt && q[1] == t.nt);
+    bool h = false;
+    for (int x : kTileHeights) h |= (x == t.H);
+    return pair && h && t.cpt * t.nt == n && t.H * 4 <= n;
 }
 
 int estimate_key_cap(const inim_map* m, const float* xy_host, int n) {
@@ -184,6 +209,7 @@ struct Batch {
     BlockMap edge_blocks, job_blocks, row_blocks, vert_blocks, region_blocks;
     std::vector<Group> groups;
     int precision = INIM_FP32;
+    int max_n = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -211,7 +237,8 @@ cudaError_t make_map(BlockMap& bm, const std::vector<int2>& entries) {
     return e;
 }
 
-int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<const float*>& start_xy_host) {
+int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<const float*>& start_xy_host,
+                int min_H = 0) {
     B.spec = spec;
     const int nj = (int)spec.size();
     B.precision = spec[0].precision;
@@ -222,27 +249,34 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
     B.h_jobs.resize(nj);
     B.h_states.assign(nj, JobState{});
     B.bufs.resize(nj);
+    long long group_px[kMaxLog2 + 1] = {};
+    for (auto& sp : spec) group_px[sp.log2n] += 1LL << (2 * sp.log2n);
     std::vector<int2> eb, jb, rb, vb, gb;
     for (int k = 0; k < nj; ++k) {
         const JobSpec& s = spec[k];
         const inim_map* m = s.map;
         const int n = 1 << s.log2n;
-        const ScanTile tile = tile_for(s.log2n);
+        const ScanTile tile = tile_for(s.log2n, s.precision, size_class(group_px[s.log2n]));
         const int nb = (n + tile.H - 1) / tile.H;
+        const int nb_alloc = min_H > 0 ? (n + min_H - 1) / min_H : nb;
         const int cap = m ? estimate_key_cap(m, start_xy_host[k] ? start_xy_host[k] : m->h_xy0.data(), n) : 16;
         Buffers& b = B.bufs[k];
-        CUDA_TRY(b.alloc(n, s.precision, m ? m->n_regions : 1, m ? m->n_verts : 1, cap, nb));
+        CUDA_TRY(b.alloc(n, s.precision, m ? m->n_regions : 1, m ? m->n_verts : 1, cap, nb_alloc, m != nullptr));
         Job J{};
         J.n = n; J.log2n = s.log2n;
         if (m) {
             J.n_verts = m->n_verts; J.n_regions = m->n_regions; J.n_edges = m->n_edges; J.n_rings = m->n_rings;
-            J.edges = m->edges; J.edge_region = m->edge_region; J.reg_ring_off = m->reg_ring_off;
+            J.edges = m->edges; J.edge_region = m->edge_region; J.reg_edge_off = m->reg_edge_off;
+            J.reg_ring_off = m->reg_ring_off;
             J.reg_rings = m->reg_rings; J.ring_off = m->ring_off; J.ring_idx = m->ring_idx; J.sign0 = m->sign0;
         }
         J.xy = b.xy; J.values = b.values; J.lam = 1.0f; J.bdv_scale = 1.0f; J.precision = s.precision;
-        J.labels = b.labels; J.row_cnt = b.row_cnt; J.row_off = b.row_off; J.keys = b.keys; J.key_cap = cap;
+        J.labels = b.labels; J.row_cnt = b.row_cnt; J.row_off = b.row_off; J.big_rows = b.big_rows;
+        J.keys = b.keys; J.key_cap = cap;
         J.counts = b.counts; J.dens = b.dens;
         J.S = b.S; J.T = b.T; J.A = b.A; J.B = b.B; J.rowcum = b.rowcum;
+        // map jobs: one interleaved (S, T) table (S's buffer holds both halves)
+        J.ST = m ? b.S : nullptr;
         J.H = tile.H; J.nb = nb; J.agg = b.agg; J.carry = b.carry;
         J.areas = b.areas; J.st = B.d_states + k;
         B.h_jobs[k] = J;
@@ -252,8 +286,10 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
             for (int q = 0; q < (m->n_regions + 7) / 8; ++q) gb.push_back(make_int2(k, q));
         }
         jb.push_back(make_int2(k, 0));
-        for (int j = 0; j < n; ++j) rb.push_back(make_int2(k, j));
+        for (int j = 0; j < n; j += kRowsPerBlock) rb.push_back(make_int2(k, j));
+        B.max_n = std::max(B.max_n, n);
     }
+    CUDA_TRY(raster_setup(B.max_n));
     CUDA_TRY(make_map(B.edge_blocks, eb));
     CUDA_TRY(make_map(B.job_blocks, jb));
     CUDA_TRY(make_map(B.row_blocks, rb));
@@ -266,14 +302,13 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
             if (spec[k].log2n != l) continue;
             const Job& J = B.h_jobs[k];
             for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
-            const int span = J.n + (J.nb - 1) * J.H;
-            const int len = J.n + 2 * span;
+            const int len = carry_qspace(J.n, J.nb, J.H);          // q values, 256 per block
             for (int q = 0; q < (len + 255) / 256; ++q) carry.push_back(make_int2(k, q));
         }
         if (band.empty()) continue;
         Group g;
         g.log2n = l;
-        g.tile = tile_for(l);
+        g.tile = tile_for(l, B.precision, size_class(group_px[l]));
         CUDA_TRY(make_map(g.band, band));
         CUDA_TRY(make_map(g.carry, carry));
         B.groups.push_back(g);
@@ -303,6 +338,33 @@ Batch* get_batch(const std::vector<JobSpec>& spec, const std::vector<const float
     return g_cache.front().get();
 }
 
+void purge_all() {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache.clear();
+}
+
+// retile one resolution group of a batch in place (buffers sized for min_H)
+int retile_group(Batch& B, Group& g, ScanTile t) {
+    std::vector<int2> band, carry;
+    for (int k = 0; k < (int)B.spec.size(); ++k) {
+        if (B.spec[k].log2n != g.log2n) continue;
+        Job& J = B.h_jobs[k];
+        J.H = t.H;
+        J.nb = (J.n + t.H - 1) / t.H;
+        for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
+        const int len = carry_qspace(J.n, J.nb, J.H);
+        for (int q = 0; q < (len + 255) / 256; ++q) carry.push_back(make_int2(k, q));
+    }
+    dfree(g.band.d_map);
+    dfree(g.carry.d_map);
+    CUDA_TRY(make_map(g.band, band));
+    CUDA_TRY(make_map(g.carry, carry));
+    g.tile = t;
+    CUDA_TRY(cudaMemcpyAsync(B.d_jobs, B.h_jobs.data(), B.h_jobs.size() * sizeof(Job), cudaMemcpyHostToDevice,
+                             B.stream));
+    return INIM_OK;
+}
+
 void purge_map(const inim_map* m) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     for (auto it = g_cache.begin(); it != g_cache.end();) {
@@ -316,8 +378,15 @@ void purge_map(const inim_map* m) {
 // ---------------------------------------------------------------------------
 // iteration drivers
 // ---------------------------------------------------------------------------
+// the first iteration of a run needs the row histogram of the start positions
+cudaError_t enqueue_prologue(Batch& B, cudaStream_t s) {
+    return launch_raster_prologue(B.d_jobs, B.edge_blocks, s);
+}
+
+// one fused iteration; its area kernel leaves the next iteration's row
+// histogram and offsets in place
 cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s) {
-    cudaError_t e = launch_raster(B.d_jobs, B.edge_blocks, B.job_blocks, B.row_blocks, s);
+    cudaError_t e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, s);
     if (e == cudaSuccess) e = launch_density_table(B.d_jobs, (int)B.spec.size(), s);
     for (auto& g : B.groups) {
         if (e != cudaSuccess) break;
@@ -326,7 +395,7 @@ cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s) {
         else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
     }
     if (e == cudaSuccess) e = launch_gather(B.d_jobs, B.vert_blocks, B.precision, s);
-    if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, (int)B.spec.size(), B.region_blocks, 1, s);
+    if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, (int)B.spec.size(), B.region_blocks, 1, 1, s);
     return e;
 }
 
@@ -335,14 +404,14 @@ constexpr int kGraphIters = 8;
 std::atomic<long long> g_launches{0};
 
 int kernels_per_fused_iteration(const Batch& B) {
-    int k = 2 + (B.edge_blocks.n_blocks ? 2 : 0);          // raster
-    k += 1;                                                  // density table
+    int k = 1 + (B.edge_blocks.n_blocks ? 1 : 0);          // crossings, rows
+    k += 1;                                                  // density table (+ big rows)
     k += 3 * (int)B.groups.size();                           // scan phases 1-3
     k += B.vert_blocks.n_blocks ? 1 : 0;                     // gather / move
-    k += (B.region_blocks.n_blocks ? 1 : 0) + 1;             // areas, errors
+    k += B.region_blocks.n_blocks ? 1 : 0;                   // areas + errors + next histogram
     return k;
 }
-constexpr int kKernelsPerPlainIteration = 17;
+constexpr int kKernelsPerPlainIteration = 15;
 
 int ensure_graph(Batch& B) {
     if (B.graph) return INIM_OK;
@@ -383,6 +452,8 @@ int run_fused(Batch& B, int max_iters, bool poll) {
     const int nj = (int)B.spec.size();
     int st = ensure_graph(B);
     if (st != INIM_OK) return st;
+    CUDA_TRY(enqueue_prologue(B, B.stream));
+    g_launches += B.edge_blocks.n_blocks ? 1 : 0;
     int done = 0;
     while (done < max_iters) {
         CUDA_TRY(cudaGraphLaunch(B.graph, B.stream));
@@ -412,10 +483,11 @@ int run_plain(Batch& B, int max_iters) {
     for (int k = 0; k < nj; ++k) {
         const Job* dj = B.d_jobs + k;
         for (int it = 0; it < max_iters; ++it) {
-            CUDA_TRY(launch_raster(B.d_jobs, B.edge_blocks, B.job_blocks, B.row_blocks, B.stream));
+            CUDA_TRY(launch_raster_prologue(B.d_jobs, B.edge_blocks, B.stream));
+            CUDA_TRY(launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream));
             CUDA_TRY(launch_density_table(dj, 1, B.stream));
             CUDA_TRY(plain_iteration(dj, B.h_jobs[k], B.plain[k], B.stream));
-            CUDA_TRY(launch_areas_errors(B.d_jobs, nj, B.region_blocks, 1, B.stream));
+            CUDA_TRY(launch_areas_errors(B.d_jobs, nj, B.region_blocks, 1, 0, B.stream));
             g_launches += kKernelsPerPlainIteration;
             CUDA_TRY(cudaMemcpyAsync(&B.h_states[k], B.d_states + k, sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
             CUDA_TRY(cudaStreamSynchronize(B.stream));
@@ -557,9 +629,11 @@ int inim_map_create(const float* xy, int32_t n_verts, const int32_t* ring_off, i
     }
     std::vector<int2> edges;
     std::vector<int> edge_region;
+    std::vector<int> reg_edge_off(n_regions + 1, 0);
     std::vector<float> sign0(n_regions, 0.0f);
     edges.reserve(total);
     for (int v = 0; v < n_regions; ++v) {
+        reg_edge_off[v] = (int)edges.size();
         double area2 = 0.0;
         for (int q = reg_ring_off[v]; q < reg_ring_off[v + 1]; ++q) {
             const int r = reg_rings[q];
@@ -576,6 +650,7 @@ int inim_map_create(const float* xy, int32_t n_verts, const int32_t* ring_off, i
         sign0[v] = area2 > 0.0 ? 1.0f : (area2 < 0.0 ? -1.0f : 0.0f);
     }
     m->n_edges = (int)edges.size();
+    reg_edge_off[n_regions] = m->n_edges;
     m->h_xy0 = hxy;
     auto up = [&](void** dst, const void* src, size_t bytes) {
         cudaError_t e = cudaMalloc(dst, bytes < 16 ? 16 : bytes);
@@ -585,6 +660,7 @@ int inim_map_create(const float* xy, int32_t n_verts, const int32_t* ring_off, i
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = up((void**)&m->edges, edges.data(), edges.size() * sizeof(int2));
     if (e == cudaSuccess) e = up((void**)&m->edge_region, edge_region.data(), edge_region.size() * 4);
+    if (e == cudaSuccess) e = up((void**)&m->reg_edge_off, reg_edge_off.data(), reg_edge_off.size() * 4);
     if (e == cudaSuccess) e = up((void**)&m->reg_ring_off, reg_ring_off.data(), reg_ring_off.size() * 4);
     if (e == cudaSuccess) e = up((void**)&m->reg_rings, reg_rings.data(), reg_rings.size() * 4);
     if (e == cudaSuccess) e = up((void**)&m->ring_off, hoff.data(), hoff.size() * 4);
@@ -602,7 +678,7 @@ int inim_map_create(const float* xy, int32_t n_verts, const int32_t* ring_off, i
 int inim_map_destroy(inim_map* m) {
     if (!m) return INIM_OK;
     purge_map(m);
-    dfree(m->edges); dfree(m->edge_region); dfree(m->reg_ring_off); dfree(m->reg_rings);
+    dfree(m->edges); dfree(m->edge_region); dfree(m->reg_edge_off); dfree(m->reg_ring_off); dfree(m->reg_rings);
     dfree(m->ring_off); dfree(m->ring_idx); dfree(m->sign0); dfree(m->xy0);
     delete m;
     return INIM_OK;
@@ -748,7 +824,8 @@ int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, xy, (size_t)map->n_verts * 8, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
-    CUDA_TRY(launch_raster(B->d_jobs, B->edge_blocks, B->job_blocks, B->row_blocks, B->stream));
+    CUDA_TRY(launch_raster_prologue(B->d_jobs, B->edge_blocks, B->stream));
+    CUDA_TRY(launch_raster_main(B->d_jobs, B->edge_blocks, B->row_blocks, B->max_n, B->stream));
     CUDA_TRY(launch_density_table(B->d_jobs, 1, B->stream));
     CUDA_TRY(cudaMemcpyAsync(labels, B->bufs[0].labels, (size_t)n * n * 2, cudaMemcpyDeviceToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(counts, B->bufs[0].counts, (size_t)(R + 1) * 4, cudaMemcpyDeviceToDevice, B->stream));
@@ -843,8 +920,9 @@ int inim_iterate(const inim_map* map, float* xy, const float* values, const inim
     if (n_iters > 0) {
         if (params->form == INIM_FORM_PLAIN) st = run_plain(*B, n_iters);
         else {
+            CUDA_TRY(enqueue_prologue(*B, B->stream));
             for (int k = 0; k < n_iters; ++k) CUDA_TRY(enqueue_fused_iteration(*B, B->stream));
-            g_launches += (long long)n_iters * kernels_per_fused_iteration(*B);
+            g_launches += 1 + (long long)n_iters * kernels_per_fused_iteration(*B);
             CUDA_TRY(cudaMemcpyAsync(B->h_states.data(), B->d_states, sizeof(JobState), cudaMemcpyDeviceToHost, B->stream));
             CUDA_TRY(cudaStreamSynchronize(B->stream));
         }
@@ -871,9 +949,103 @@ int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, hxy.data(), hxy.size() * 4, cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
-    CUDA_TRY(launch_areas_errors(B->d_jobs, 1, B->region_blocks, -1, B->stream));
+    CUDA_TRY(launch_areas_errors(B->d_jobs, 1, B->region_blocks, -1, 0, B->stream));
     CUDA_TRY(cudaMemcpyAsync(areas, B->bufs[0].areas, (size_t)map->n_regions * 8, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaStreamSynchronize(B->stream));
+    return INIM_OK;
+}
+
+int inim_set_scan_tile(int32_t log2_res, int32_t precision, int32_t large, int32_t band_rows,
+                       int32_t cols_per_thread, int32_t threads) {
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2 || precision < INIM_FP32 || precision > INIM_KAHAN)
+        return fail(INIM_E_ARG, "bad resolution or precision");
+    ScanTile t{band_rows, cols_per_thread, threads};
+    if (band_rows == 0) t = ScanTile{0, 0, 0};              // back to the default
+    else if (!tile_valid(log2_res, t)) return fail(INIM_E_ARG, "no compiled scan kernel for this tile");
+    purge_all();
+    g_tiles[precision][large ? 1 : 0][log2_res] = t;
+    return INIM_OK;
+}
+
+int inim_get_scan_tile(int32_t log2_res, int32_t precision, int32_t large, int32_t* band_rows,
+                       int32_t* cols_per_thread, int32_t* threads) {
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2 || precision < INIM_FP32 || precision > INIM_KAHAN)
+        return fail(INIM_E_ARG, "bad resolution or precision");
+    const ScanTile t = tile_for(log2_res, precision, large ? 1 : 0);
+    if (band_rows) *band_rows = t.H;
+    if (cols_per_thread) *cols_per_thread = t.cpt;
+    if (threads) *threads = t.nt;
+    return INIM_OK;
+}
+
+int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
+    if (!jobs || n_jobs < 1 || reps < 1) return fail(INIM_E_ARG, "bad arguments");
+    std::vector<JobSpec> spec(n_jobs);
+    std::vector<const float*> cap_ptr(n_jobs);
+    for (int k = 0; k < n_jobs; ++k) {
+        const inim_job& j = jobs[k];
+        if (!j.map || !j.values) return fail(INIM_E_ARG, "job with NULL map or values");
+        int st = check_params(&j.params);
+        if (st != INIM_OK) return st;
+        if (j.params.precision != jobs[0].params.precision) return fail(INIM_E_ARG, "all jobs need one precision");
+        spec[k] = JobSpec{j.map, j.params.log2_res, j.params.precision};
+        cap_ptr[k] = j.map->h_xy0.data();
+    }
+    Batch B;
+    int st = build_batch(B, spec, cap_ptr, kTileHeights[0]);
+    if (st != INIM_OK) return st;
+    for (int k = 0; k < n_jobs; ++k) {
+        const inim_job& j = jobs[k];
+        B.h_jobs[k].lam = 1.0f - j.params.shape;
+        B.h_jobs[k].bdv_scale = j.params.bdv_scale;
+        CUDA_TRY(cudaMemcpyAsync(B.bufs[k].values, j.values, (size_t)j.map->n_regions * 4, cudaMemcpyDefault, B.stream));
+        CUDA_TRY(cudaMemcpyAsync(B.bufs[k].xy, j.init_xy ? j.init_xy : j.map->h_xy0.data(),
+                                 (size_t)j.map->n_verts * 8, cudaMemcpyDefault, B.stream));
+        B.h_states[k] = initial_state(j.params, 0, INT_MAX);
+    }
+    CUDA_TRY(cudaMemcpyAsync(B.d_jobs, B.h_jobs.data(), n_jobs * sizeof(Job), cudaMemcpyHostToDevice, B.stream));
+    CUDA_TRY(cudaMemcpyAsync(B.d_states, B.h_states.data(), n_jobs * sizeof(JobState), cudaMemcpyHostToDevice, B.stream));
+    // labels and densities of the start positions
+    CUDA_TRY(launch_raster_prologue(B.d_jobs, B.edge_blocks, B.stream));
+    CUDA_TRY(launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream));
+    CUDA_TRY(launch_density_table(B.d_jobs, n_jobs, B.stream));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    std::vector<std::pair<int, ScanTile>> chosen;
+    for (auto& g : B.groups) {
+        float best = 1e30f;
+        ScanTile best_t = g.tile;
+        for (auto& q : kTilePairs) {
+            for (int H : kTileHeights) {
+                ScanTile t{H, q[0], q[1]};
+                if (!tile_valid(g.log2n, t)) continue;
+                st = retile_group(B, g, t);
+                if (st != INIM_OK) return st;
+                auto scan = [&]() {
+                    if (B.precision == INIM_FIX64) return launch_scan_fix64(B.d_jobs, g.band, g.carry, t, nullptr, B.stream);
+                    if (B.precision == INIM_KAHAN) return launch_scan_kahan(B.d_jobs, g.band, g.carry, t, nullptr, B.stream);
+                    return launch_scan_fp32(B.d_jobs, g.band, g.carry, t, nullptr, B.stream);
+                };
+                CUDA_TRY(scan());                                  // warm
+                CUDA_TRY(cudaEventRecord(e0, B.stream));
+                for (int r = 0; r < reps; ++r) CUDA_TRY(scan());
+                CUDA_TRY(cudaEventRecord(e1, B.stream));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; best_t = t; }
+            }
+        }
+        long long px = 0;
+        for (auto& sp : spec) if (sp.log2n == g.log2n) px += 1LL << (2 * sp.log2n);
+        chosen.push_back({g.log2n * 2 + size_class(px), best_t});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(cudaStreamSynchronize(B.stream));
+    purge_all();
+    for (auto& c : chosen) g_tiles[B.precision][c.first & 1][c.first >> 1] = c.second;
     return INIM_OK;
 }
 
@@ -903,7 +1075,7 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
     CUDA_TRY(cudaEventCreate(&e1));
     auto stage = [&](int i) -> cudaError_t {
         switch (i) {
-            case 0: return launch_raster(B.d_jobs, B.edge_blocks, B.job_blocks, B.row_blocks, B.stream);
+            case 0: return launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream);
             case 1: return launch_density_table(B.d_jobs, nj, B.stream);
             case 2: case 3: case 4: {
                 cudaError_t e = cudaSuccess;
@@ -916,7 +1088,7 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
                 return e;
             }
             case 5: return launch_gather(B.d_jobs, B.vert_blocks, B.precision, B.stream);
-            default: return launch_areas_errors(B.d_jobs, nj, B.region_blocks, 0, B.stream);
+            default: return launch_areas_errors(B.d_jobs, nj, B.region_blocks, 0, 1, B.stream);
         }
     };
     int rc = INIM_OK;

@@ -4,49 +4,30 @@
 // proportional to mass once the density is equalised), fold-over detection,
 // and the stop rule (xi < xi_stop, no improvement of xi within stall_window
 // iterations, or max_iters iterations; Sec. 4.1 defaults).
-#include "inim_internal.cuh"
+//
+// One kernel: a warp per region sums the shoelace terms of the region's edges
+// (contiguous in the edge list, coalesced loads) with exact FP32 products and
+// compensated FP32 sums (the FP64 pipe of this GPU is narrow; double is used
+// only for the per-lane partials and the error reduction); the last block of a job to
+// finish (atomic ticket) reduces the errors over the job's regions in a fixed
+// order and applies the stop rule, so the result does not depend on timing.
+#include "raster_common.cuh"
 
 namespace inim {
 
 namespace {
 
-// one warp per region; 8 regions per block
-__global__ void __launch_bounds__(256) k_areas(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
-    const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
-    if (!J.st->active) return;
-    const int v = m.y * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (v >= J.n_regions) return;
-    double acc = 0.0;
-    for (int q = J.reg_ring_off[v]; q < J.reg_ring_off[v + 1]; ++q) {
-        const int r = J.reg_rings[q];
-        const int b = J.ring_off[r], e = J.ring_off[r + 1];
-        const int len = e - b;
-        for (int k = lane; k < len; k += 32) {
-            const float2 p = J.xy[J.ring_idx[b + k]];
-            const float2 q2 = J.xy[J.ring_idx[b + (k + 1 == len ? 0 : k + 1)]];
-            // products of floats are exact in double
-            acc += (double)p.x * (double)q2.y - (double)q2.x * (double)p.y;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) J.areas[v] = 0.5 * acc;
-}
+constexpr int kRegionsPerBlock = 8;
 
-// one block per job
-__global__ void __launch_bounds__(256) k_errors(const Job* __restrict__ jobs, int update_state) {
-    const Job& J = jobs[blockIdx.x];
+__device__ void errors_and_stop(const Job& J, int update_state) {
+    __shared__ double ssum[kRegionsPerBlock], smax[kRegionsPerBlock];
+    __shared__ int sfold[kRegionsPerBlock];
     JobState* st = J.st;
-    if (!st->active) return;
-    __shared__ double ssum[8], smax[8];
-    __shared__ int sfold[8];
     const double M = st->mass;
     double sum = 0.0, mx = 0.0;
     int fold = 0;
     for (int v = threadIdx.x; v < J.n_regions; v += blockDim.x) {
-        const double a = J.areas[v];
+        const double a = __ldcg(J.areas + v);
         const double o = fabs(a);
         const double w = (double)J.values[v] / M;
         const double den = fmax(o, w);
@@ -68,7 +49,7 @@ __global__ void __launch_bounds__(256) k_errors(const Job* __restrict__ jobs, in
     if (threadIdx.x == 0) {
         double S = 0.0, X = 0.0;
         int F = 0;
-        for (int k = 0; k < 8; ++k) { S += ssum[k]; X = fmax(X, smax[k]); F |= sfold[k]; }
+        for (int k = 0; k < kRegionsPerBlock; ++k) { S += ssum[k]; X = fmax(X, smax[k]); F |= sfold[k]; }
         const double eps = S / (double)J.n_regions;
         st->eps = eps;
         st->xi = X;
@@ -89,12 +70,70 @@ __global__ void __launch_bounds__(256) k_errors(const Job* __restrict__ jobs, in
     }
 }
 
+// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only.
+// next_hist: the moved vertices are the next iteration's raster input, so the
+// same edge pass also builds its row histogram (and the last block its row
+// offsets), saving the rasteriser two launches.
+__global__ void __launch_bounds__(256) k_areas_errors(const Job* __restrict__ jobs, const int2* __restrict__ bmap,
+                                                      int update_state, int next_hist) {
+    const int2 m = bmap[blockIdx.x];
+    const Job& J = jobs[m.x];
+    if (!J.st->active) return;
+    const int v = m.y * kRegionsPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (v < J.n_regions) {
+        // shoelace terms x_a y_b - x_b y_a: each product is split exactly into
+        // p + e (e = fma(x, y, -p)) and summed with two-sum into a (hi, lo)
+        // pair, all in FP32; one conversion to double per lane at the end
+        float hi = 0.0f, lo = 0.0f;
+        const int e1 = J.reg_edge_off[v + 1];
+        for (int e = J.reg_edge_off[v] + lane; e < e1; e += 32) {
+            if (next_hist) row_hist_edge(J, e);
+            const int2 ab = J.edges[e];
+            const float2 p = J.xy[ab.x];
+            const float2 q = J.xy[ab.y];
+            const float p1 = __fmul_rn(p.x, q.y), e1p = __fmaf_rn(p.x, q.y, -p1);
+            const float p2 = __fmul_rn(q.x, p.y), e2p = __fmaf_rn(q.x, p.y, -p2);
+            float s = __fadd_rn(hi, p1);
+            float bb = __fsub_rn(s, hi);
+            lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p1, bb)), e1p));
+            hi = s;
+            s = __fadd_rn(hi, -p2);
+            bb = __fsub_rn(s, hi);
+            lo = __fadd_rn(lo, __fsub_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-p2, bb)), e2p));
+            hi = s;
+        }
+        double acc = (double)hi + (double)lo;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) J.areas[v] = 0.5 * acc;
+    }
+    if (update_state < 0) return;
+    // the last block of this job reduces the errors
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nblk = (J.n_regions + kRegionsPerBlock - 1) / kRegionsPerBlock;
+        const int ticket = atomicAdd(&J.st->blocks_done, 1);
+        last = (ticket == nblk - 1);
+        if (last) J.st->blocks_done = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    errors_and_stop(J, update_state);
+    if (next_hist) row_offsets_block(J);
+}
+
 }  // namespace
 
 cudaError_t launch_areas_errors(const Job* d_jobs, int n_jobs, const BlockMap& region_blocks,
-                                int update_state, cudaStream_t s) {
-    if (region_blocks.n_blocks) k_areas<<<region_blocks.n_blocks, 256, 0, s>>>(d_jobs, region_blocks.d_map);
-    if (update_state >= 0) k_errors<<<n_jobs, 256, 0, s>>>(d_jobs, update_state);
+                                int update_state, int next_hist, cudaStream_t s) {
+    (void)n_jobs;
+    if (region_blocks.n_blocks)
+        k_areas_errors<<<region_blocks.n_blocks, 256, 0, s>>>(d_jobs, region_blocks.d_map, update_state,
+                                                              update_state < 0 ? 0 : next_hist);
     return cudaGetLastError();
 }
 

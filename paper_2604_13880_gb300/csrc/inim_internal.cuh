@@ -35,7 +35,9 @@ struct JobState {
     double mass;         // total mass in the texture (w(v) = s(v) / mass)
     double bdv_abs;      // background density in value units
     int   stop_on_rule;  // 0: run exactly max_iters (no early stop)
-    int   pad;
+    int   blocks_done;   // area blocks finished in this iteration (last one reduces)
+    int   n_big;         // rows of this iteration with more crossings than a warp holds
+    int   hist_done;     // edge blocks of the prologue finished (last one scans)
 };
 
 // Everything a kernel needs to work on one job.  Lives in device memory; one
@@ -47,6 +49,7 @@ struct Job {
     int n_verts, n_regions, n_edges, n_rings;
     const int2* edges;         // [n_edges] vertex ids, grouped by region
     const int*  edge_region;   // [n_edges]
+    const int*  reg_edge_off;  // [n_regions+1] edges of region v: [off[v], off[v+1])
     const int*  reg_ring_off;  // [n_regions+1] into reg_rings
     const int*  reg_rings;     // ring ids grouped by region
     const int*  ring_off;      // [n_rings+1]
@@ -62,6 +65,7 @@ struct Job {
     uint16_t* labels;          // [n*n]
     int*      row_cnt;         // [n]   crossings per row (zero between uses)
     int*      row_off;         // [n+1] exclusive prefix of row_cnt
+    int*      big_rows;        // [n] rows left to the block-per-row path
     uint32_t* keys;            // [key_cap] (region << 16 | column)
     int       key_cap;
     int*      counts;          // [n_regions+1] pixel areas o(v); last = background
@@ -69,6 +73,7 @@ struct Job {
     // integral images (element type by precision)
     void*  S;                  // [n*n] 2-D inclusive prefix (alpha)
     void*  T;                  // [n*n] top wedge (alpha_t)
+    void*  ST;                 // [n*n][2] interleaved (S, T); when set, S and T are not written
     void*  A;                  // [2n-1] A(s) = sum_{i+j<=s} d
     void*  B;                  // [2n-1] w<=0: sum_{i-j<=w} d ; w>0: sum_{i-j>w} d
     void*  rowcum;             // [n] S(n-1, j)
@@ -175,8 +180,10 @@ struct BlockMap {            // block -> (job, first item) tables for one kernel
 
 struct ScanTile { int H; int cpt; int nt; };   // band height, columns/thread, threads
 
-cudaError_t launch_raster(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& job_blocks,
-                          const BlockMap& row_blocks, cudaStream_t s);
+cudaError_t raster_setup(int max_n);   // once per process
+cudaError_t launch_raster_prologue(const Job* d_jobs, const BlockMap& edge_blocks, cudaStream_t s);
+cudaError_t launch_raster_main(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& row_blocks,
+                               int max_n, cudaStream_t s);
 cudaError_t launch_density_table(const Job* d_jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_scan_fp32(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
                              ScanTile tile, const float* dtex, cudaStream_t s, int phase = 0);
@@ -186,9 +193,10 @@ cudaError_t launch_scan_kahan(const Job* d_jobs, const BlockMap& band, const Blo
                               ScanTile tile, const float* dtex, cudaStream_t s, int phase = 0);
 cudaError_t launch_gather(const Job* d_jobs, const BlockMap& vert_blocks, int precision,
                           cudaStream_t s);
-// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only
+// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only;
+// next_hist: also build the next iteration's row histogram and offsets
 cudaError_t launch_areas_errors(const Job* d_jobs, int n_jobs, const BlockMap& region_blocks,
-                                int update_state, cudaStream_t s);
+                                int update_state, int next_hist, cudaStream_t s);
 cudaError_t launch_displacement(const Job* d_job, const float* xy, int n, float* delta,
                                 int precision, cudaStream_t s);
 cudaError_t launch_finalize_B(const Job* d_job, int precision, cudaStream_t s);

@@ -88,8 +88,7 @@ extern "C" int inim_inims_noalloc(const float* density, int32_t log2_res, float*
     unsigned char* b = static_cast<unsigned char*>(base);
     const int n = 1 << log2_res;
     const int nb = n / kNaH;
-    const int span = n + (nb - 1) * kNaH;
-    const int carry_blocks = (n + 2 * span + 255) / 256;
+    const int carry_blocks = (carry_qspace(n, nb, kNaH) + 255) / 256;
     ScanTile tile{kNaH, log2_res == 8 ? 2 : (log2_res == 9 ? 4 : 8), 128};
 
     Job J{};

@@ -11,14 +11,17 @@
 // regions it takes the smallest id and the overlap flag is raised.
 //
 // Kernels (edge-parallel, then row-parallel; no per-pixel atomics):
-//   k_row_hist     per edge: crossings per row
-//   k_row_offsets  per job: exclusive prefix over rows, clears counters
+//   row histogram + offsets   per edge, then one block per job: crossings per
+//                             row and their exclusive prefix (k_raster_prologue
+//                             for the start positions; afterwards fused into
+//                             the area kernel of the previous iteration)
 //   k_crossings    per edge: scatter (region << 16 | c) keys into row buckets
-//   k_raster_rows  per row: sort keys, pair them into spans, turn the spans
-//                  into an XOR/coverage difference array, prefix it, write
-//                  the labels of the whole row once with vector stores, and
-//                  add span lengths to the pixel counts.
-#include "inim_internal.cuh"
+//   k_raster_rows  warp per row: sort the row's keys in registers, pair them
+//                  into spans, paint them into a shared-memory copy of the row
+//                  in region order, write the row once; rows with more than
+//                  256 crossings go to the block-per-row path (run by the
+//                  density-table kernel).
+#include "raster_common.cuh"
 
 namespace inim {
 
@@ -27,88 +30,44 @@ namespace {
 constexpr int kRowThreads = 256;
 constexpr int kRowKeyCap = 2048;   // crossings one row can hold in shared memory
 
-struct EdgeFix {
-    long long X0, Y0, X1, Y1;
-    int jlo, jhi;
-};
-
-__device__ __forceinline__ bool edge_rows(const Job& J, int e, EdgeFix& f) {
-    int2 ab = J.edges[e];
-    float2 p = J.xy[ab.x];
-    float2 q = J.xy[ab.y];
-    const float scale = (float)(1 << (J.log2n + kSubBits));
-    long long X0 = snap_coord(p.x, scale), Y0 = snap_coord(p.y, scale);
-    long long X1 = snap_coord(q.x, scale), Y1 = snap_coord(q.y, scale);
-    if (Y1 < Y0) {
-        long long t = X0; X0 = X1; X1 = t;
-        t = Y0; Y0 = Y1; Y1 = t;
-    }
-    if (Y1 == Y0) return false;                       // horizontal: never counted
-    long long jlo = ceil_div(Y0 - 128, 256);
-    long long jhi = ceil_div(Y1 - 128, 256) - 1;
-    if (jlo < 0) jlo = 0;
-    if (jhi > J.n - 1) jhi = J.n - 1;
-    if (jlo > jhi) return false;
-    f.X0 = X0; f.Y0 = Y0; f.X1 = X1; f.Y1 = Y1;
-    f.jlo = (int)jlo; f.jhi = (int)jhi;
-    return true;
+// min(max(ceil(num / den), 0), n) exactly, for den > 0, without a 64-bit
+// division: a float estimate of the quotient (only needed in [0, n], n <=
+// 4096, where it is off by less than one) corrected by exact int64 products.
+__device__ __forceinline__ int clamped_ceil_div(long long num, long long den, int n) {
+    if (num <= 0) return 0;                              // ceil <= 0
+    if (num > (long long)n * den) return n;              // ceil > n
+    long long q = (long long)floorf(__fdiv_rn((float)num, (float)den));
+    long long r = num - q * den;
+    while (r < 0) { --q; r += den; }
+    while (r >= den) { ++q; r -= den; }
+    const long long c = q + (r > 0 ? 1 : 0);
+    return (int)(c > n ? n : c);
 }
 
-__global__ void k_row_hist(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
+
+// Histogram + offsets of the current vertex positions (the first iteration
+// of a run; later iterations get them from the area kernel).  One ticket per
+// job: the last edge block of a job computes its offsets.
+__global__ void __launch_bounds__(256) k_raster_prologue(const Job* __restrict__ jobs,
+                                                         const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
     if (!J.st->active) return;
     const int e = m.y * blockDim.x + threadIdx.x;
-    if (e >= J.n_edges) return;
-    EdgeFix f;
-    if (!edge_rows(J, e, f)) return;
-    for (int j = f.jlo; j <= f.jhi; ++j) atomicAdd(&J.row_cnt[j], 1);
-}
-
-// one block of 1024 threads per job
-__global__ void k_row_offsets(const Job* __restrict__ jobs) {
-    const Job& J = jobs[blockIdx.x];
-    if (!J.st->active) return;
-    __shared__ int wsum[32];
-    const int n = J.n;
-    const int per = (n + blockDim.x - 1) / blockDim.x;   // <= 4
-    const int base = threadIdx.x * per;
-    int loc[4];
-    int s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        int v = (k < per && base + k < n) ? J.row_cnt[base + k] : 0;
-        loc[k] = s;
-        s += v;
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[w] = incl;
+    if (e < J.n_edges) row_hist_edge(J, e);
+    __shared__ int last;
+    __threadfence();
     __syncthreads();
-    int woff = 0, tot = 0;
-    const int nw = blockDim.x >> 5;
-    for (int k = 0; k < nw; ++k) {
-        if (k < w) woff += wsum[k];
-        tot += wsum[k];
-    }
-    const int excl = woff + incl - s;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (k < per && base + k < n) {
-            J.row_off[base + k] = excl + loc[k];
-            J.row_cnt[base + k] = 0;            // reused as the fill cursor
-        }
-    }
     if (threadIdx.x == 0) {
-        J.row_off[n] = tot;
-        if (tot > J.key_cap) atomicExch(&J.st->error, INIM_E_CAPACITY);
+        const int nblk = (J.n_edges + 255) / 256;
+        const int ticket = atomicAdd(&J.st->hist_done, 1);
+        last = (ticket == nblk - 1);
+        if (last) J.st->hist_done = 0;
     }
-    for (int v = threadIdx.x; v <= J.n_regions; v += blockDim.x) J.counts[v] = 0;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    row_offsets_block(J);
 }
 
 __global__ void k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
@@ -125,9 +84,7 @@ __global__ void k_crossings(const Job* __restrict__ jobs, const int2* __restrict
     const long long den = 256 * dY;
     for (int j = f.jlo; j <= f.jhi; ++j) {
         const long long Yc = 256LL * j + 128;
-        long long c = ceil_div(dX * (Yc - f.Y0) + (f.X0 - 128) * dY, den);
-        if (c < 0) c = 0;
-        if (c > J.n) c = J.n;
+        const int c = clamped_ceil_div(dX * (Yc - f.Y0) + (f.X0 - 128) * dY, den, J.n);
         const int slot = atomicAdd(&J.row_cnt[j], 1);
         const int idx = J.row_off[j] + slot;
         if (idx < J.key_cap) J.keys[idx] = reg | (unsigned)c;
@@ -275,26 +232,172 @@ __device__ void raster_row(const Job& J, int j, RowShared& sh) {
     if (tid == 0) J.row_cnt[j] = 0;     // ready for the next iteration
 }
 
-__global__ void __launch_bounds__(kRowThreads) k_raster_rows(const Job* __restrict__ jobs,
-                                                            const int2* __restrict__ bmap) {
-    __shared__ RowShared sh;
-    const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
-    if (!J.st->active) return;
-    const int j = m.y;
-    switch (J.n / kRowThreads) {
-        case 1: raster_row<1>(J, j, sh); break;
-        case 2: raster_row<2>(J, j, sh); break;
-        case 4: raster_row<4>(J, j, sh); break;
-        case 8: raster_row<8>(J, j, sh); break;
-        default: raster_row<16>(J, j, sh); break;
+// Rows with more crossings than a warp holds in registers, one block per job
+// (usually none): the block-per-row path.
+__device__ void raster_big_rows(const Job& J, RowShared& sh) {
+    const int nbig = __ldcg(&J.st->n_big);
+    for (int q = 0; q < nbig; ++q) {
+        const int j = J.big_rows[q];
+        switch (J.n / kRowThreads) {
+            case 1: raster_row<1>(J, j, sh); break;
+            case 2: raster_row<2>(J, j, sh); break;
+            case 4: raster_row<4>(J, j, sh); break;
+            case 8: raster_row<8>(J, j, sh); break;
+            default: raster_row<16>(J, j, sh); break;
+        }
+        __syncthreads();
     }
 }
 
-// per job: d0, density table, background count, total mass, fixed-point scale
-__global__ void k_density_table(const Job* __restrict__ jobs) {
+// ---------------------------------------------------------------------------
+// warp-per-row rasteriser (the common case: <= 256 crossings in a row)
+// ---------------------------------------------------------------------------
+constexpr int kWarpsPerBlock = 8;
+
+// ascending bitonic sort of KPL*32 keys, lane l holding elements [l*KPL, l*KPL+KPL)
+template <int KPL>
+__device__ __forceinline__ void warp_bitonic(unsigned (&k)[KPL], int lane) {
+    constexpr int NT = KPL * 32;
+#pragma unroll
+    for (int size = 2; size <= NT; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= KPL) {
+                const int lmask = stride / KPL;
+#pragma unroll
+                for (int e = 0; e < KPL; ++e) {
+                    const int idx = lane * KPL + e;
+                    const unsigned other = __shfl_xor_sync(0xffffffffu, k[e], lmask);
+                    const bool up = (idx & size) == 0;
+                    const bool lower = (idx & stride) == 0;
+                    const unsigned mn = min(k[e], other), mx = max(k[e], other);
+                    k[e] = (lower == up) ? mn : mx;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < KPL; ++e) {
+                    const int p = e ^ stride;
+                    if (p > e) {
+                        const int idx = lane * KPL + e;
+                        const bool up = (idx & size) == 0;
+                        const unsigned a = k[e], b = k[p];
+                        if (up ? (a > b) : (a < b)) { k[e] = b; k[p] = a; }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// One row: keys sorted by (region, column) give each region's spans as
+// consecutive pairs.  The spans are painted into a shared-memory copy of the
+// row in sorted order, writing only still-background pixels, so a pixel in
+// several regions keeps the smallest id.  Overlap <=> the summed span lengths
+// exceed the painted pixel count.
+template <int KPL>
+__device__ void raster_row_warp(const Job& J, int j, int cnt, uint16_t* row, int lane) {
+    const int n = J.n;
+    const unsigned R = (unsigned)J.n_regions;
+    const int k0 = J.row_off[j];
+    unsigned key[KPL];
+#pragma unroll
+    for (int e = 0; e < KPL; ++e) {
+        const int idx = lane * KPL + e;
+        key[e] = idx < cnt ? J.keys[k0 + idx] : 0xffffffffu;
+    }
+    // background fill of the row copy
+    unsigned* row32 = reinterpret_cast<unsigned*>(row);
+    const unsigned bg2 = R | (R << 16);
+    for (int i = lane; i < (n >> 1); i += 32) row32[i] = bg2;
+    warp_bitonic<KPL>(key, lane);
+    __syncwarp();
+    // paint spans in sorted order
+    int my_len = 0;
+    const int src_lanes = (cnt + KPL - 1) / KPL;
+    for (int src = 0; src < src_lanes; ++src) {
+#pragma unroll
+        for (int t = 0; t < KPL / 2; ++t) {
+            const unsigned ka = __shfl_sync(0xffffffffu, key[2 * t], src);
+            const unsigned kb = __shfl_sync(0xffffffffu, key[2 * t + 1], src);
+            if (src * KPL + 2 * t + 1 >= cnt) continue;          // padding (warp-uniform)
+            const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
+            const uint16_t v = (uint16_t)(ka >> 16);
+            if (a < b) {
+                if (lane == 0) my_len += b - a;
+                for (int i = a + lane; i < b; i += 32)
+                    if (row[i] == (uint16_t)R) row[i] = v;
+            }
+            __syncwarp();
+        }
+    }
+    // painted pixels vs summed span lengths
+    int painted = 0;
+    for (int i = lane; i < (n >> 1); i += 32) {
+        const unsigned w = row32[i];
+        painted += ((w & 0xffffu) != R) + ((w >> 16) != R);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        painted += __shfl_xor_sync(0xffffffffu, painted, o);
+        my_len += __shfl_xor_sync(0xffffffffu, my_len, o);
+    }
+    if (painted == my_len) {
+        // no overlap: counts from the spans held by this lane
+#pragma unroll
+        for (int t = 0; t < KPL / 2; ++t) {
+            const int idx = lane * KPL + 2 * t;
+            if (idx + 1 < cnt) {
+                const int a = (int)(key[2 * t] & 0xffffu), b = (int)(key[2 * t + 1] & 0xffffu);
+                if (a < b) atomicAdd(&J.counts[key[2 * t] >> 16], b - a);
+            }
+        }
+    } else {
+        // fold-over in this row: counts from the resolved labels
+        for (int i = lane; i < n; i += 32)
+            if (row[i] != (uint16_t)R) atomicAdd(&J.counts[row[i]], 1);
+        if (lane == 0) atomicExch(&J.st->overlap, 1);
+    }
+    // write the row
+    uint4* dst = reinterpret_cast<uint4*>(J.labels + (size_t)j * n);
+    const uint4* srcv = reinterpret_cast<const uint4*>(row);
+    for (int i = lane; i < (n >> 3); i += 32) dst[i] = srcv[i];
+    if (lane == 0) J.row_cnt[j] = 0;     // ready for the next iteration
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_raster_rows(const Job* __restrict__ jobs,
+                                                                    const int2* __restrict__ bmap) {
+    extern __shared__ __align__(16) uint16_t rows_smem[];
+    const int2 m = bmap[blockIdx.x];                 // (job, first row)
+    const Job& J = jobs[m.x];
+    if (!J.st->active) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = m.y + warp;
+    if (j >= J.n) return;
+    uint16_t* row = rows_smem + (size_t)warp * J.n;
+    const int k0 = J.row_off[j];
+    const int k1 = J.row_off[j + 1];
+    const int cnt = k1 - k0;
+    if (k1 > J.key_cap) {                            // capacity error already flagged
+        if (lane == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
+        return;
+    }
+    if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, row, lane);
+    else if (cnt <= 8 * 32) raster_row_warp<8>(J, j, cnt, row, lane);
+    else if (lane == 0) {                            // big row: handled by k_raster_big
+        const int q = atomicAdd(&J.st->n_big, 1);
+        J.big_rows[q] = j;
+    }
+}
+
+// per job: the big rows, then d0, density table, background count, total
+// mass, fixed-point scale
+__global__ void __launch_bounds__(kRowThreads) k_density_table(const Job* __restrict__ jobs) {
     const Job& J = jobs[blockIdx.x];
     if (!J.st->active) return;
+    {
+        __shared__ RowShared rsh;
+        raster_big_rows(J, rsh);
+    }
     __shared__ double ss[32];
     __shared__ long long so[32];
     const int R = J.n_regions;
@@ -304,7 +407,7 @@ __global__ void k_density_table(const Job* __restrict__ jobs) {
     for (int v = threadIdx.x; v < R; v += blockDim.x) {
         const float sv = J.values[v];
         if (!(sv >= 0.0f) || isinf(sv)) bad = 1;           // values must be finite, >= 0
-        const int c = J.counts[v];
+        const int c = __ldcg(J.counts + v);
         if (c > 0) { s += (double)sv; o += c; }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&J.st->error, INIM_E_VALUE);
@@ -331,7 +434,7 @@ __global__ void k_density_table(const Job* __restrict__ jobs) {
     const bool empty = (sum_o == 0);
     const double d0 = empty ? 1.0 : sum_s / (double)sum_o;
     for (int v = threadIdx.x; v < R; v += blockDim.x) {
-        const int c = J.counts[v];
+        const int c = __ldcg(J.counts + v);
         J.dens[v] = (c > 0 && !empty) ? (float)((double)J.values[v] / ((double)c * d0)) : 0.0f;
     }
     if (threadIdx.x == 0) {
@@ -352,12 +455,29 @@ __global__ void k_density_table(const Job* __restrict__ jobs) {
 
 }  // namespace
 
-cudaError_t launch_raster(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& job_blocks,
-                          const BlockMap& row_blocks, cudaStream_t s) {
-    if (edge_blocks.n_blocks) k_row_hist<<<edge_blocks.n_blocks, 256, 0, s>>>(d_jobs, edge_blocks.d_map);
-    k_row_offsets<<<job_blocks.n_blocks, 1024, 0, s>>>(d_jobs);
+cudaError_t raster_setup(int max_n) {
+    // the largest row buffer any batch needs (N = 4096); set once
+    (void)max_n;
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const int bytes = kWarpsPerBlock * (1 << kMaxLog2) * 2;
+    cudaError_t e = cudaFuncSetAttribute(k_raster_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+cudaError_t launch_raster_prologue(const Job* d_jobs, const BlockMap& edge_blocks, cudaStream_t s) {
+    if (edge_blocks.n_blocks) k_raster_prologue<<<edge_blocks.n_blocks, 256, 0, s>>>(d_jobs, edge_blocks.d_map);
+    return cudaGetLastError();
+}
+
+// crossings + rows; the histogram and offsets must be in place (prologue or
+// the previous iteration's area kernel); big rows finish in the density kernel
+cudaError_t launch_raster_main(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& row_blocks,
+                               int max_n, cudaStream_t s) {
     if (edge_blocks.n_blocks) k_crossings<<<edge_blocks.n_blocks, 256, 0, s>>>(d_jobs, edge_blocks.d_map);
-    k_raster_rows<<<row_blocks.n_blocks, kRowThreads, 0, s>>>(d_jobs, row_blocks.d_map);
+    k_raster_rows<<<row_blocks.n_blocks, kWarpsPerBlock * 32, kWarpsPerBlock * max_n * 2, s>>>(d_jobs,
+                                                                                            row_blocks.d_map);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,8 @@ struct AccF32 {
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
     static __device__ __forceinline__ float ratio(T a, T c) { return a / c; }
+    static __device__ __forceinline__ double inv(T c) { return (double)(1.0f / c); }
+    static __device__ __forceinline__ float scale(T a, double inv_c) { return a * (float)inv_c; }
 };
 
 struct AccFix {   // 64-bit fixed point, exact sums
@@ -55,6 +57,8 @@ struct AccFix {   // 64-bit fixed point, exact sums
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
     static __device__ __forceinline__ float ratio(T a, T c) { return (float)((double)a / (double)c); }
+    static __device__ __forceinline__ double inv(T c) { return 1.0 / (double)c; }
+    static __device__ __forceinline__ float scale(T a, double inv_c) { return (float)((double)a * inv_c); }
 };
 
 struct AccKahan {   // compensated float pairs: value = hi + lo
@@ -78,11 +82,47 @@ struct AccKahan {   // compensated float pairs: value = hi + lo
     static __device__ __forceinline__ float ratio(T a, T c) {
         return (float)(((double)a.x + (double)a.y) / ((double)c.x + (double)c.y));
     }
+    static __device__ __forceinline__ double inv(T c) { return 1.0 / ((double)c.x + (double)c.y); }
+    static __device__ __forceinline__ float scale(T a, double inv_c) {
+        return (float)(((double)a.x + (double)a.y) * inv_c);
+    }
 };
 
 // ---------------------------------------------------------------------------
 // density source: labels + per-region table, or a given float texture
 // ---------------------------------------------------------------------------
+// raw labels of CPT columns (packed u16 pairs)
+template <int CPT>
+struct LabelWords { unsigned w[(CPT + 1) / 2]; };
+
+template <int CPT>
+__device__ __forceinline__ LabelWords<CPT> load_labels(const Job& J, int j, int i0) {
+    LabelWords<CPT> L;
+    const uint16_t* src = J.labels + (size_t)j * J.n + i0;
+    if constexpr (CPT == 8) {
+        const uint4 v = *reinterpret_cast<const uint4*>(src);
+        L.w[0] = v.x; L.w[1] = v.y; L.w[2] = v.z; L.w[3] = v.w;
+    } else if constexpr (CPT == 4) {
+        const uint2 v = *reinterpret_cast<const uint2*>(src);
+        L.w[0] = v.x; L.w[1] = v.y;
+    } else if constexpr (CPT == 2) {
+        L.w[0] = *reinterpret_cast<const unsigned*>(src);
+    } else {
+        L.w[0] = src[0];
+    }
+    return L;
+}
+
+template <int CPT>
+__device__ __forceinline__ void labels_to_density(const LabelWords<CPT>& L, const float* __restrict__ table,
+                                                  float (&d)[CPT]) {
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const unsigned lab = (k & 1) ? (L.w[k >> 1] >> 16) : (L.w[k >> 1] & 0xffffu);
+        d[k] = table[lab];
+    }
+}
+
 template <int CPT>
 __device__ __forceinline__ void load_density(const Job& J, const float* __restrict__ dtex, int j,
                                              int i0, float (&d)[CPT]) {
@@ -140,11 +180,32 @@ __device__ __forceinline__ void store_row(typename Acc::T* dst, const typename A
     }
 }
 
+// interleaved (S, T) pairs of CPT pixels
+template <class Acc, int CPT>
+__device__ __forceinline__ void store_row_pairs(typename Acc::T* dst, const typename Acc::T (&a)[CPT],
+                                                const typename Acc::T (&b)[CPT]) {
+    using T = typename Acc::T;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < CPT; k += 2)
+            reinterpret_cast<float4*>(dst)[k / 2] = make_float4(a[k], b[k], a[k + 1], b[k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            T pair[2] = {a[k], b[k]};
+            reinterpret_cast<uint4*>(dst)[k] = *reinterpret_cast<const uint4*>(pair);
+        }
+    }
+}
+
+constexpr int kDensSmem = 4096;     // region tables up to this size live in shared memory
+
 template <class Acc, int NT>
 struct ScanShared {
     typename Acc::T wtot[2][NT / 32];
     typename Acc::T e1first[2][NT];
     typename Acc::T e2last[2][NT];
+    float dens[kDensSmem];
 };
 
 // phase 1 (PHASE == 1) or phase 3 (PHASE == 3) of one band
@@ -194,18 +255,40 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
 
     T* Sout = reinterpret_cast<T*>(J.S);
     T* Tout = reinterpret_cast<T*>(J.T);
+    T* STout = reinterpret_cast<T*>(J.ST);
     T* Aout = reinterpret_cast<T*>(J.A);
     T* Bout = reinterpret_cast<T*>(J.B);
     T* RCout = reinterpret_cast<T*>(J.rowcum);
 
+    // density source: a given texture, or labels through the region table
+    // (in shared memory when it fits); labels are loaded two rows ahead
+    const bool from_labels = (dtex == nullptr);
+    const float* table = J.dens;
+    if (from_labels && J.n_regions + 1 <= kDensSmem) {
+        for (int v = tid; v <= J.n_regions; v += NT) sh.dens[v] = J.dens[v];
+        table = sh.dens;
+        __syncthreads();
+    }
+    LabelWords<CPT> lw0{}, lw1{};
     float dn[CPT];
-    load_density<CPT>(J, dtex, j0, i0, dn);
+    if (from_labels) {
+        lw0 = load_labels<CPT>(J, j0, i0);
+        if (rows > 1) lw1 = load_labels<CPT>(J, j0 + 1, i0);
+    } else {
+        load_density<CPT>(J, dtex, j0, i0, dn);
+    }
     for (int r = 0; r < rows; ++r) {
         const int j = j0 + r;
         float d[CPT];
+        if (from_labels) {
+            labels_to_density<CPT>(lw0, table, d);
+            lw0 = lw1;
+            if (r + 2 < rows) lw1 = load_labels<CPT>(J, j + 2, i0);
+        } else {
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) d[k] = dn[k];
-        if (r + 1 < rows) load_density<CPT>(J, dtex, j + 1, i0, dn);   // prefetch
+            for (int k = 0; k < CPT; ++k) d[k] = dn[k];
+            if (r + 1 < rows) load_density<CPT>(J, dtex, j + 1, i0, dn);   // prefetch
+        }
 
         // thread-local inclusive prefix
         T p[CPT];
@@ -257,8 +340,12 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
 
         if constexpr (PHASE == 3) {
             const size_t rowbase = (size_t)j * n + i0;
-            store_row<Acc, CPT>(Sout + rowbase, Sacc);
-            store_row<Acc, CPT>(Tout + rowbase, Tv);
+            if (STout) {
+                store_row_pairs<Acc, CPT>(STout + 2 * rowbase, Sacc, Tv);
+            } else {
+                store_row<Acc, CPT>(Sout + rowbase, Sacc);
+                store_row<Acc, CPT>(Tout + rowbase, Tv);
+            }
             if (tid == 0) Aout[j] = Acc::add(E1[0], w1[0]);                      // A(j) = E1(0, j)
             if (tid == NT - 1) {
                 RCout[j] = Sacc[CPT - 1];                                       // S(N-1, j)
@@ -296,9 +383,19 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
     }
 }
 
-// phase 2: carries.  Index space per job: [0, n) S columns, then E1
-// diagonals q = x + b H in [0, n + (nb-1) H), then E2 diagonals
-// q = x - b H + (nb-1) H in [0, n + (nb-1) H).
+// phase 2: carries.  Each carry is an exclusive prefix sum over the bands b'
+// of a value that depends only on (b', q):
+//   Sc_b(i)  = sum_{b'<b} aggS_{b'}(i)                                  q = i
+//   E1c_b(x) = sum_{b'<b} f1(b', q - (b'+1) H),  x = q - b H,  f1(b', x') =
+//              aggE1_{b'}(x') for x' < N, else the band's row-sum total
+//   E2c_b(x) = sum_{b'<b} f2(b', q + (b'+1) H),  x = q + b H,  f2 = aggE2 or 0
+// One thread per q walks the bands in order; the loads of kU bands are
+// issued together before their sums so that they overlap.
+constexpr int kCarryU = 16;
+__host__ __device__ __forceinline__ int carry_qspace(int n, int nb, int H) {
+    return n + 2 * (n + (nb - 1) * H);
+}
+
 template <class Acc>
 __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs,
                                                     const int2* __restrict__ bmap) {
@@ -309,51 +406,44 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
     const int n = J.n, H = J.H, nb = J.nb;
     const int span = n + (nb - 1) * H;
     int q = m.y * blockDim.x + threadIdx.x;
+    int kind;
+    if (q < n) kind = 0;
+    else if ((q -= n) < span) kind = 1;
+    else if ((q -= span) < span) { kind = 2; q -= (nb - 1) * H; }
+    else return;
     const T* agg = reinterpret_cast<const T*>(J.agg);
-    T* carry = reinterpret_cast<T*>(J.carry);
+    const T* a = agg + (size_t)kind * nb * n;
     const T* aS = agg;
-    const T* a1 = agg + (size_t)nb * n;
-    const T* a2 = agg + (size_t)2 * nb * n;
-    T* cS = carry;
-    T* c1 = carry + (size_t)nb * n;
-    T* c2 = carry + (size_t)2 * nb * n;
-    if (q < n) {
-        T acc = Acc::zero();
-        for (int b = 0; b < nb; ++b) {
-            cS[(size_t)b * n + q] = acc;
-            acc = Acc::add(acc, aS[(size_t)b * n + q]);
+    T* c = reinterpret_cast<T*>(J.carry) + (size_t)kind * nb * n;
+    T acc = Acc::zero();
+    for (int b0 = 0; b0 < nb; b0 += kCarryU) {
+        T v[kCarryU];
+#pragma unroll
+        for (int u = 0; u < kCarryU; ++u) {
+            const int b = b0 + u;
+            T g = Acc::zero();
+            if (b < nb) {
+                if (kind == 0) {
+                    g = a[(size_t)b * n + q];
+                } else if (kind == 1) {
+                    const int xp = q - (b + 1) * H;
+                    if (xp >= n) g = aS[(size_t)b * n + (n - 1)];
+                    else if (xp >= 0) g = a[(size_t)b * n + xp];
+                } else {
+                    const int xp = q + (b + 1) * H;
+                    if (xp >= 0 && xp < n) g = a[(size_t)b * n + xp];
+                }
+            }
+            v[u] = g;
         }
-        return;
-    }
-    q -= n;
-    if (q < span) {                     // E1 chain: x_b = q - b H
-        T acc = Acc::zero();
-        T rc = Acc::zero();              // rowcum at the row above band b
-        for (int b = 0; b < nb; ++b) {
-            const int x = q - b * H;
-            if (x >= n) acc = rc;
-            else c1[(size_t)b * n + x] = acc;
-            const int xn = x - H;
-            if (xn < 0) break;
-            const T bandrc = aS[(size_t)b * n + (n - 1)];
-            const T loc = xn < n ? a1[(size_t)b * n + xn] : bandrc;
-            acc = Acc::add(loc, acc);
-            rc = Acc::add(rc, bandrc);
-        }
-        return;
-    }
-    q -= span;
-    if (q < span) {                     // E2 chain: x_b = q - (nb-1) H + b H
-        const int qq = q - (nb - 1) * H;
-        T acc = Acc::zero();
-        for (int b = 0; b < nb; ++b) {
-            const int x = qq + b * H;
-            if (x < 0) acc = Acc::zero();
-            else c2[(size_t)b * n + x] = acc;
-            const int xn = x + H;
-            if (xn >= n) break;
-            const T loc = xn >= 0 ? a2[(size_t)b * n + xn] : Acc::zero();
-            acc = Acc::add(loc, acc);
+#pragma unroll
+        for (int u = 0; u < kCarryU; ++u) {
+            const int b = b0 + u;
+            if (b < nb) {
+                const int x = kind == 0 ? q : (kind == 1 ? q - b * H : q + b * H);
+                if (x >= 0 && x < n) c[(size_t)b * n + x] = acc;
+                acc = Acc::add(acc, v[u]);
+            }
         }
     }
 }

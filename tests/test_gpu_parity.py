@@ -9,7 +9,8 @@ Tolerances (derived in the design notes):
   KAHAN integral images |err| <= 1e-10 * C
   displacement          3e-5 (FP32 sums), 1e-6 (FIX64 / KAHAN)
   one iteration         max |dp| <= 1e-5 of the map extent
-  N iterations          max |dp| <= 1e-4 of the map extent, areas <= 1e-4 relative
+  N iterations          max |dp| <= 1e-4 of the map extent, areas <= 1e-4 of the
+                        mean region area
 """
 import numpy as np
 import pytest
@@ -207,7 +208,16 @@ def test_areas():
     a = torch.empty(mesh.n_regions, dtype=torch.float64, device="cuda")
     P.inim_areas(m, dev(xy), a)
     want = O.signed_areas(xy.astype(np.float64), *arrays(mesh))
-    np.testing.assert_allclose(a.cpu().numpy(), want, rtol=1e-12, atol=1e-15)
+    # compensated FP32 sums of exact products: error <= (edges per lane + 2)
+    # * 2^-47 * sum over the region's edges of |x_a y_b| + |x_b y_a|
+    x = xy.astype(np.float64)
+    bound = np.zeros(mesh.n_regions)
+    for r in range(mesh.n_rings):
+        idx = mesh.ring_idx[mesh.ring_off[r]:mesh.ring_off[r + 1]]
+        nxt = np.roll(idx, -1)
+        mag = np.abs(x[idx, 0] * x[nxt, 1]) + np.abs(x[nxt, 0] * x[idx, 1])
+        bound[mesh.ring_region[r]] += (len(idx) / 32 + 2) * 2.0 ** -47 * mag.sum()
+    assert (np.abs(a.cpu().numpy() - want) <= bound + 1e-16).all()
 
 
 @pytest.mark.parametrize("shape", [0.25, 0.5, 0.75])
@@ -258,10 +268,15 @@ def test_trajectory_single_step_config():
         P.inim_iterate(m, x, dev(vals), p, 1)
         ora, _ = O.iterate(ora, arrays(mesh), vals.astype(np.float64), k, 0.5, t0=t0)
     g = x.cpu().numpy()
-    assert np.abs(g - ora).max() <= 1e-4 * EXTENT
+    dp = np.abs(g - ora).max()
+    assert dp <= 1e-4 * EXTENT, dp
     ga = O.signed_areas(g.astype(np.float64), *arrays(mesh))
     oa = O.signed_areas(ora, *arrays(mesh))
-    assert (np.abs(ga - oa) / np.abs(oa)).max() <= 1e-4
+    # area errors relative to the mean region area: a region's area moves by at
+    # most (its perimeter) x (vertex error), so a bound relative to its own area
+    # would be tighter than the vertex bound for small regions
+    rel = np.abs(ga - oa).max() / np.abs(oa).mean()
+    assert rel <= 1e-4, (rel, dp)
 
 
 @pytest.mark.parametrize("precision", [P.INIM_FIX64, P.INIM_KAHAN])
@@ -354,3 +369,49 @@ def test_stop_rule_reports_consistent_errors():
     eps, xi = O.cartographic_errors(areas, desired)
     assert abs(eps - s["eps"]) <= 2e-3 and abs(xi - s["xi"]) <= 5e-3
     assert s["foldover"] == 0 and s["overlap"] == 0
+
+
+# ---------------------------------------------------------------------------
+# A8: scan tiles and the autotuner
+# ---------------------------------------------------------------------------
+TILES_1024 = [(h, c, t) for h in (4, 8, 16, 32, 64) for (c, t) in ((8, 128), (4, 256))]
+
+
+@pytest.mark.parametrize("tile", TILES_1024)
+def test_every_scan_tile_is_exact_in_fixed_point(tile):
+    k = 10
+    d = texture(k, 77)
+    q = np.rint(d.astype(np.float64) * 2.0 ** 30).astype(np.int64)
+    I = O.inims(q)
+    try:
+        P.inim_set_scan_tile(k, P.INIM_FIX64, 0, *tile)
+        S, T, A, B = gpu_inims(d, k, P.INIM_FIX64, 30)
+    finally:
+        P.inim_set_scan_tile(k, P.INIM_FIX64, 0, 0, 0, 0)
+    np.testing.assert_array_equal(S, I["a"])
+    np.testing.assert_array_equal(T, I["at"])
+    np.testing.assert_array_equal(A, I["A"])
+    np.testing.assert_array_equal(B, I["B"])
+
+
+def test_autotuner_picks_a_valid_tile_and_stays_on_the_oracle():
+    w = synth.single_step_workload()
+    mesh = w["mesh"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    p = P.params(log2_res=8, shape=0.5, max_iters=5, xi_stop=0.0, stall_window=0)
+    arr = (P.inim_job * 4)()
+    for q in range(4):
+        arr[q].map = m.handle
+        arr[q].values = vals.ctypes.data
+        arr[q].params = p
+    try:
+        P.inim_autotune_scan(arr, reps=3)
+        t = P.inim_get_scan_tile(8, P.INIM_FP32, 0)
+        assert t["band_rows"] in (4, 8, 16, 32, 64) and t["cols_per_thread"] * t["threads"] == 256
+        out, _, _ = P.inim_run(m, vals[None], p)
+    finally:
+        P.inim_set_scan_tile(8, P.INIM_FP32, 0, 0, 0, 0)
+    ora, _ = O.run(mesh.with_verts(mesh.verts_f32().astype(np.float64)), vals[None].astype(np.float64), 8,
+                   shape=0.5, max_iters=5, xi_stop=0, stall_window=0)
+    assert np.abs(out[0] - ora[0]).max() <= 1e-4 * EXTENT
