@@ -178,22 +178,30 @@ def main():
         return arr
 
     def make_plan(vals_buf, out_direct, out_cum, stride):
-        """ctypes job arrays of one step over the given buffers (device or pinned host)."""
+        """The sweep as one inim_run_series call (3 direct + 3 cumulative series)
+        over the given buffers (device or pinned host), plus job arrays of the
+        two batch shapes for the autotuner and the stage profile."""
         vp = lambda t: vals_buf.data_ptr() + t * R * 4                    # noqa: E731
         op = lambda buf, q: buf.data_ptr() + q * V * 2 * 4                 # noqa: E731
+        ser = (P.inim_series * (2 * len(SHAPES)))()
+        for q, (mode, buf) in enumerate(((P.INIM_DIRECT, out_direct), (P.INIM_CUMULATIVE, out_cum))):
+            for s_, sh in enumerate(SHAPES):
+                x = ser[q * len(SHAPES) + s_]
+                x.map = m.handle
+                x.values = vp(0)
+                x.T = T_STEPS
+                x.init_xy = None
+                x.out_xy = op(buf, s_ * T_STEPS)
+                x.params = prm(sh, mode=mode)
+                x.stats = None
         direct = job_array([(vp(t), None, op(out_direct, s * T_STEPS + t), prm(sh))
                             for s, sh in enumerate(SHAPES) for t in range(T_STEPS)])
-        rounds = []
-        for t in range(T_STEPS):
-            rounds.append(job_array([(vp(t), None if t == 0 else op(out_cum, s * T_STEPS + t - 1),
-                                      op(out_cum, s * T_STEPS + t), prm(sh)) for s, sh in enumerate(SHAPES)]))
-        return direct, rounds
+        small = job_array([(vp(0), None, op(out_cum, s * T_STEPS), prm(sh)) for s, sh in enumerate(SHAPES)])
+        return ser, direct, small
 
     def run_step(plan):
-        direct, rounds = plan
-        _lib.check(lib.inim_run_batch(direct, len(direct), None), "direct batch")
-        for r in rounds:
-            _lib.check(lib.inim_run_batch(r, len(r), None), "cumulative round")
+        ser = plan[0]
+        _lib.check(lib.inim_run_series(ser, len(ser), None), "sweep")
 
     # device-resident inputs and outputs
     vals_d = torch.as_tensor(vals, device=dev).contiguous()
@@ -202,8 +210,8 @@ def main():
     plan_d = make_plan(vals_d, out_dir_d, out_cum_d, None)
 
     # scan tiles chosen by the autotuner on the two batch shapes of the step
-    P.inim_autotune_scan(plan_d[0], reps=5)
-    P.inim_autotune_scan(plan_d[1][0], reps=20)
+    P.inim_autotune_scan(plan_d[1], reps=5)
+    P.inim_autotune_scan(plan_d[2], reps=20)
     tiles = {cls: P.inim_get_scan_tile(k, P.INIM_FP32, large) for cls, large in (("large", 1), ("small", 0))}
 
     def barrier():
@@ -259,8 +267,8 @@ def main():
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_value = ITERS_PER_STEP * e_steps * world / float(e2e_t.item())
     n_sol = 2 * len(SHAPES) * T_STEPS
-    h2d = n_sol * R * 4 + len(SHAPES) * (T_STEPS - 1) * V * 8
-    d2h = n_sol * V * 8
+    h2d = n_sol * R * 4            # the values of every solve
+    d2h = n_sol * V * 8            # the vertices after every solve
 
     line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -278,7 +286,7 @@ def main():
     if rank == 0:
         # roofline of the dominant stage, measured on the 72-solve batch
         run_step(plan_d)
-        _lib.check(lib.inim_run_batch(plan_d[0], len(plan_d[0]), None), "direct batch")
+        _lib.check(lib.inim_run_batch(plan_d[1], len(plan_d[1]), None), "direct batch")
         stages = P.inim_profile_stages(reps=10)
         N = 1 << k
         Ppx = N * N
@@ -304,9 +312,24 @@ def main():
                             else "fallback"}
         line["stages_ms"] = stages
         line["stages_gbs"] = {s: algo[s] / (stages[s] / 1e3) / 1e9 for s in stages}
-        # the same stages on a 3-solve cumulative round (latency-bound sizes)
-        _lib.check(lib.inim_run_batch(plan_d[1][1], len(plan_d[1][1]), None), "cumulative round")
+        # the same stages (per-step kernels) on a 3-solve batch, latency-bound
+        _lib.check(lib.inim_run_batch(plan_d[2], len(plan_d[2]), None), "3-solve batch")
         line["stages_3solve_ms"] = P.inim_profile_stages(reps=20)
+        # the sweep with the cumulative series in one persistent launch instead
+        # (runs after the direct batch), with its phase times per iteration
+        P.inim_set_persistent(True)
+        run_step(plan_d)
+        torch.cuda.synchronize()
+        P.inim_persistent_phase_times(True)
+        t = time.perf_counter()
+        run_step(plan_d)
+        torch.cuda.synchronize()
+        pers_s = time.perf_counter() - t
+        ph = P.inim_persistent_phase_times(False)
+        P.inim_set_persistent(False)
+        line["persistent_variant"] = {
+            "value": ITERS_PER_STEP / pers_s, "unit": "iterations/s",
+            "phase_us_per_iteration": {k: 1e3 * v / (T_STEPS * ITERS) for k, v in ph.items()}}
 
     if rank == 0 and not args.no_extras:
         # plain unfused form on a bounded sample: 2 time steps x 3 shapes, direct

@@ -109,6 +109,17 @@ typedef struct {
     inim_step_stats* stats;    /* NULL or one host struct */
 } inim_job;
 
+/* One time series for inim_run_series. */
+typedef struct {
+    const inim_map* map;
+    const float*    values;    /* [T*n_regions] s_t(v); host or device */
+    int32_t         T;         /* time steps */
+    const float*    init_xy;   /* [n_verts*2] start vertices, NULL = the map's own; host or device */
+    float*          out_xy;    /* [T*n_verts*2] vertices after each step; host or device */
+    inim_params     params;    /* mode: INIM_DIRECT or INIM_CUMULATIVE; fused form */
+    inim_step_stats* stats;    /* NULL or [T] host structs */
+} inim_series;
+
 /* Defaults of Sec. 4.1: 1024^2, stop at xi < 0.01 / 32-iteration stall / 512 iterations. */
 void inim_params_default(inim_params* p);
 
@@ -162,6 +173,30 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
  * stop rule fires.
  */
 int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream);
+
+/*
+ * Many time series at once (Sec. 4.2 direct and cumulative modes).  Direct
+ * series run as independent solves of one batch; cumulative series run
+ * their steps in order, all series together.  Small FP32 batches (N <= 2048,
+ * fewer than 2^23 pixels in total) run in one persistent cooperative launch
+ * that covers every iteration and, for cumulative series, every time step;
+ * larger ones as CUDA graphs of the per-step kernels.  All series need the
+ * fused form and one precision.  inim_run is this call with one series.
+ */
+int inim_run_series(const inim_series* series, int32_t n_series, void* stream);
+
+/* Use (1, default) or skip (0) the persistent launch for small batches. */
+int inim_set_persistent(int32_t enable);
+
+/*
+ * Phase timing of persistent launches: while enabled, block 0 of the
+ * persistent kernel adds the time from one grid barrier to the next (its own
+ * work plus the wait for the slowest block) to 8 counters, one per phase of
+ * an iteration: crossings, rows, density, scan 1, carries, scan 3, gather,
+ * areas.  The call copies the counters (ms, n <= 8 entries, may be NULL),
+ * resets them and sets the switch.
+ */
+int inim_persistent_phase_times(int32_t enable, double* ms, int32_t n);
 
 /* ---------------- single steps of the iteration (device memory) -------- */
 

@@ -22,7 +22,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_FIX64, INIM_FORM_FUSED, INIM_FORM_PLAIN,  # noqa: F401
-                   INIM_FP32, INIM_KAHAN, InimError, inim_job, inim_params, inim_step_stats)
+                   INIM_FP32, INIM_KAHAN, InimError, inim_job, inim_params, inim_series, inim_step_stats)
 
 __all__ = [
     "params", "inim_params_default", "inim_status_string", "inim_map_create", "inim_map_destroy",
@@ -226,3 +226,52 @@ def inim_get_scan_tile(log2_res: int, precision: int = 0, large: int = 1):
 def inim_autotune_scan(job_array, reps: int = 5) -> None:
     """job_array: a ctypes (inim_job * n) array (see inim_run_batch)."""
     _lib.check(_lib.load().inim_autotune_scan(job_array, len(job_array), reps), "inim_autotune_scan")
+
+
+def inim_run_series(series, stream=None):
+    """series: list of dicts(map=Map, values [T, R], params, init_xy=None, out_xy=None).
+
+    Returns (list of out_xy [T, V, 2], list of stats lists, status)."""
+    lib = _lib.load()
+    n = len(series)
+    arr = (inim_series * n)()
+    keep, outs, stats = [], [], []
+    for k, x in enumerate(series):
+        vals = x["values"]
+        if isinstance(vals, np.ndarray) or not hasattr(vals, "data_ptr"):
+            vals = np.ascontiguousarray(np.atleast_2d(vals), dtype=np.float32)
+        T = int(vals.shape[0])
+        init = x.get("init_xy")
+        if init is not None and isinstance(init, np.ndarray):
+            init = np.ascontiguousarray(init, dtype=np.float32)
+        out = x.get("out_xy")
+        if out is None:
+            out = np.empty((T, x["map"].n_verts, 2), np.float32)
+        st = _stats_array(T)
+        keep += [vals, init]
+        outs.append(out)
+        stats.append(st)
+        arr[k].map = x["map"].handle
+        arr[k].values = _lib.ptr(vals)
+        arr[k].T = T
+        arr[k].init_xy = _lib.ptr(init)
+        arr[k].out_xy = _lib.ptr(out)
+        arr[k].params = x["params"]
+        arr[k].stats = st
+    status = _lib.check(lib.inim_run_series(arr, n, stream), "inim_run_series")
+    return outs, [[s.as_dict() for s in st] for st in stats], status
+
+
+def inim_set_persistent(enable: bool) -> None:
+    _lib.load().inim_set_persistent(1 if enable else 0)
+
+
+PERSISTENT_PHASES = ("crossings", "rows", "density", "scan_phase1", "scan_carry", "scan_phase3", "gather_move",
+                     "areas_errors")
+
+
+def inim_persistent_phase_times(enable: bool):
+    """Toggle phase timing of persistent launches; returns the ms per phase so far."""
+    ms = (ctypes.c_double * 8)()
+    _lib.check(_lib.load().inim_persistent_phase_times(1 if enable else 0, ms, 8), "inim_persistent_phase_times")
+    return dict(zip(PERSISTENT_PHASES, list(ms)))

@@ -65,6 +65,18 @@ class inim_job(ctypes.Structure):
     ]
 
 
+class inim_series(ctypes.Structure):
+    _fields_ = [
+        ("map", ctypes.c_void_p),
+        ("values", ctypes.c_void_p),
+        ("T", ctypes.c_int32),
+        ("init_xy", ctypes.c_void_p),
+        ("out_xy", ctypes.c_void_p),
+        ("params", inim_params),
+        ("stats", ctypes.POINTER(inim_step_stats)),
+    ]
+
+
 # name -> (restype, argtypes)
 _SIGS = {
     "inim_params_default": (None, [ctypes.POINTER(inim_params)]),
@@ -79,6 +91,9 @@ _SIGS = {
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(inim_step_stats),
                                 ctypes.c_void_p]),
     "inim_run_batch": (ctypes.c_int, [ctypes.POINTER(inim_job), ctypes.c_int32, ctypes.c_void_p]),
+    "inim_run_series": (ctypes.c_int, [ctypes.POINTER(inim_series), ctypes.c_int32, ctypes.c_void_p]),
+    "inim_set_persistent": (ctypes.c_int, [ctypes.c_int32]),
+    "inim_persistent_phase_times": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "inim_raster": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "inim_inims": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,

@@ -215,8 +215,34 @@ struct Batch {
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     std::vector<PlainWork> plain;   // per job (plain form only)
+    // persistent form: all resolution groups' band / carry items, barrier words,
+    // per-job round tables (time series), their device pointer arrays
+    BlockMap all_band, all_carry;
+    unsigned* d_bar = nullptr;
+    int* d_err = nullptr;
+    int round_cap = 0;                      // rounds the round buffers hold
+    std::vector<float*> round_vals;         // per job [round_cap][R]
+    std::vector<float2*> round_outs;        // per job [round_cap][V]
+    std::vector<JobState*> round_stats;     // per job [round_cap]
+    int* d_job_rounds = nullptr;
+    const float** d_round_vals = nullptr;
+    float2** d_round_outs = nullptr;
+    JobState** d_round_stats = nullptr;
+    JobState* d_round_init = nullptr;
+    long long total_px = 0;
+
+    void free_rounds() {
+        for (auto& p : round_vals) dfree(p);
+        for (auto& p : round_outs) dfree(p);
+        for (auto& p : round_stats) dfree(p);
+        round_vals.clear(); round_outs.clear(); round_stats.clear();
+        dfree(d_job_rounds); dfree(d_round_vals); dfree(d_round_outs); dfree(d_round_stats); dfree(d_round_init);
+        round_cap = 0;
+    }
 
     ~Batch() {
+        free_rounds();
+        dfree(d_bar); dfree(d_err); dfree(all_band.d_map); dfree(all_carry.d_map);
         if (graph) cudaGraphExecDestroy(graph);
         for (auto& b : bufs) b.release();
         for (auto& p : plain) plain_free(p);
@@ -295,7 +321,19 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
     CUDA_TRY(make_map(B.row_blocks, rb));
     CUDA_TRY(make_map(B.vert_blocks, vb));
     CUDA_TRY(make_map(B.region_blocks, gb));
-    // scan groups by resolution
+    // scan groups by resolution (and, for the persistent form, all of them)
+    std::vector<int2> all_band, all_carry;
+    for (int k = 0; k < nj; ++k) {
+        const Job& J = B.h_jobs[k];
+        B.total_px += (long long)J.n * J.n;
+        for (int b = 0; b < J.nb; ++b) all_band.push_back(make_int2(k, b));
+        const int len = carry_qspace(J.n, J.nb, J.H);
+        for (int q = 0; q < (len + 255) / 256; ++q) all_carry.push_back(make_int2(k, q));
+    }
+    CUDA_TRY(make_map(B.all_band, all_band));
+    CUDA_TRY(make_map(B.all_carry, all_carry));
+    CUDA_TRY(cudaMalloc(&B.d_bar, 2 * sizeof(unsigned)));
+    CUDA_TRY(cudaMalloc(&B.d_err, sizeof(int)));
     for (int l = kMinLog2; l <= kMaxLog2; ++l) {
         std::vector<int2> band, carry;
         for (int k = 0; k < nj; ++k) {
@@ -443,6 +481,79 @@ JobState initial_state(const inim_params& p, int stop_on_rule, int max_iters) {
     return st;
 }
 
+// persistent form: small FP32 batches of textures up to 2048^2
+int g_persistent = 0;                         // off by default: see inim_set_persistent
+int g_phase_profile = 0;                      // record per-phase time of persistent runs
+unsigned long long* g_phase_ns = nullptr;     // device [8]
+
+bool persistent_ok(const Batch& B) {
+    return g_persistent && B.precision == INIM_FP32 && B.max_n <= 2048 && B.total_px < (1LL << 23) &&
+           B.spec[0].map != nullptr;
+}
+
+int ensure_rounds(Batch& B, int rounds) {
+    if (B.round_cap >= rounds && (int)B.round_vals.size() == (int)B.spec.size()) return INIM_OK;
+    B.free_rounds();
+    const int nj = (int)B.spec.size();
+    B.round_vals.assign(nj, nullptr);
+    B.round_outs.assign(nj, nullptr);
+    B.round_stats.assign(nj, nullptr);
+    for (int k = 0; k < nj; ++k) {
+        const Job& J = B.h_jobs[k];
+        CUDA_TRY(cudaMalloc(&B.round_vals[k], (size_t)rounds * J.n_regions * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&B.round_outs[k], (size_t)rounds * J.n_verts * sizeof(float2)));
+        CUDA_TRY(cudaMalloc(&B.round_stats[k], (size_t)rounds * sizeof(JobState)));
+    }
+    CUDA_TRY(cudaMalloc(&B.d_job_rounds, nj * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&B.d_round_vals, nj * sizeof(float*)));
+    CUDA_TRY(cudaMalloc(&B.d_round_outs, nj * sizeof(float2*)));
+    CUDA_TRY(cudaMalloc(&B.d_round_stats, nj * sizeof(JobState*)));
+    CUDA_TRY(cudaMalloc(&B.d_round_init, nj * sizeof(JobState)));
+    CUDA_TRY(cudaMemcpy(B.d_round_vals, B.round_vals.data(), nj * sizeof(float*), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(B.d_round_outs, B.round_outs.data(), nj * sizeof(float2*), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(B.d_round_stats, B.round_stats.data(), nj * sizeof(JobState*), cudaMemcpyHostToDevice));
+    B.round_cap = rounds;
+    return INIM_OK;
+}
+
+// One cooperative launch for every iteration (and every time step when
+// rounds > 1) of the batch.  Values of round 0 must be in the jobs' value
+// buffers, later rounds in round_vals; states (round 0) must be uploaded;
+// h_states gets the final state of each job.
+int run_persistent(Batch& B, int iters, int rounds, const std::vector<int>& job_rounds) {
+    const int nj = (int)B.spec.size();
+    int st = ensure_rounds(B, rounds);
+    if (st != INIM_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(B.d_job_rounds, job_rounds.data(), nj * sizeof(int), cudaMemcpyHostToDevice, B.stream));
+    CUDA_TRY(cudaMemcpyAsync(B.d_round_init, B.h_states.data(), nj * sizeof(JobState), cudaMemcpyHostToDevice,
+                             B.stream));
+    CUDA_TRY(launch_persistent(B.d_jobs, nj, B.edge_blocks, B.row_blocks, B.all_band, B.all_carry, B.vert_blocks,
+                               B.region_blocks, iters, rounds, B.d_job_rounds, B.d_round_vals,
+                               reinterpret_cast<float2* const*>(B.d_round_outs), B.d_round_init,
+                               B.d_round_stats, B.d_bar, B.d_err, B.max_n, 0,
+                               g_phase_profile ? g_phase_ns : nullptr, B.stream));
+    g_launches += 1;
+    int err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, B.d_err, sizeof(int), cudaMemcpyDeviceToHost, B.stream));
+    CUDA_TRY(cudaMemcpyAsync(B.h_states.data(), B.d_states, nj * sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
+    CUDA_TRY(cudaStreamSynchronize(B.stream));
+    if (err) return fail(err, "persistent kernel: a grid barrier wait hit its cap");
+    return INIM_OK;
+}
+
+// enqueue a fixed-iteration run of the batch (graph replays) without waiting
+int enqueue_fused_async(Batch& B, int max_iters) {
+    int st = ensure_graph(B);
+    if (st != INIM_OK) return st;
+    CUDA_TRY(enqueue_prologue(B, B.stream));
+    g_launches += B.edge_blocks.n_blocks ? 1 : 0;
+    for (int done = 0; done < max_iters; done += B.graph_iters) {
+        CUDA_TRY(cudaGraphLaunch(B.graph, B.stream));
+        g_launches += (long long)B.graph_iters * kernels_per_fused_iteration(B);
+    }
+    return INIM_OK;
+}
+
 bool needs_poll(const inim_params& p) {
     return p.xi_stop > 0.0f || p.eps_stop > 0.0f || p.stall_window > 0;
 }
@@ -450,6 +561,7 @@ bool needs_poll(const inim_params& p) {
 // run the fused form until every job stopped; states must be uploaded
 int run_fused(Batch& B, int max_iters, bool poll) {
     const int nj = (int)B.spec.size();
+    if (persistent_ok(B)) return run_persistent(B, max_iters, 1, std::vector<int>(nj, 1));
     int st = ensure_graph(B);
     if (st != INIM_OK) return st;
     CUDA_TRY(enqueue_prologue(B, B.stream));
@@ -543,6 +655,163 @@ int fill_stats(const JobState& s, inim_step_stats* out) {
 int worst(int a, int b) {
     if (a < 0 || b < 0) return std::min(a, b);
     return std::max(a, b);
+}
+
+// Many time series at once (the fused form).  Direct series become T
+// independent jobs of one batch; cumulative series become one job each with T
+// rounds, run in one persistent launch when the batch is small enough, else
+// round by round.
+int run_series_impl(const inim_series* S, int n) {
+    int result = INIM_OK;
+    struct Ref { int series, t; };
+    std::vector<JobSpec> dspec, cspec;
+    std::vector<Ref> dref, cref;
+    std::vector<const float*> dcap, ccap;
+    for (int i = 0; i < n; ++i) {
+        const inim_series& x = S[i];
+        const JobSpec sp{x.map, x.params.log2_res, x.params.precision};
+        if (x.params.mode == INIM_DIRECT) {
+            for (int t = 0; t < x.T; ++t) {
+                dspec.push_back(sp); dref.push_back({i, t}); dcap.push_back(x.map->h_xy0.data());
+            }
+        } else {
+            cspec.push_back(sp); cref.push_back({i, 0}); ccap.push_back(x.map->h_xy0.data());
+        }
+    }
+    int st = INIM_OK;
+    auto setup_job = [&](Batch& B, int k, const inim_series& x, int t, bool reset_xy) -> int {
+        Job& J = B.h_jobs[k];
+        J.lam = 1.0f - x.params.shape;
+        J.bdv_scale = x.params.bdv_scale;
+        const int R = x.map->n_regions, V = x.map->n_verts;
+        CUDA_TRY(cudaMemcpyAsync(B.bufs[k].values, x.values + (size_t)t * R, (size_t)R * 4, cudaMemcpyDefault, B.stream));
+        if (reset_xy)
+            CUDA_TRY(cudaMemcpyAsync(B.bufs[k].xy, x.init_xy ? x.init_xy : (const float*)x.map->xy0, (size_t)V * 8,
+                                     cudaMemcpyDefault, B.stream));
+        B.h_states[k] = initial_state(x.params, 1, x.params.max_iters);
+        return INIM_OK;
+    };
+    // The direct batch (bandwidth-bound) and the cumulative chain (latency-
+    // bound) are independent: when the direct batch needs no host polling it
+    // is enqueued on its own stream and runs while the cumulative rounds
+    // proceed on theirs.
+    Batch* D = nullptr;
+    bool d_async = false;
+    if (!dspec.empty()) {
+        D = get_batch(dspec, dcap, &st);
+        if (!D) return st;
+        int max_it = 1;
+        bool poll = false;
+        for (int k = 0; k < (int)dspec.size(); ++k) {
+            const inim_series& x = S[dref[k].series];
+            st = setup_job(*D, k, x, dref[k].t, true);
+            if (st != INIM_OK) return st;
+            max_it = std::max(max_it, x.params.max_iters);
+            poll |= needs_poll(x.params);
+        }
+        CUDA_TRY(cudaMemcpyAsync(D->d_jobs, D->h_jobs.data(), dspec.size() * sizeof(Job), cudaMemcpyHostToDevice, D->stream));
+        CUDA_TRY(cudaMemcpyAsync(D->d_states, D->h_states.data(), dspec.size() * sizeof(JobState),
+                                 cudaMemcpyHostToDevice, D->stream));
+        d_async = !poll && !cspec.empty() && !persistent_ok(*D);
+        if (d_async) st = enqueue_fused_async(*D, max_it);
+        else st = run_fused(*D, max_it, poll);
+        if (st != INIM_OK) return st;
+    }
+    auto collect_direct = [&]() -> int {
+        if (!D) return INIM_OK;
+        if (d_async) {
+            CUDA_TRY(cudaMemcpyAsync(D->h_states.data(), D->d_states, dspec.size() * sizeof(JobState),
+                                     cudaMemcpyDeviceToHost, D->stream));
+        }
+        for (int k = 0; k < (int)dspec.size(); ++k) {
+            const inim_series& x = S[dref[k].series];
+            const int V = x.map->n_verts, t = dref[k].t;
+            CUDA_TRY(cudaMemcpyAsync(x.out_xy + (size_t)t * V * 2, D->bufs[k].xy, (size_t)V * 8, cudaMemcpyDefault,
+                                     D->stream));
+        }
+        CUDA_TRY(cudaStreamSynchronize(D->stream));
+        for (int k = 0; k < (int)dspec.size(); ++k) {
+            const inim_series& x = S[dref[k].series];
+            result = worst(result, fill_stats(D->h_states[k], x.stats ? x.stats + dref[k].t : nullptr));
+        }
+        return INIM_OK;
+    };
+    if (!d_async) {
+        st = collect_direct();
+        if (st != INIM_OK) return st;
+    }
+    if (!cspec.empty()) {
+        Batch* B = get_batch(cspec, ccap, &st);
+        if (!B) return st;
+        const int nc = (int)cspec.size();
+        int rounds = 1, max_it = 1;
+        bool poll = false;
+        std::vector<int> job_rounds(nc);
+        for (int k = 0; k < nc; ++k) {
+            const inim_series& x = S[cref[k].series];
+            job_rounds[k] = x.T;
+            rounds = std::max(rounds, x.T);
+            max_it = std::max(max_it, x.params.max_iters);
+            poll |= needs_poll(x.params);
+            st = setup_job(*B, k, x, 0, true);
+            if (st != INIM_OK) return st;
+        }
+        if (persistent_ok(*B)) {
+            st = ensure_rounds(*B, rounds);
+            if (st != INIM_OK) return st;
+            for (int k = 0; k < nc; ++k) {
+                const inim_series& x = S[cref[k].series];
+                CUDA_TRY(cudaMemcpyAsync(B->round_vals[k], x.values, (size_t)x.T * x.map->n_regions * 4,
+                                         cudaMemcpyDefault, B->stream));
+            }
+            CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), nc * sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+            CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), nc * sizeof(JobState), cudaMemcpyHostToDevice,
+                                     B->stream));
+            st = run_persistent(*B, max_it, rounds, job_rounds);
+            if (st != INIM_OK) return st;
+            std::vector<JobState> rs(rounds);
+            for (int k = 0; k < nc; ++k) {
+                const inim_series& x = S[cref[k].series];
+                const int V = x.map->n_verts;
+                CUDA_TRY(cudaMemcpyAsync(x.out_xy, B->round_outs[k], (size_t)x.T * V * 8, cudaMemcpyDefault, B->stream));
+                CUDA_TRY(cudaMemcpyAsync(rs.data(), B->round_stats[k], (size_t)x.T * sizeof(JobState),
+                                         cudaMemcpyDeviceToHost, B->stream));
+                CUDA_TRY(cudaStreamSynchronize(B->stream));
+                for (int t = 0; t < x.T; ++t) result = worst(result, fill_stats(rs[t], x.stats ? x.stats + t : nullptr));
+            }
+        } else {
+            for (int t = 0; t < rounds; ++t) {
+                for (int k = 0; k < nc; ++k) {
+                    const inim_series& x = S[cref[k].series];
+                    if (t > 0 && t < x.T) {
+                        st = setup_job(*B, k, x, t, false);
+                        if (st != INIM_OK) return st;
+                    } else if (t >= x.T) {
+                        B->h_states[k].active = 0;
+                    }
+                }
+                CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), nc * sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+                CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), nc * sizeof(JobState), cudaMemcpyHostToDevice,
+                                         B->stream));
+                st = run_fused(*B, max_it, poll);
+                if (st != INIM_OK) return st;
+                for (int k = 0; k < nc; ++k) {
+                    const inim_series& x = S[cref[k].series];
+                    if (t >= x.T) continue;
+                    const int V = x.map->n_verts;
+                    CUDA_TRY(cudaMemcpyAsync(x.out_xy + (size_t)t * V * 2, B->bufs[k].xy, (size_t)V * 8,
+                                             cudaMemcpyDefault, B->stream));
+                    result = worst(result, fill_stats(B->h_states[k], x.stats ? x.stats + t : nullptr));
+                }
+                CUDA_TRY(cudaStreamSynchronize(B->stream));
+            }
+        }
+    }
+    if (d_async) {
+        st = collect_direct();
+        if (st != INIM_OK) return st;
+    }
+    return result;
 }
 
 }  // namespace
@@ -714,6 +983,10 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
     std::lock_guard<std::mutex> lk(g_cache_mu);
     const bool direct = params->mode == INIM_DIRECT;
     const bool plain = params->form == INIM_FORM_PLAIN;
+    if (!plain) {       // the fused form: one series
+        inim_series x{map, values, T, init_xy, out_xy, *params, stats};
+        return run_series_impl(&x, 1);
+    }
     const int nj = (direct && !plain) ? T : 1;
     std::vector<JobSpec> spec(nj, JobSpec{map, params->log2_res, params->precision});
     std::vector<const float*> starts(nj, map->h_xy0.data());
@@ -749,6 +1022,42 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
     return result;
 }
 
+int inim_run_series(const inim_series* S, int32_t n, void* stream) {
+    if (!S || n < 1) return fail(INIM_E_ARG, "no series");
+    for (int i = 0; i < n; ++i) {
+        const inim_series& x = S[i];
+        if (!x.map || !x.values || !x.out_xy || x.T < 1) return fail(INIM_E_ARG, "series with NULL map/values/out or T < 1");
+        int st = check_params(&x.params);
+        if (st != INIM_OK) return st;
+        if (x.params.form != INIM_FORM_FUSED) return fail(INIM_E_ARG, "inim_run_series needs the fused form");
+        if (x.params.precision != S[0].params.precision) return fail(INIM_E_ARG, "all series need one precision");
+        if (!is_device_ptr(x.values)) {
+            st = check_values(x.values, (size_t)x.T * x.map->n_regions);
+            if (st != INIM_OK) return st;
+        }
+    }
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    return run_series_impl(S, n);
+}
+
+int inim_set_persistent(int32_t enable) {
+    g_persistent = enable ? 1 : 0;
+    return INIM_OK;
+}
+
+int inim_persistent_phase_times(int32_t enable, double* ms, int32_t n) {
+    if (enable && !g_phase_ns) CUDA_TRY(cudaMalloc(&g_phase_ns, 8 * sizeof(unsigned long long)));
+    if (g_phase_ns && ms && n > 0) {
+        unsigned long long h[8];
+        CUDA_TRY(cudaMemcpy(h, g_phase_ns, sizeof(h), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < n && k < 8; ++k) ms[k] = (double)h[k] * 1e-6;
+    }
+    if (g_phase_ns) CUDA_TRY(cudaMemset(g_phase_ns, 0, 8 * sizeof(unsigned long long)));
+    g_phase_profile = enable ? 1 : 0;
+    return INIM_OK;
+}
+
 int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
     if (!jobs || n_jobs < 1) return fail(INIM_E_ARG, "no jobs");
     std::vector<JobSpec> spec(n_jobs);
@@ -766,7 +1075,7 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
             if (st != INIM_OK) return st;
         }
         cap_ptr[k] = j.map->h_xy0.data();   // capacity estimate from the map (4x margin)
-        start_ptr[k] = j.init_xy ? j.init_xy : j.map->h_xy0.data();
+        start_ptr[k] = j.init_xy ? j.init_xy : (const float*)j.map->xy0;   // the map's device copy
         spec[k] = JobSpec{j.map, j.params.log2_res, j.params.precision};
         poll |= needs_poll(j.params);
     }

@@ -11,119 +11,18 @@
 // only for the per-lane partials and the error reduction); the last block of a job to
 // finish (atomic ticket) reduces the errors over the job's regions in a fixed
 // order and applies the stop rule, so the result does not depend on timing.
-#include "raster_common.cuh"
+#include "area_impl.cuh"
 
 namespace inim {
 
 namespace {
 
-constexpr int kRegionsPerBlock = 8;
-
-__device__ void errors_and_stop(const Job& J, int update_state) {
-    __shared__ double ssum[kRegionsPerBlock], smax[kRegionsPerBlock];
-    __shared__ int sfold[kRegionsPerBlock];
-    JobState* st = J.st;
-    const double M = st->mass;
-    double sum = 0.0, mx = 0.0;
-    int fold = 0;
-    for (int v = threadIdx.x; v < J.n_regions; v += blockDim.x) {
-        const double a = __ldcg(J.areas + v);
-        const double o = fabs(a);
-        const double w = (double)J.values[v] / M;
-        const double den = fmax(o, w);
-        const double e = den > 0.0 ? fabs(o - w) / den : 0.0;
-        sum += e;
-        mx = fmax(mx, e);
-        const float s0 = J.sign0[v];
-        if (s0 != 0.0f && ((a > 0.0) != (s0 > 0.0f) || a == 0.0)) fold = 1;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        fold |= __shfl_xor_sync(0xffffffffu, fold, o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { ssum[w] = sum; smax[w] = mx; sfold[w] = fold; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double S = 0.0, X = 0.0;
-        int F = 0;
-        for (int k = 0; k < kRegionsPerBlock; ++k) { S += ssum[k]; X = fmax(X, smax[k]); F |= sfold[k]; }
-        const double eps = S / (double)J.n_regions;
-        st->eps = eps;
-        st->xi = X;
-        if (F) st->foldover = 1;
-        if (update_state) {
-            st->iters += 1;
-            if (X < st->best_xi) { st->best_xi = X; st->since = 0; }
-            else st->since += 1;
-            bool stop = st->iters >= st->max_iters;
-            if (st->stop_on_rule) {
-                if (st->xi_stop > 0.0f && X < (double)st->xi_stop) stop = true;
-                if (st->eps_stop > 0.0f && eps < (double)st->eps_stop) stop = true;
-                if (st->stall_window > 0 && st->since >= st->stall_window) stop = true;
-            }
-            if (st->error != 0) stop = true;
-            if (stop) st->active = 0;
-        }
-    }
-}
-
-// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only.
-// next_hist: the moved vertices are the next iteration's raster input, so the
-// same edge pass also builds its row histogram (and the last block its row
-// offsets), saving the rasteriser two launches.
 __global__ void __launch_bounds__(256) k_areas_errors(const Job* __restrict__ jobs, const int2* __restrict__ bmap,
                                                       int update_state, int next_hist) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
     if (!J.st->active) return;
-    const int v = m.y * kRegionsPerBlock + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (v < J.n_regions) {
-        // shoelace terms x_a y_b - x_b y_a: each product is split exactly into
-        // p + e (e = fma(x, y, -p)) and summed with two-sum into a (hi, lo)
-        // pair, all in FP32; one conversion to double per lane at the end
-        float hi = 0.0f, lo = 0.0f;
-        const int e1 = J.reg_edge_off[v + 1];
-        for (int e = J.reg_edge_off[v] + lane; e < e1; e += 32) {
-            if (next_hist) row_hist_edge(J, e);
-            const int2 ab = J.edges[e];
-            const float2 p = J.xy[ab.x];
-            const float2 q = J.xy[ab.y];
-            const float p1 = __fmul_rn(p.x, q.y), e1p = __fmaf_rn(p.x, q.y, -p1);
-            const float p2 = __fmul_rn(q.x, p.y), e2p = __fmaf_rn(q.x, p.y, -p2);
-            float s = __fadd_rn(hi, p1);
-            float bb = __fsub_rn(s, hi);
-            lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p1, bb)), e1p));
-            hi = s;
-            s = __fadd_rn(hi, -p2);
-            bb = __fsub_rn(s, hi);
-            lo = __fadd_rn(lo, __fsub_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-p2, bb)), e2p));
-            hi = s;
-        }
-        double acc = (double)hi + (double)lo;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) J.areas[v] = 0.5 * acc;
-    }
-    if (update_state < 0) return;
-    // the last block of this job reduces the errors
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nblk = (J.n_regions + kRegionsPerBlock - 1) / kRegionsPerBlock;
-        const int ticket = atomicAdd(&J.st->blocks_done, 1);
-        last = (ticket == nblk - 1);
-        if (last) J.st->blocks_done = 0;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    errors_and_stop(J, update_state);
-    if (next_hist) row_offsets_block(J);
+    areas_item(J, m.y, update_state, next_hist);
 }
 
 }  // namespace

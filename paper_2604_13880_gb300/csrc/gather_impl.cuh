@@ -1,0 +1,134 @@
+// Device bodies of steps 5-6 of the static algorithm (Sec. 4.1): the displacement
+// t(x, y; d) - t(x, y; d0) of Eq. (3) at the four pixel centres around every
+// vertex, bilinear interpolation, the shape blend and the move.
+//
+// Per corner pixel (i, j) the eight InIms come from S, T and the 1-D arrays
+// through Eq. (1) (see scan_impl.cuh); differences are formed in the
+// accumulator type (exact for FIX64, compensated for KAHAN), then scaled to
+// ratios of C.  t(.; d0) uses the exact pixel counts of a constant texture
+// (closed form) scaled by 1/N^2 (a power of two).  Eq. (2) is linear in the
+// eight weights for fixed anchors, so the displacement t(d) - t(d0) is one
+// evaluation of Eq. (2) on the weight differences; a constant texture gives
+// exactly zero.
+#pragma once
+
+#include "scan_impl.cuh"
+
+namespace inim {
+
+
+struct Ratios { float a, b, g, d, at, bt, gt, dt; };
+
+// The eight sums at pixel (i, j) from S, T and the 1-D arrays (Eq. 1),
+// formed in the accumulator type, as ratios to C (inv_c = 1 / C).
+template <class Acc>
+__device__ __forceinline__ Ratios corner_ratios(const Job& J, int i, int j, typename Acc::T C, double inv_c) {
+    using T = typename Acc::T;
+    const int n = J.n;
+    const T* A = reinterpret_cast<const T*>(J.A);
+    const T* B = reinterpret_cast<const T*>(J.B);
+    const T* RC = reinterpret_cast<const T*>(J.rowcum);
+    T a, at, colcum;
+    if (J.ST) {
+        const T* ST = reinterpret_cast<const T*>(J.ST);
+        const size_t p = 2 * ((size_t)j * n + i);
+        a = ST[p];
+        at = ST[p + 1];
+        colcum = ST[2 * ((size_t)(n - 1) * n + i)];
+    } else {
+        const T* S = reinterpret_cast<const T*>(J.S);
+        a = S[(size_t)j * n + i];
+        at = reinterpret_cast<const T*>(J.T)[(size_t)j * n + i];
+        colcum = S[(size_t)(n - 1) * n + i];
+    }
+    const T b = Acc::sub(colcum, a);
+    const T d = Acc::sub(RC[j], a);
+    const T g = Acc::sub(Acc::sub(Acc::sub(C, a), b), d);
+    const T bt = Acc::sub(A[i + j], at);
+    const int w = i - j;
+    const T Bw = (w <= 0) ? B[w + n - 1] : Acc::sub(C, B[w + n - 1]);
+    const T gt = Acc::sub(Bw, bt);
+    const T dt = Acc::sub(Acc::sub(Acc::sub(C, at), bt), gt);
+    Ratios r;
+    r.a = Acc::scale(a, inv_c); r.b = Acc::scale(b, inv_c); r.g = Acc::scale(g, inv_c); r.d = Acc::scale(d, inv_c);
+    r.at = Acc::scale(at, inv_c); r.bt = Acc::scale(bt, inv_c); r.gt = Acc::scale(gt, inv_c);
+    r.dt = Acc::scale(dt, inv_c);
+    return r;
+}
+
+// #{(i', j') in [0,n)^2 : i' + j' <= s} in 32-bit integers (n <= 4096)
+__device__ __forceinline__ int anti_count32(int s, int n) {
+    if (s < 0) return 0;
+    if (s >= 2 * n - 2) return n * n;
+    if (s <= n - 1) return ((s + 1) * (s + 2)) >> 1;
+    const int m = 2 * n - 3 - s;
+    return n * n - (((m + 1) * (m + 2)) >> 1);
+}
+
+// The same eight sums for a constant texture (exact pixel counts, t(.; d0)),
+// as ratios to C0 = N^2 = 2^(2k): an exact power-of-two scaling.
+__device__ __forceinline__ Ratios uniform_ratios(int i, int j, int n, float inv_c0) {
+    const int a = (i + 1) * (j + 1);
+    const int b = (i + 1) * (n - 1 - j);
+    const int g = (n - 1 - i) * (n - 1 - j);
+    const int d = (n - 1 - i) * (j + 1);
+    const int m = i + 1;
+    const int k1 = min(i, j), k2 = min(i, n - 1 - j);
+    const int L = m + (k1 * m - ((k1 * (k1 + 1)) >> 1)) + (k2 * m - ((k2 * (k2 + 1)) >> 1));
+    const int at = anti_count32(i + j, n) - L;
+    const int gt = anti_count32(i - j + n - 1, n) - L;
+    const int dt = n * n - L - at - gt;
+    Ratios r;
+    r.a = (float)a * inv_c0; r.b = (float)b * inv_c0; r.g = (float)g * inv_c0; r.d = (float)d * inv_c0;
+    r.at = (float)at * inv_c0; r.bt = (float)L * inv_c0; r.gt = (float)gt * inv_c0; r.dt = (float)dt * inv_c0;
+    return r;
+}
+
+// Eq. (3) at one pixel: t(d) - t(d0) = Eq. (2) applied to the difference of
+// the weights (Eq. 2 is linear in the eight weights for fixed anchors).
+__device__ __forceinline__ float2 delta_at_pixel(const Ratios& r, const Ratios& r0, int i, int j, float inv_n) {
+    const float x = ((float)i + 0.5f) * inv_n, y = ((float)j + 0.5f) * inv_n;
+    float tx, ty;
+    eq2<float>(r.a - r0.a, r.b - r0.b, r.g - r0.g, r.d - r0.d, r.at - r0.at, r.bt - r0.bt, r.gt - r0.gt,
+               r.dt - r0.dt, 1.0f, x, y, tx, ty);
+    return make_float2(tx, ty);
+}
+
+template <class Acc>
+__device__ __forceinline__ float2 displacement_at(const Job& J, float2 p) {
+    using T = typename Acc::T;
+    const int n = J.n;
+    const T C = J.ST ? reinterpret_cast<const T*>(J.ST)[2 * ((size_t)n * n - 1)]
+                     : reinterpret_cast<const T*>(J.S)[(size_t)n * n - 1];
+    const double inv_c = Acc::inv(C);
+    const float inv_n = 1.0f / (float)n;
+    const float inv_c0 = ldexpf(1.0f, -2 * J.log2n);
+    const float fx = p.x * (float)n - 0.5f;
+    const float fy = p.y * (float)n - 0.5f;
+    int i0 = (int)floorf(fx), j0 = (int)floorf(fy);
+    i0 = min(max(i0, 0), n - 2);
+    j0 = min(max(j0, 0), n - 2);
+    const float a = fminf(fmaxf(fx - (float)i0, 0.0f), 1.0f);
+    const float b = fminf(fmaxf(fy - (float)j0, 0.0f), 1.0f);
+    float2 f[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int i = i0 + (c & 1), j = j0 + (c >> 1);
+        f[c] = delta_at_pixel(corner_ratios<Acc>(J, i, j, C, inv_c), uniform_ratios(i, j, n, inv_c0), i, j, inv_n);
+    }
+    const float2 top = make_float2((1.0f - a) * f[0].x + a * f[1].x, (1.0f - a) * f[0].y + a * f[1].y);
+    const float2 bot = make_float2((1.0f - a) * f[2].x + a * f[3].x, (1.0f - a) * f[2].y + a * f[3].y);
+    return make_float2((1.0f - b) * top.x + b * bot.x, (1.0f - b) * top.y + b * bot.y);
+}
+
+template <class Acc>
+__device__ __forceinline__ void gather_vertex(const Job& J, int v) {
+    if (v >= J.n_verts) return;
+    float2 p = J.xy[v];
+    const float2 dlt = displacement_at<Acc>(J, p);
+    p.x += J.lam * dlt.x;
+    p.y += J.lam * dlt.y;
+    J.xy[v] = p;
+}
+
+}  // namespace inim

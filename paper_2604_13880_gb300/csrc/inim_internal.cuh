@@ -201,6 +201,15 @@ cudaError_t launch_displacement(const Job* d_job, const float* xy, int n, float*
                                 int precision, cudaStream_t s);
 cudaError_t launch_finalize_B(const Job* d_job, int precision, cudaStream_t s);
 
+// persistent form (small FP32 batches, N <= 2048)
+int persistent_smem_bytes(int max_n);
+cudaError_t launch_persistent(Job* d_jobs, int n_jobs, const BlockMap& edge, const BlockMap& row,
+                              const BlockMap& band, const BlockMap& carry, const BlockMap& vert,
+                              const BlockMap& region, int iters, int rounds, const int* job_rounds,
+                              const float* const* round_values, float2* const* round_out,
+                              JobState* round_init, JobState* const* round_stats, unsigned* bar, int* err,
+                              int max_n, int max_blocks, unsigned long long* phase_ns, cudaStream_t s);
+
 // plain (unfused) form: extra full textures of one job
 struct PlainWork {
     float*  d   = nullptr;   // [n*n] density

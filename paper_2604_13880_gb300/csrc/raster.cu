@@ -21,29 +21,11 @@
 //                  in region order, write the row once; rows with more than
 //                  256 crossings go to the block-per-row path (run by the
 //                  density-table kernel).
-#include "raster_common.cuh"
+#include "raster_impl.cuh"
 
 namespace inim {
 
 namespace {
-
-constexpr int kRowThreads = 256;
-constexpr int kRowKeyCap = 2048;   // crossings one row can hold in shared memory
-
-// min(max(ceil(num / den), 0), n) exactly, for den > 0, without a 64-bit
-// division: a float estimate of the quotient (only needed in [0, n], n <=
-// 4096, where it is off by less than one) corrected by exact int64 products.
-__device__ __forceinline__ int clamped_ceil_div(long long num, long long den, int n) {
-    if (num <= 0) return 0;                              // ceil <= 0
-    if (num > (long long)n * den) return n;              // ceil > n
-    long long q = (long long)floorf(__fdiv_rn((float)num, (float)den));
-    long long r = num - q * den;
-    while (r < 0) { --q; r += den; }
-    while (r >= den) { ++q; r -= den; }
-    const long long c = q + (r > 0 ? 1 : 0);
-    return (int)(c > n ? n : c);
-}
-
 
 // Histogram + offsets of the current vertex positions (the first iteration
 // of a run; later iterations get them from the area kernel).  One ticket per
@@ -70,298 +52,11 @@ __global__ void __launch_bounds__(256) k_raster_prologue(const Job* __restrict__
     row_offsets_block(J);
 }
 
-__global__ void k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
+__global__ void __launch_bounds__(256) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
     if (!J.st->active) return;
-    const int e = m.y * blockDim.x + threadIdx.x;
-    if (e >= J.n_edges) return;
-    EdgeFix f;
-    if (!edge_rows(J, e, f)) return;
-    const unsigned reg = (unsigned)J.edge_region[e] << 16;
-    const long long dY = f.Y1 - f.Y0;
-    const long long dX = f.X1 - f.X0;
-    const long long den = 256 * dY;
-    for (int j = f.jlo; j <= f.jhi; ++j) {
-        const long long Yc = 256LL * j + 128;
-        const int c = clamped_ceil_div(dX * (Yc - f.Y0) + (f.X0 - 128) * dY, den, J.n);
-        const int slot = atomicAdd(&J.row_cnt[j], 1);
-        const int idx = J.row_off[j] + slot;
-        if (idx < J.key_cap) J.keys[idx] = reg | (unsigned)c;
-    }
-}
-
-template <int CPT>
-__device__ __forceinline__ void store_labels(uint16_t* dst, const uint16_t (&lab)[CPT]) {
-    if constexpr (CPT == 16) {
-        uint4 a, b;
-        a.x = lab[0] | (lab[1] << 16); a.y = lab[2] | (lab[3] << 16);
-        a.z = lab[4] | (lab[5] << 16); a.w = lab[6] | (lab[7] << 16);
-        b.x = lab[8] | (lab[9] << 16); b.y = lab[10] | (lab[11] << 16);
-        b.z = lab[12] | (lab[13] << 16); b.w = lab[14] | (lab[15] << 16);
-        reinterpret_cast<uint4*>(dst)[0] = a;
-        reinterpret_cast<uint4*>(dst)[1] = b;
-    } else if constexpr (CPT == 8) {
-        uint4 a;
-        a.x = lab[0] | (lab[1] << 16); a.y = lab[2] | (lab[3] << 16);
-        a.z = lab[4] | (lab[5] << 16); a.w = lab[6] | (lab[7] << 16);
-        reinterpret_cast<uint4*>(dst)[0] = a;
-    } else if constexpr (CPT == 4) {
-        uint2 a;
-        a.x = lab[0] | (lab[1] << 16); a.y = lab[2] | (lab[3] << 16);
-        reinterpret_cast<uint2*>(dst)[0] = a;
-    } else if constexpr (CPT == 2) {
-        reinterpret_cast<unsigned*>(dst)[0] = lab[0] | (lab[1] << 16);
-    } else {
-        dst[0] = lab[0];
-    }
-}
-
-struct RowShared {
-    unsigned keys[kRowKeyCap];
-    unsigned sorted[kRowKeyCap];
-    unsigned diff[4097];          // low 16 bits: XOR of (v+1); high 16 bits: coverage delta
-    unsigned wx[kRowThreads / 32];
-    unsigned wc[kRowThreads / 32];
-};
-
-template <int CPT>
-__device__ void raster_row(const Job& J, int j, RowShared& sh) {
-    const int n = J.n;
-    const int R = J.n_regions;
-    const int tid = threadIdx.x;
-    const int k0 = J.row_off[j];
-    const int k1 = J.row_off[j + 1];
-    const int cnt = k1 - k0;
-    const bool bad = (k1 > J.key_cap) || (cnt > kRowKeyCap);
-    if (bad) {   // capacity error already (or now) flagged; write background
-        if (tid == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
-        uint16_t lab[CPT];
-#pragma unroll
-        for (int k = 0; k < CPT; ++k) lab[k] = (uint16_t)R;
-        store_labels<CPT>(J.labels + (size_t)j * n + tid * CPT, lab);
-        return;
-    }
-    for (int k = tid; k < cnt; k += blockDim.x) sh.keys[k] = J.keys[k0 + k];
-    for (int k = tid; k <= n; k += blockDim.x) sh.diff[k] = 0u;
-    __syncthreads();
-    // rank sort (ties broken by position): sorted by (region, column)
-    for (int e = tid; e < cnt; e += blockDim.x) {
-        const unsigned key = sh.keys[e];
-        int rank = 0;
-        for (int k = 0; k < cnt; ++k) {
-            const unsigned o = sh.keys[k];
-            rank += (o < key) || (o == key && k < e);
-        }
-        sh.sorted[rank] = key;
-    }
-    __syncthreads();
-    // consecutive pairs of one region are its spans [a, b)
-    const int nspan = cnt >> 1;
-    for (int p = tid; p < nspan; p += blockDim.x) {
-        const unsigned ka = sh.sorted[2 * p], kb = sh.sorted[2 * p + 1];
-        const unsigned a = ka & 0xffffu, b = kb & 0xffffu, v = ka >> 16;
-        if (a < b) {
-            atomicXor(&sh.diff[a], v + 1u);
-            atomicXor(&sh.diff[b], v + 1u);
-            atomicAdd(&sh.diff[a], 1u << 16);
-            atomicAdd(&sh.diff[b], 0xffff0000u);
-        }
-    }
-    __syncthreads();
-    // prefix (XOR on the low half, sum on the high half) over the row
-    const int i0 = tid * CPT;
-    unsigned px[CPT], pc[CPT];
-    unsigned ax = 0, ac = 0;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        const unsigned w = sh.diff[i0 + k];
-        ax ^= (w & 0xffffu);
-        ac += (w >> 16);
-        px[k] = ax;
-        pc[k] = ac;
-    }
-    const int lane = tid & 31, wid = tid >> 5;
-    unsigned ix = ax, ic = ac;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned tx = __shfl_up_sync(0xffffffffu, ix, o);
-        const unsigned tc = __shfl_up_sync(0xffffffffu, ic, o);
-        if (lane >= o) { ix ^= tx; ic += tc; }
-    }
-    if (lane == 31) { sh.wx[wid] = ix; sh.wc[wid] = ic; }
-    __syncthreads();
-    unsigned ox = ix ^ ax, oc = ic - ac;          // exclusive within the warp
-    for (int w = 0; w < wid; ++w) { ox ^= sh.wx[w]; oc += sh.wc[w]; }
-    uint16_t lab[CPT];
-    int over = 0;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        const unsigned c = (oc + pc[k]) & 0xffffu;
-        const unsigned x = (ox ^ px[k]) & 0xffffu;
-        if (c == 0) lab[k] = (uint16_t)R;
-        else if (c == 1) lab[k] = (uint16_t)(x - 1);
-        else { over = 1; lab[k] = 0xffffu; }
-    }
-    const int any_over = __syncthreads_or(over);
-    if (any_over) {
-        // slow path (fold-over): smallest region id among the covering spans,
-        // counts from the resolved labels
-#pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-            if (lab[k] == 0xffffu) {
-                const unsigned i = (unsigned)(i0 + k);
-                unsigned best = 0xffffu;
-                for (int p = 0; p < nspan; ++p) {
-                    const unsigned ka = sh.sorted[2 * p], kb = sh.sorted[2 * p + 1];
-                    if ((ka & 0xffffu) <= i && i < (kb & 0xffffu) && (ka >> 16) < best) best = ka >> 16;
-                }
-                lab[k] = (uint16_t)best;
-            }
-            if (lab[k] != (uint16_t)R) atomicAdd(&J.counts[lab[k]], 1);
-        }
-        if (tid == 0) atomicExch(&J.st->overlap, 1);
-    } else {
-        for (int p = tid; p < nspan; p += blockDim.x) {
-            const unsigned ka = sh.sorted[2 * p], kb = sh.sorted[2 * p + 1];
-            const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
-            if (a < b) atomicAdd(&J.counts[ka >> 16], b - a);
-        }
-    }
-    store_labels<CPT>(J.labels + (size_t)j * n + i0, lab);
-    if (tid == 0) J.row_cnt[j] = 0;     // ready for the next iteration
-}
-
-// Rows with more crossings than a warp holds in registers, one block per job
-// (usually none): the block-per-row path.
-__device__ void raster_big_rows(const Job& J, RowShared& sh) {
-    const int nbig = __ldcg(&J.st->n_big);
-    for (int q = 0; q < nbig; ++q) {
-        const int j = J.big_rows[q];
-        switch (J.n / kRowThreads) {
-            case 1: raster_row<1>(J, j, sh); break;
-            case 2: raster_row<2>(J, j, sh); break;
-            case 4: raster_row<4>(J, j, sh); break;
-            case 8: raster_row<8>(J, j, sh); break;
-            default: raster_row<16>(J, j, sh); break;
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// warp-per-row rasteriser (the common case: <= 256 crossings in a row)
-// ---------------------------------------------------------------------------
-constexpr int kWarpsPerBlock = 8;
-
-// ascending bitonic sort of KPL*32 keys, lane l holding elements [l*KPL, l*KPL+KPL)
-template <int KPL>
-__device__ __forceinline__ void warp_bitonic(unsigned (&k)[KPL], int lane) {
-    constexpr int NT = KPL * 32;
-#pragma unroll
-    for (int size = 2; size <= NT; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= KPL) {
-                const int lmask = stride / KPL;
-#pragma unroll
-                for (int e = 0; e < KPL; ++e) {
-                    const int idx = lane * KPL + e;
-                    const unsigned other = __shfl_xor_sync(0xffffffffu, k[e], lmask);
-                    const bool up = (idx & size) == 0;
-                    const bool lower = (idx & stride) == 0;
-                    const unsigned mn = min(k[e], other), mx = max(k[e], other);
-                    k[e] = (lower == up) ? mn : mx;
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < KPL; ++e) {
-                    const int p = e ^ stride;
-                    if (p > e) {
-                        const int idx = lane * KPL + e;
-                        const bool up = (idx & size) == 0;
-                        const unsigned a = k[e], b = k[p];
-                        if (up ? (a > b) : (a < b)) { k[e] = b; k[p] = a; }
-                    }
-                }
-            }
-        }
-    }
-}
-
-// One row: keys sorted by (region, column) give each region's spans as
-// consecutive pairs.  The spans are painted into a shared-memory copy of the
-// row in sorted order, writing only still-background pixels, so a pixel in
-// several regions keeps the smallest id.  Overlap <=> the summed span lengths
-// exceed the painted pixel count.
-template <int KPL>
-__device__ void raster_row_warp(const Job& J, int j, int cnt, uint16_t* row, int lane) {
-    const int n = J.n;
-    const unsigned R = (unsigned)J.n_regions;
-    const int k0 = J.row_off[j];
-    unsigned key[KPL];
-#pragma unroll
-    for (int e = 0; e < KPL; ++e) {
-        const int idx = lane * KPL + e;
-        key[e] = idx < cnt ? J.keys[k0 + idx] : 0xffffffffu;
-    }
-    // background fill of the row copy
-    unsigned* row32 = reinterpret_cast<unsigned*>(row);
-    const unsigned bg2 = R | (R << 16);
-    for (int i = lane; i < (n >> 1); i += 32) row32[i] = bg2;
-    warp_bitonic<KPL>(key, lane);
-    __syncwarp();
-    // paint spans in sorted order
-    int my_len = 0;
-    const int src_lanes = (cnt + KPL - 1) / KPL;
-    for (int src = 0; src < src_lanes; ++src) {
-#pragma unroll
-        for (int t = 0; t < KPL / 2; ++t) {
-            const unsigned ka = __shfl_sync(0xffffffffu, key[2 * t], src);
-            const unsigned kb = __shfl_sync(0xffffffffu, key[2 * t + 1], src);
-            if (src * KPL + 2 * t + 1 >= cnt) continue;          // padding (warp-uniform)
-            const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
-            const uint16_t v = (uint16_t)(ka >> 16);
-            if (a < b) {
-                if (lane == 0) my_len += b - a;
-                for (int i = a + lane; i < b; i += 32)
-                    if (row[i] == (uint16_t)R) row[i] = v;
-            }
-            __syncwarp();
-        }
-    }
-    // painted pixels vs summed span lengths
-    int painted = 0;
-    for (int i = lane; i < (n >> 1); i += 32) {
-        const unsigned w = row32[i];
-        painted += ((w & 0xffffu) != R) + ((w >> 16) != R);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        painted += __shfl_xor_sync(0xffffffffu, painted, o);
-        my_len += __shfl_xor_sync(0xffffffffu, my_len, o);
-    }
-    if (painted == my_len) {
-        // no overlap: counts from the spans held by this lane
-#pragma unroll
-        for (int t = 0; t < KPL / 2; ++t) {
-            const int idx = lane * KPL + 2 * t;
-            if (idx + 1 < cnt) {
-                const int a = (int)(key[2 * t] & 0xffffu), b = (int)(key[2 * t + 1] & 0xffffu);
-                if (a < b) atomicAdd(&J.counts[key[2 * t] >> 16], b - a);
-            }
-        }
-    } else {
-        // fold-over in this row: counts from the resolved labels
-        for (int i = lane; i < n; i += 32)
-            if (row[i] != (uint16_t)R) atomicAdd(&J.counts[row[i]], 1);
-        if (lane == 0) atomicExch(&J.st->overlap, 1);
-    }
-    // write the row
-    uint4* dst = reinterpret_cast<uint4*>(J.labels + (size_t)j * n);
-    const uint4* srcv = reinterpret_cast<const uint4*>(row);
-    for (int i = lane; i < (n >> 3); i += 32) dst[i] = srcv[i];
-    if (lane == 0) J.row_cnt[j] = 0;     // ready for the next iteration
+    crossings_edge(J, m.y * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_raster_rows(const Job* __restrict__ jobs,
@@ -370,87 +65,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_raster_rows(const Job* 
     const int2 m = bmap[blockIdx.x];                 // (job, first row)
     const Job& J = jobs[m.x];
     if (!J.st->active) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = m.y + warp;
-    if (j >= J.n) return;
-    uint16_t* row = rows_smem + (size_t)warp * J.n;
-    const int k0 = J.row_off[j];
-    const int k1 = J.row_off[j + 1];
-    const int cnt = k1 - k0;
-    if (k1 > J.key_cap) {                            // capacity error already flagged
-        if (lane == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
-        return;
-    }
-    if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, row, lane);
-    else if (cnt <= 8 * 32) raster_row_warp<8>(J, j, cnt, row, lane);
-    else if (lane == 0) {                            // big row: handled by k_raster_big
-        const int q = atomicAdd(&J.st->n_big, 1);
-        J.big_rows[q] = j;
-    }
+    raster_rows_item(J, m.y, rows_smem);
 }
 
-// per job: the big rows, then d0, density table, background count, total
-// mass, fixed-point scale
 __global__ void __launch_bounds__(kRowThreads) k_density_table(const Job* __restrict__ jobs) {
-    const Job& J = jobs[blockIdx.x];
-    if (!J.st->active) return;
-    {
-        __shared__ RowShared rsh;
-        raster_big_rows(J, rsh);
-    }
+    __shared__ RowShared rsh;
     __shared__ double ss[32];
     __shared__ long long so[32];
-    const int R = J.n_regions;
-    double s = 0.0;
-    long long o = 0;
-    int bad = 0;
-    for (int v = threadIdx.x; v < R; v += blockDim.x) {
-        const float sv = J.values[v];
-        if (!(sv >= 0.0f) || isinf(sv)) bad = 1;           // values must be finite, >= 0
-        const int c = __ldcg(J.counts + v);
-        if (c > 0) { s += (double)sv; o += c; }
-    }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&J.st->error, INIM_E_VALUE);
-#pragma unroll
-    for (int k = 16; k > 0; k >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, k);
-        o += __shfl_xor_sync(0xffffffffu, o, k);
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { ss[w] = s; so[w] = o; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double S = 0.0;
-        long long O = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { S += ss[k]; O += so[k]; }
-        ss[0] = S;
-        so[0] = O;
-    }
-    __syncthreads();
-    const double sum_s = ss[0];
-    const long long sum_o = so[0];
-    const long long npx = (long long)J.n * J.n;
-    const long long o_bg = npx - sum_o;
-    const bool empty = (sum_o == 0);
-    const double d0 = empty ? 1.0 : sum_s / (double)sum_o;
-    for (int v = threadIdx.x; v < R; v += blockDim.x) {
-        const int c = __ldcg(J.counts + v);
-        J.dens[v] = (c > 0 && !empty) ? (float)((double)J.values[v] / ((double)c * d0)) : 0.0f;
-    }
-    if (threadIdx.x == 0) {
-        J.dens[R] = empty ? 1.0f : J.bdv_scale;
-        J.counts[R] = (int)o_bg;
-        JobState* st = J.st;
-        st->d0 = d0;
-        st->bdv_abs = (double)J.bdv_scale * d0;
-        st->mass = empty ? 1.0 : sum_s + st->bdv_abs * (double)o_bg;
-        // all InIm magnitudes are <= C' = sum_o + bdv * o_bg (relative units)
-        const double cbound = empty ? (double)npx : ((double)sum_o + (double)J.bdv_scale * (double)o_bg);
-        int e = 0;
-        frexp(cbound * 1.0001 + 1.0, &e);   // cbound < 2^e
-        int fb = 61 - e;
-        st->fix_bits = fb < 0 ? 0 : fb;
-    }
+    const Job& J = jobs[blockIdx.x];
+    if (!J.st->active) return;
+    density_table_body(J, rsh, ss, so);
 }
 
 }  // namespace

@@ -185,10 +185,13 @@ template <class Acc, int CPT>
 __device__ __forceinline__ void store_row_pairs(typename Acc::T* dst, const typename Acc::T (&a)[CPT],
                                                 const typename Acc::T (&b)[CPT]) {
     using T = typename Acc::T;
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && CPT % 2 == 0) {
 #pragma unroll
         for (int k = 0; k < CPT; k += 2)
             reinterpret_cast<float4*>(dst)[k / 2] = make_float4(a[k], b[k], a[k + 1], b[k + 1]);
+    } else if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) reinterpret_cast<float2*>(dst)[k] = make_float2(a[k], b[k]);
     } else {
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
@@ -208,18 +211,12 @@ struct ScanShared {
     float dens[kDensSmem];
 };
 
-// phase 1 (PHASE == 1) or phase 3 (PHASE == 3) of one band
+// phase 1 (PHASE == 1) or phase 3 (PHASE == 3) of one band, by a block of NT
+// threads; the caller provides the shared memory
 template <class Acc, int CPT, int NT, int PHASE>
-__global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
-                                                  const int2* __restrict__ bmap,
-                                                  const float* __restrict__ dtex) {
+__device__ inline void scan_band_body(const Job& J, int band, const float* __restrict__ dtex, ScanShared<Acc, NT>& sh) {
     using T = typename Acc::T;
-    __shared__ ScanShared<Acc, NT> sh;
-    const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
-    if (!J.st->active) return;
     const int n = J.n, H = J.H, nb = J.nb;
-    const int band = m.y;
     const int j0 = band * H;
     const int rows = min(H, n - j0);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -383,6 +380,17 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
     }
 }
 
+template <class Acc, int CPT, int NT, int PHASE>
+__global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
+                                                  const int2* __restrict__ bmap,
+                                                  const float* __restrict__ dtex) {
+    __shared__ ScanShared<Acc, NT> sh;
+    const int2 m = bmap[blockIdx.x];
+    const Job& J = jobs[m.x];
+    if (!J.st->active) return;
+    scan_band_body<Acc, CPT, NT, PHASE>(J, m.y, dtex, sh);
+}
+
 // phase 2: carries.  Each carry is an exclusive prefix sum over the bands b'
 // of a value that depends only on (b', q):
 //   Sc_b(i)  = sum_{b'<b} aggS_{b'}(i)                                  q = i
@@ -397,15 +405,10 @@ __host__ __device__ __forceinline__ int carry_qspace(int n, int nb, int H) {
 }
 
 template <class Acc>
-__global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs,
-                                                    const int2* __restrict__ bmap) {
+__device__ inline void scan_carry_body(const Job& J, int q) {
     using T = typename Acc::T;
-    const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
-    if (!J.st->active) return;
     const int n = J.n, H = J.H, nb = J.nb;
     const int span = n + (nb - 1) * H;
-    int q = m.y * blockDim.x + threadIdx.x;
     int kind;
     if (q < n) kind = 0;
     else if ((q -= n) < span) kind = 1;
@@ -446,6 +449,15 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
             }
         }
     }
+}
+
+template <class Acc>
+__global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs,
+                                                    const int2* __restrict__ bmap) {
+    const int2 m = bmap[blockIdx.x];
+    const Job& J = jobs[m.x];
+    if (!J.st->active) return;
+    scan_carry_body<Acc>(J, m.y * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -415,3 +415,63 @@ def test_autotuner_picks_a_valid_tile_and_stays_on_the_oracle():
     ora, _ = O.run(mesh.with_verts(mesh.verts_f32().astype(np.float64)), vals[None].astype(np.float64), 8,
                    shape=0.5, max_iters=5, xi_stop=0, stall_window=0)
     assert np.abs(out[0] - ora[0]).max() <= 1e-4 * EXTENT
+
+
+# ---------------------------------------------------------------------------
+# A7 / A8: time series in one call; the persistent launch vs the graph path
+# ---------------------------------------------------------------------------
+def _series_case():
+    mesh = synth.voronoi_map(40, 2500, seed=71, jitter=0.3)
+    vals = synth.random_walk_values(40, 3, seed=72).astype(np.float32)
+    return mesh, vals
+
+
+def test_series_persistent_and_graph_paths_agree_with_oracle():
+    mesh, vals = _series_case()
+    m = P.inim_map_create(mesh)
+    pd = P.params(log2_res=9, shape=0.5, max_iters=8, xi_stop=0.0, stall_window=0, mode=P.INIM_DIRECT)
+    pc = P.params(log2_res=9, shape=0.25, max_iters=6, xi_stop=0.0, stall_window=0, mode=P.INIM_CUMULATIVE)
+    series = [dict(map=m, values=vals[:2], params=pd), dict(map=m, values=vals, params=pc)]
+    graph, gstats, _ = P.inim_run_series(series)          # per-step kernels under CUDA graphs
+    try:
+        P.inim_set_persistent(True)
+        pers, pstats, _ = P.inim_run_series(series)       # one persistent launch per batch
+    finally:
+        P.inim_set_persistent(False)
+    base = mesh.with_verts(mesh.verts_f32().astype(np.float64))
+    od, _ = O.run(base, vals[:2].astype(np.float64), 9, shape=0.5, max_iters=8, xi_stop=0, stall_window=0)
+    oc, _ = O.run(base, vals.astype(np.float64), 9, shape=0.25, max_iters=6, xi_stop=0, stall_window=0,
+                  mode="cumulative")
+    for got in (graph, pers):
+        assert np.abs(got[0] - od).max() <= 1e-4 * EXTENT
+        assert np.abs(got[1] - oc).max() <= 1e-4 * EXTENT
+    assert np.abs(graph[1] - pers[1]).max() <= 1e-5
+    assert [s["iters"] for s in pstats[1]] == [6, 6, 6] and [s["iters"] for s in gstats[1]] == [6, 6, 6]
+
+
+def test_cumulative_series_with_stop_rule_on_device():
+    """Every time step stops by its own rule inside one persistent launch; the
+    per-step statistics come back per step."""
+    mesh, vals = _series_case()
+    m = P.inim_map_create(mesh)
+    p = P.params(log2_res=8, shape=0.0, max_iters=200, xi_stop=0.0, stall_window=0, eps_stop=0.08,
+                 mode=P.INIM_CUMULATIVE)
+    try:
+        P.inim_set_persistent(True)
+        out, stats, _ = P.inim_run(m, vals, p)
+    finally:
+        P.inim_set_persistent(False)
+    gout, gstats, _ = P.inim_run(m, vals, p)           # the same series round by round
+    # same stop decisions; vertices within the N-iteration bound (the two paths
+    # tile the FP32 scan differently, hence round differently)
+    assert [s["iters"] for s in gstats] == [s["iters"] for s in stats]
+    assert np.abs(gout - out).max() <= 1e-4 * EXTENT
+    for t, s in enumerate(stats):
+        assert s["iters"] == 200 or s["eps"] < 0.08, (t, s)
+    # the last step's reported eps is the error of its returned vertices
+    g = out[-1].astype(np.float64)
+    _, cnt, _ = O.labels_scanline(g, *arrays(mesh), 8)
+    v = vals[-1].astype(np.float64)
+    d0 = v[cnt > 0].sum() / cnt.sum()
+    eps, _ = O.cartographic_errors(O.signed_areas(g, *arrays(mesh)), O.desired_areas(v, cnt, d0, 256))
+    assert abs(eps - stats[-1]["eps"]) <= 2e-3
