@@ -127,6 +127,40 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# precision study: the 4096^2 workload in the three precisions
+# ---------------------------------------------------------------------------
+def precision_study(args):
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import synth
+    w = synth.precision_workload()
+    mesh = w["mesh"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    xy0 = mesh.verts_f32()
+    K = args.precision_study
+    res = {"workload": w["name"], "iterations": K, "precisions": {}}
+    outs = {}
+    for name, prec in (("fp32", P.INIM_FP32), ("fix64", P.INIM_FIX64), ("kahan", P.INIM_KAHAN)):
+        p = P.params(log2_res=12, shape=0.5, precision=prec)
+        x = torch.as_tensor(xy0, device="cuda")
+        v = torch.as_tensor(vals, device="cuda")
+        P.inim_iterate(m, x.clone(), v, p, 2)             # warm
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, _ = P.inim_iterate(m, x, v, p, K)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        outs[name] = x.cpu().numpy()
+        res["precisions"][name] = {"ms_per_iteration": 1e3 * dt / K, "eps": st["eps"], "xi": st["xi"]}
+    np.savez_compressed(args.study_out, verts=xy0, ring_off=mesh.ring_off, ring_idx=mesh.ring_idx,
+                        ring_region=mesh.ring_region, n_regions=mesh.n_regions, values=vals, iterations=K,
+                        **{f"gpu_{k}": v for k, v in outs.items()})
+    print(json.dumps(res))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -136,10 +170,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain form, time-to-eps and CPU baseline")
+    ap.add_argument("--precision-study", type=int, default=0, metavar="K",
+                    help="instead of the sweep: K iterations of the 4096^2 precision workload in FP32, "
+                         "FIX64 and compensated sums; results to --study-out for the FP64 oracle comparison")
+    ap.add_argument("--study-out", default="precision_study.npz")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_study:
+        return precision_study(args)
 
     import torch
     import paper_2604_13880_gb300 as P

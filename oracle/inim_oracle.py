@@ -259,10 +259,14 @@ def inims(d):
     gamma = C - alpha - beta - delta
     L = left_wedge_sweep(d)
     jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
-    anti = np.zeros(2 * N - 1, dtype=d.dtype)
-    diag = np.zeros(2 * N - 1, dtype=d.dtype)
-    np.add.at(anti, (ii + jj).ravel(), d.ravel())
-    np.add.at(diag, (ii - jj + N - 1).ravel(), d.ravel())
+    if np.issubdtype(d.dtype, np.integer):        # exact integer sums
+        anti = np.zeros(2 * N - 1, dtype=d.dtype)
+        diag = np.zeros(2 * N - 1, dtype=d.dtype)
+        np.add.at(anti, (ii + jj).ravel(), d.ravel())
+        np.add.at(diag, (ii - jj + N - 1).ravel(), d.ravel())
+    else:
+        anti = np.bincount((ii + jj).ravel(), weights=d.ravel(), minlength=2 * N - 1)
+        diag = np.bincount((ii - jj + N - 1).ravel(), weights=d.ravel(), minlength=2 * N - 1)
     A = np.cumsum(anti)
     B = np.cumsum(diag)
     at = A[ii + jj] - L

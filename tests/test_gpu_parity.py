@@ -475,3 +475,27 @@ def test_cumulative_series_with_stop_rule_on_device():
     d0 = v[cnt > 0].sum() / cnt.sum()
     eps, _ = O.cartographic_errors(O.signed_areas(g, *arrays(mesh)), O.desired_areas(v, cnt, d0, 256))
     assert abs(eps - stats[-1]["eps"]) <= 2e-3
+
+
+# ---------------------------------------------------------------------------
+# A9: precision study at 4096^2 (values over six decades), a few iterations
+# ---------------------------------------------------------------------------
+@pytest.mark.slow
+def test_precision_variants_at_4096_against_fp64_oracle():
+    w = synth.precision_workload()
+    mesh = w["mesh"]
+    vals = w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    K = 3
+    xy0 = mesh.verts_f32()
+    ora = xy0.astype(np.float64)
+    t0 = O.transform_uniform(4096)
+    for _ in range(K):
+        ora, _ = O.iterate(ora, arrays(mesh), vals.astype(np.float64), 12, 0.5, t0=t0)
+    err = {}
+    for name, prec in (("fp32", P.INIM_FP32), ("fix64", P.INIM_FIX64), ("kahan", P.INIM_KAHAN)):
+        x = dev(xy0)
+        P.inim_iterate(m, x, dev(vals), P.params(log2_res=12, shape=0.5, precision=prec), K)
+        err[name] = np.abs(x.cpu().numpy() - ora).max()
+    assert max(err.values()) <= 1e-5 * EXTENT, err           # the one-iteration bound, K = 3
+    assert err["fix64"] <= err["fp32"] + 1e-7 and err["kahan"] <= err["fp32"] + 1e-7, err
