@@ -283,6 +283,48 @@ int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream
 int inim_inims_noalloc(const float* density, int32_t log2_res, float* S, float* T,
                        float* A, float* B, void* stream);
 
+/* ---------------- learned warm start (not part of the paper) ------------ */
+
+/*
+ * CNN input of a map state: rasterise the map at xy (host or device, like
+ * inim_raster), build the density texture of Sec. 4.1 step 3 with values
+ * (host or device, [n_regions]) and average log(d / d0) over pool x pool
+ * pixel blocks.  out: [(N/pool)^2] float, row-major, host or device.
+ */
+int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, const float* values,
+                        int32_t pool, float* out, void* stream);
+
+typedef struct inim_cnn inim_cnn;   /* encoder-decoder CNN, 64^2 -> 64^2 x 2 */
+
+/* Create with He-initialised weights (seeded); 1,163,234 f32 parameters. */
+int inim_cnn_create(int32_t seed, inim_cnn** out);
+int inim_cnn_destroy(inim_cnn* cnn);
+long long inim_cnn_num_params(const inim_cnn* cnn);   /* cnn may be NULL */
+/* Parameter blob (per layer: weights [cout][3][3][cin], bias [cout]) to / from host or device. */
+int inim_cnn_get_params(const inim_cnn* cnn, float* out, long long n);
+int inim_cnn_set_params(inim_cnn* cnn, const float* in, long long n);
+/*
+ * x: [B][64][64] f32 pooled log densities, y: [B][64][64][2] f32 predicted
+ * displacement x 10 (unit-square units); device memory.
+ */
+int inim_cnn_forward(inim_cnn* cnn, const float* x, int32_t B, float* y, void* stream);
+/* Mean squared error against targets y and its gradient w.r.t. every parameter
+ * (grads: host or device [n_params], may be NULL; loss: host, may be NULL). */
+int inim_cnn_gradients(inim_cnn* cnn, const float* x, const float* y, int32_t B, float* loss, float* grads,
+                       void* stream);
+/* One Adam step (beta 0.9 / 0.999) on the mean squared error. */
+int inim_cnn_train_step(inim_cnn* cnn, const float* x, const float* y, int32_t B, float lr, float* loss,
+                        void* stream);
+const char* inim_cnn_last_error(void);
+
+/*
+ * Load the network used by inim_params.warm_start (the f32 parameter blob of
+ * inim_cnn_get_params; bytes = 4 * inim_cnn_num_params(NULL)).  Direct steps
+ * with warm_start = 1 first move every vertex by the predicted field, then
+ * iterate as usual.
+ */
+int inim_warmstart_load(const void* weights, size_t bytes);
+
 /* ---------------- scan tiles and their autotuner ------------------------- */
 
 /*

@@ -166,6 +166,20 @@ def density(labels, counts, values, bdv_scale=1.0):
     return d, d0, bdv
 
 
+def pooled_log_density(labels, counts, values, pool, bdv_scale=1.0):
+    """Input of the learned warm start (no counterpart in the paper).
+
+    The density texture of Sec. 4.1 step 3 as d / d0, floored at 1e-6, in
+    logarithms, averaged over pool x pool pixel blocks.  Returns
+    [N / pool, N / pool], indexed [block row, block column].
+    """
+    d, d0, _ = density(labels, counts, values, bdv_scale)
+    lg = np.log(np.maximum(d / d0, 1e-6))
+    N = lg.shape[0]
+    m = N // pool
+    return lg.reshape(m, pool, m, pool).mean(axis=(1, 3))
+
+
 # ----------------------------------------------------------------------------
 # Step 4: integral images (Sec. 3.1)
 # ----------------------------------------------------------------------------

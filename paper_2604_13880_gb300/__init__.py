@@ -275,3 +275,92 @@ def inim_persistent_phase_times(enable: bool):
     ms = (ctypes.c_double * 8)()
     _lib.check(_lib.load().inim_persistent_phase_times(1 if enable else 0, ms, 8), "inim_persistent_phase_times")
     return dict(zip(PERSISTENT_PHASES, list(ms)))
+
+
+# ---------------------------------------------------------------------------
+# learned warm start (not part of the paper): density input, network, loading
+# ---------------------------------------------------------------------------
+def inim_density_pooled(m: Map, xy, log2_res: int, values, pool: int, out, stream=None) -> None:
+    """out[(N/pool)^2] = block averages of log(d / d0) of the map at xy (host or device arrays)."""
+    if isinstance(values, np.ndarray) or not hasattr(values, "data_ptr"):
+        values = np.ascontiguousarray(values, dtype=np.float32)
+    _lib.check(_lib.load().inim_density_pooled(m.handle, _lib.ptr(xy), log2_res, _lib.ptr(values), pool,
+                                               _lib.ptr(out), stream or _lib.stream_of(xy, out)),
+               "inim_density_pooled")
+
+
+class Cnn:
+    """Owner of an inim_cnn handle (encoder-decoder, 64^2 -> 64^2 x 2)."""
+
+    def __init__(self, seed: int = 0):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check_cnn(lib.inim_cnn_create(seed, ctypes.byref(h)), "inim_cnn_create")
+        self.handle = h.value
+        self.n_params = int(lib.inim_cnn_num_params(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().inim_cnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def inim_cnn_create(seed: int = 0) -> Cnn:
+    return Cnn(seed)
+
+
+def inim_cnn_destroy(c: Cnn) -> None:
+    c.close()
+
+
+def inim_cnn_num_params(c: Cnn = None) -> int:
+    return int(_lib.load().inim_cnn_num_params(c.handle if c else None))
+
+
+def inim_cnn_get_params(c: Cnn, out=None):
+    if out is None:
+        out = np.empty(c.n_params, np.float32)
+    _lib.check_cnn(_lib.load().inim_cnn_get_params(c.handle, _lib.ptr(out), c.n_params), "inim_cnn_get_params")
+    return out
+
+
+def inim_cnn_set_params(c: Cnn, blob) -> None:
+    if isinstance(blob, np.ndarray) or not hasattr(blob, "data_ptr"):
+        blob = np.ascontiguousarray(blob, dtype=np.float32)
+    _lib.check_cnn(_lib.load().inim_cnn_set_params(c.handle, _lib.ptr(blob), c.n_params), "inim_cnn_set_params")
+
+
+def inim_cnn_forward(c: Cnn, x, y, stream=None) -> None:
+    """x [B, 64, 64] f32, y [B, 64, 64, 2] f32; device tensors."""
+    _lib.check_cnn(_lib.load().inim_cnn_forward(c.handle, _lib.ptr(x), int(x.shape[0]), _lib.ptr(y),
+                                                stream or _lib.stream_of(x)), "inim_cnn_forward")
+
+
+def inim_cnn_gradients(c: Cnn, x, y, grads=None, stream=None) -> float:
+    """Mean squared error of the prediction for x against y; its gradient into grads [n_params]."""
+    loss = ctypes.c_float()
+    _lib.check_cnn(_lib.load().inim_cnn_gradients(c.handle, _lib.ptr(x), _lib.ptr(y), int(x.shape[0]),
+                                                  ctypes.byref(loss), _lib.ptr(grads), stream or _lib.stream_of(x)),
+                   "inim_cnn_gradients")
+    return loss.value
+
+
+def inim_cnn_train_step(c: Cnn, x, y, lr: float, stream=None) -> float:
+    """One Adam step; returns the batch loss before the step."""
+    loss = ctypes.c_float()
+    _lib.check_cnn(_lib.load().inim_cnn_train_step(c.handle, _lib.ptr(x), _lib.ptr(y), int(x.shape[0]), lr,
+                                                   ctypes.byref(loss), stream or _lib.stream_of(x)),
+                   "inim_cnn_train_step")
+    return loss.value
+
+
+def inim_warmstart_load(blob) -> None:
+    """Install the network used by params(warm_start=1) (an f32 parameter blob)."""
+    blob = np.ascontiguousarray(blob, dtype=np.float32)
+    _lib.check_cnn(_lib.load().inim_warmstart_load(blob.ctypes.data, blob.nbytes), "inim_warmstart_load")

@@ -106,6 +106,21 @@ _SIGS = {
     "inim_areas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "inim_inims_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "inim_density_pooled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "inim_cnn_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "inim_cnn_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "inim_cnn_num_params": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "inim_cnn_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong]),
+    "inim_cnn_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong]),
+    "inim_cnn_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "inim_cnn_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_float), ctypes.c_void_p, ctypes.c_void_p]),
+    "inim_cnn_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
+    "inim_cnn_last_error": (ctypes.c_char_p, []),
+    "inim_warmstart_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t]),
     "inim_set_scan_tile": (ctypes.c_int, [ctypes.c_int32] * 6),
     "inim_get_scan_tile": (ctypes.c_int, [ctypes.c_int32] * 3 + [ctypes.POINTER(ctypes.c_int32)] * 3),
     "inim_autotune_scan": (ctypes.c_int, [ctypes.POINTER(inim_job), ctypes.c_int32, ctypes.c_int32]),
@@ -175,3 +190,19 @@ def stream_of(*arrays):
             import torch
             return torch.cuda.current_stream(a.device).cuda_stream
     return None
+
+
+
+class CnnError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        super().__init__(f"{where}: {lib.inim_status_string(status).decode()} ({status}) "
+                         f"{lib.inim_cnn_last_error().decode()}")
+        self.status = status
+
+
+def check_cnn(status, where):
+    """Status check for the inim_cnn_* entry points (they keep their own error text)."""
+    if status < 0:
+        raise CnnError(status, where)
+    return status

@@ -230,6 +230,10 @@ struct Batch {
     JobState** d_round_stats = nullptr;
     JobState* d_round_init = nullptr;
     long long total_px = 0;
+    // learned warm start: pooled inputs, predicted fields, per-job field pointers
+    float* ws_in = nullptr;
+    float* ws_out = nullptr;
+    const float** ws_ptrs = nullptr;
 
     void free_rounds() {
         for (auto& p : round_vals) dfree(p);
@@ -242,6 +246,7 @@ struct Batch {
 
     ~Batch() {
         free_rounds();
+        dfree(ws_in); dfree(ws_out); dfree(ws_ptrs);
         dfree(d_bar); dfree(d_err); dfree(all_band.d_map); dfree(all_carry.d_map);
         if (graph) cudaGraphExecDestroy(graph);
         for (auto& b : bufs) b.release();
@@ -618,7 +623,8 @@ int check_params(const inim_params* p) {
     if (p->precision < INIM_FP32 || p->precision > INIM_KAHAN) return fail(INIM_E_ARG, "bad precision");
     if (p->form != INIM_FORM_FUSED && p->form != INIM_FORM_PLAIN) return fail(INIM_E_ARG, "bad form");
     if (p->mode != INIM_DIRECT && p->mode != INIM_CUMULATIVE) return fail(INIM_E_ARG, "bad mode");
-    if (p->warm_start) return fail(INIM_E_STATE, "no warm-start network loaded");
+    if (p->warm_start && !warmstart_loaded()) return fail(INIM_E_STATE, "no warm-start network loaded");
+    if (p->warm_start && p->mode != INIM_DIRECT) return fail(INIM_E_ARG, "the warm start applies to direct steps");
     return INIM_OK;
 }
 
@@ -655,6 +661,39 @@ int fill_stats(const JobState& s, inim_step_stats* out) {
 int worst(int a, int b) {
     if (a < 0 || b < 0) return std::min(a, b);
     return std::max(a, b);
+}
+
+// Learned warm start of the jobs flagged in warm[]: rasterise their start
+// positions, pool log(d/d0) to 64^2, predict the displacement field with the
+// loaded network and move every vertex by it (bilinear).  States and values
+// must be uploaded.
+int apply_warm_start(Batch& B, const std::vector<char>& warm) {
+    const int nj = (int)B.spec.size();
+    std::vector<int> idx;
+    for (int k = 0; k < nj; ++k) if (warm[k]) idx.push_back(k);
+    if (idx.empty()) return INIM_OK;
+    const size_t cell = (size_t)kFieldRes * kFieldRes;
+    if (!B.ws_in) {
+        CUDA_TRY(cudaMalloc(&B.ws_in, nj * cell * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&B.ws_out, nj * cell * 2 * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&B.ws_ptrs, nj * sizeof(float*)));
+    }
+    CUDA_TRY(enqueue_prologue(B, B.stream));
+    CUDA_TRY(launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream));
+    CUDA_TRY(launch_density_table(B.d_jobs, nj, B.stream));
+    for (int q = 0; q < (int)idx.size(); ++q) {
+        const Job& J = B.h_jobs[idx[q]];
+        if (J.n % kFieldRes) return fail(INIM_E_ARG, "warm start needs N >= 64");
+        CUDA_TRY(launch_density_pooled(B.d_jobs + idx[q], J.n, J.n / kFieldRes, B.ws_in + q * cell, B.stream));
+    }
+    const int st = warmstart_predict(B.ws_in, (int)idx.size(), B.ws_out, B.stream);
+    if (st != INIM_OK) return fail(st, "warm-start prediction failed");
+    std::vector<const float*> ptrs(nj, nullptr);
+    for (int q = 0; q < (int)idx.size(); ++q) ptrs[idx[q]] = B.ws_out + q * cell * 2;
+    CUDA_TRY(cudaMemcpyAsync(B.ws_ptrs, ptrs.data(), nj * sizeof(float*), cudaMemcpyHostToDevice, B.stream));
+    CUDA_TRY(launch_apply_field(B.d_jobs, B.vert_blocks, B.ws_ptrs, kFieldRes, 1.0f / kFieldScale, B.stream));
+    CUDA_TRY(cudaStreamSynchronize(B.stream));
+    return INIM_OK;
 }
 
 // Many time series at once (the fused form).  Direct series become T
@@ -712,6 +751,13 @@ int run_series_impl(const inim_series* S, int n) {
         CUDA_TRY(cudaMemcpyAsync(D->d_jobs, D->h_jobs.data(), dspec.size() * sizeof(Job), cudaMemcpyHostToDevice, D->stream));
         CUDA_TRY(cudaMemcpyAsync(D->d_states, D->h_states.data(), dspec.size() * sizeof(JobState),
                                  cudaMemcpyHostToDevice, D->stream));
+        std::vector<char> warm(dspec.size(), 0);
+        bool any_warm = false;
+        for (int k = 0; k < (int)dspec.size(); ++k) any_warm |= (warm[k] = S[dref[k].series].params.warm_start != 0);
+        if (any_warm) {
+            st = apply_warm_start(*D, warm);
+            if (st != INIM_OK) return st;
+        }
         d_async = !poll && !cspec.empty() && !persistent_ok(*D);
         if (d_async) st = enqueue_fused_async(*D, max_it);
         else st = run_fused(*D, max_it, poll);
@@ -1142,6 +1188,40 @@ int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t
     CUDA_TRY(cudaStreamSynchronize(B->stream));
     if (overlap) *overlap = B->h_states[0].overlap;
     if (B->h_states[0].error) return fail(B->h_states[0].error, "raster capacity exceeded");
+    return INIM_OK;
+}
+
+int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, const float* values, int32_t pool,
+                        float* out, void* stream) {
+    if (!map || !xy || !values || !out || pool < 1) return fail(INIM_E_ARG, "NULL argument");
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
+    if (((1 << log2_res) % pool) != 0) return fail(INIM_E_ARG, "pool must divide N");
+    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    int st = INIM_OK;
+    std::vector<JobSpec> spec{JobSpec{map, log2_res, INIM_FP32}};
+    std::vector<const float*> starts{map->h_xy0.data()};
+    Batch* B = get_batch(spec, starts, &st);
+    if (!B) return st;
+    inim_params p;
+    inim_params_default(&p);
+    B->h_states[0] = initial_state(p, 0, 1);
+    B->h_jobs[0].bdv_scale = 1.0f;
+    CUDA_TRY(cudaMemcpyAsync(B->bufs[0].values, values, (size_t)map->n_regions * 4, cudaMemcpyDefault, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, xy, (size_t)map->n_verts * 8, cudaMemcpyDefault, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+    CUDA_TRY(launch_raster_prologue(B->d_jobs, B->edge_blocks, B->stream));
+    CUDA_TRY(launch_raster_main(B->d_jobs, B->edge_blocks, B->row_blocks, B->max_n, B->stream));
+    CUDA_TRY(launch_density_table(B->d_jobs, 1, B->stream));
+    const int m = (1 << log2_res) / pool;
+    float* tmp = nullptr;
+    const bool dev = is_device_ptr(out);
+    if (!dev) CUDA_TRY(cudaMalloc(&tmp, (size_t)m * m * 4));
+    CUDA_TRY(launch_density_pooled(B->d_jobs, 1 << log2_res, pool, dev ? out : tmp, B->stream));
+    if (!dev) CUDA_TRY(cudaMemcpyAsync(out, tmp, (size_t)m * m * 4, cudaMemcpyDeviceToHost, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
+    if (tmp) cudaFree(tmp);
     return INIM_OK;
 }
 

@@ -45,7 +45,61 @@ __global__ void k_finalize_B(const Job* __restrict__ job) {
         B[w + n - 1] = Acc::sub(C, B[w + n - 1]);
 }
 
+// CNN input: mean of log(d / d0) over pool x pool pixel blocks of the label
+// texture (the densities are already relative to d0)
+__global__ void k_density_pooled(const Job* __restrict__ job, int pool, float* __restrict__ out) {
+    const Job& J = *job;
+    const int m = J.n / pool;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m * m) return;
+    const int bi = q % m, bj = q / m;
+    float s = 0.0f;
+    for (int dj = 0; dj < pool; ++dj) {
+        const uint16_t* row = J.labels + (size_t)(bj * pool + dj) * J.n + bi * pool;
+        for (int di = 0; di < pool; ++di) s += logf(fmaxf(J.dens[row[di]], 1e-6f));
+    }
+    out[q] = s / (float)(pool * pool);
+}
+
+// warm start: every vertex moves by the field (m x m cell-centre samples,
+// 2 channels, scaled by inv_scale) interpolated bilinearly at its position
+__global__ void k_apply_field(const Job* __restrict__ jobs, const int2* __restrict__ bmap, const float* const* fields,
+                              int m, float inv_scale) {
+    const int2 bm = bmap[blockIdx.x];
+    const Job& J = jobs[bm.x];
+    const float* f = fields[bm.x];
+    if (!f) return;
+    const int v = bm.y * blockDim.x + threadIdx.x;
+    if (v >= J.n_verts) return;
+    float2 p = J.xy[v];
+    const float fx = p.x * (float)m - 0.5f, fy = p.y * (float)m - 0.5f;
+    const int i0 = min(max((int)floorf(fx), 0), m - 2), j0 = min(max((int)floorf(fy), 0), m - 2);
+    const float a = fminf(fmaxf(fx - (float)i0, 0.0f), 1.0f), b = fminf(fmaxf(fy - (float)j0, 0.0f), 1.0f);
+    const float* c00 = f + ((size_t)j0 * m + i0) * 2;
+    const float* c01 = c00 + 2;
+    const float* c10 = c00 + (size_t)m * 2;
+    const float* c11 = c10 + 2;
+    for (int d = 0; d < 2; ++d) {
+        const float val = (1.0f - b) * ((1.0f - a) * c00[d] + a * c01[d]) + b * ((1.0f - a) * c10[d] + a * c11[d]);
+        if (d == 0) p.x += inv_scale * val; else p.y += inv_scale * val;
+    }
+    J.xy[v] = p;
+}
+
 }  // namespace
+
+cudaError_t launch_density_pooled(const Job* d_job, int n, int pool, float* out, cudaStream_t s) {
+    const int m = n / pool;
+    k_density_pooled<<<(m * m + 255) / 256, 256, 0, s>>>(d_job, pool, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_field(const Job* d_jobs, const BlockMap& vert_blocks, const float* const* fields, int m,
+                               float inv_scale, cudaStream_t s) {
+    if (vert_blocks.n_blocks)
+        k_apply_field<<<vert_blocks.n_blocks, 256, 0, s>>>(d_jobs, vert_blocks.d_map, fields, m, inv_scale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gather(const Job* d_jobs, const BlockMap& vert_blocks, int precision, cudaStream_t s) {
     if (!vert_blocks.n_blocks) return cudaSuccess;

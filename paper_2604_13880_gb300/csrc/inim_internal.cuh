@@ -210,6 +210,15 @@ cudaError_t launch_persistent(Job* d_jobs, int n_jobs, const BlockMap& edge, con
                               JobState* round_init, JobState* const* round_stats, unsigned* bar, int* err,
                               int max_n, int max_blocks, unsigned long long* phase_ns, cudaStream_t s);
 
+// learned warm start
+constexpr int kFieldRes = 64;          // CNN input / output resolution
+constexpr float kFieldScale = 10.0f;   // the CNN predicts 10 x the displacement
+cudaError_t launch_density_pooled(const Job* d_job, int n, int pool, float* out, cudaStream_t s);
+cudaError_t launch_apply_field(const Job* d_jobs, const BlockMap& vert_blocks, const float* const* fields, int m,
+                               float inv_scale, cudaStream_t s);
+int warmstart_predict(const float* x, int B, float* y, cudaStream_t s);
+bool warmstart_loaded();
+
 // plain (unfused) form: extra full textures of one job
 struct PlainWork {
     float*  d   = nullptr;   // [n*n] density

@@ -1,0 +1,183 @@
+"""GPU parity of the learned warm start (no counterpart in the paper).
+
+The network's forward pass and its parameter gradients on the BF16 tensor
+cores against the FP64 oracle network with the same parameters; the pooled
+log-density input against the oracle's density texture; training lowers the
+loss; a warm-started solve with an untrained (zero) field equals a cold one.
+
+Tolerances follow from BF16 rounding: unit roundoff u = 2^-9 on the network
+input, every weight and every stored activation (and, backwards, every stored
+activation gradient).  14 convolutions plus 3 skip additions give about 40
+independent roundings on the forward path, whose relative effects add like a
+random walk: sqrt(40) * u = 1.2e-2 expected relative L2 error of the output;
+the bound used is 3e-2 (2.5 sigma).  The backward path doubles the count and
+adds ReLU mask flips where a pre-activation is within rounding of 0: 6e-2
+per layer gradient, cosine similarity >= 0.998 over the whole blob.
+Accumulation is FP32 throughout (its error, ~1e-6 relative, is negligible).
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as C
+from oracle import inim_oracle as O
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def _P():
+    import paper_2604_13880_gb300 as P
+    return P
+
+
+def _fields(B, seed, scale=1.0):
+    """Smooth random log-density-like inputs [B, 64, 64] (sums of Gaussian bumps)."""
+    rng = np.random.default_rng(seed)
+    c = (np.arange(64) + 0.5) / 64
+    y, x = np.meshgrid(c, c, indexing="ij")
+    out = np.zeros((B, 64, 64))
+    for b in range(B):
+        for _ in range(12):
+            cx, cy, s, a = rng.uniform(0, 1), rng.uniform(0, 1), rng.uniform(0.03, 0.2), rng.normal(0, 1)
+            out[b] += a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * s * s))
+    return scale * (out + 0.05 * rng.normal(size=out.shape))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _cos(a, b):
+    return float(np.dot(a.ravel(), b.ravel()) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+@pytest.fixture(scope="module")
+def net():
+    P = _P()
+    c = P.inim_cnn_create(0)
+    yield c
+    c.close()
+
+
+def test_params_roundtrip(net):
+    P = _P()
+    assert P.inim_cnn_num_params(net) == C.n_params() == P.inim_cnn_num_params()
+    blob = C.he_init(5).astype(np.float32)
+    P.inim_cnn_set_params(net, blob)
+    assert np.array_equal(P.inim_cnn_get_params(net), blob)
+
+
+@pytest.mark.parametrize("B,seed", [(1, 11), (3, 12)])
+def test_forward_matches_oracle(net, B, seed):
+    P = _P()
+    blob = C.he_init(seed).astype(np.float32)
+    P.inim_cnn_set_params(net, blob)
+    x = _fields(B, seed)
+    xd = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    yd = torch.empty((B, 64, 64, 2), dtype=torch.float32, device="cuda")
+    P.inim_cnn_forward(net, xd, yd)
+    got = yd.cpu().numpy().astype(np.float64)
+    want, _ = C.forward(blob.astype(np.float64), x.astype(np.float32).astype(np.float64))
+    assert np.isfinite(got).all()
+    err = _rel(got, want)
+    assert err < 3e-2 and _cos(got, want) > 0.999, (err, _cos(got, want))
+    # each sample of the batch is computed independently
+    if B > 1:
+        y1 = torch.empty((1, 64, 64, 2), dtype=torch.float32, device="cuda")
+        P.inim_cnn_forward(net, xd[1:2].contiguous(), y1)
+        assert np.array_equal(y1.cpu().numpy()[0], got[1].astype(np.float32))
+
+
+def test_gradients_match_oracle(net):
+    P = _P()
+    blob = C.he_init(21).astype(np.float32)
+    P.inim_cnn_set_params(net, blob)
+    B = 2
+    x = _fields(B, 21)
+    rng = np.random.default_rng(22)
+    target = 0.3 * _fields(2 * B, 23).reshape(B, 2, 64, 64).transpose(0, 2, 3, 1) + 0.01 * rng.normal(size=(B, 64, 64, 2))
+    xd = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    td = torch.as_tensor(target, dtype=torch.float32, device="cuda").contiguous()
+    gd = torch.empty(C.n_params(), dtype=torch.float32, device="cuda")
+    loss = P.inim_cnn_gradients(net, xd, td, gd)
+    g = gd.cpu().numpy().astype(np.float64)
+    want_loss, want = C.loss_and_grads(blob.astype(np.float64), x.astype(np.float32).astype(np.float64),
+                                       target.astype(np.float32).astype(np.float64))
+    assert abs(loss - want_loss) <= 2e-2 * want_loss, (loss, want_loss)
+    assert _cos(g, want) > 0.998, _cos(g, want)
+    off = 0
+    for k, (ci, co, _) in enumerate(C.LAYERS):
+        nw = co * 9 * ci
+        ew = _rel(g[off:off + nw], want[off:off + nw])
+        eb = _rel(g[off + nw:off + nw + co], want[off + nw:off + nw + co])
+        assert ew < 6e-2 and eb < 6e-2, (k, ew, eb)
+        off += nw + co
+
+
+def test_training_lowers_loss():
+    P = _P()
+    c = P.inim_cnn_create(3)
+    B = 8
+    x = _fields(B, 31)
+    # a learnable target: a smooth field derived from the input's gradient
+    gy, gx = np.gradient(x, axis=(1, 2))
+    t = 0.5 * np.stack([-gx, -gy], axis=-1) * 64 / 8
+    xd = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    td = torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
+    losses = [P.inim_cnn_train_step(c, xd, td, 1e-3) for _ in range(80)]
+    c.close()
+    assert all(np.isfinite(losses))
+    assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
+
+
+def test_density_pooled_matches_oracle():
+    P = _P()
+    from paper_2604_13880_gb300 import synth
+    mesh = synth.voronoi_map(60, 3000, seed=41, jitter=0.2)
+    vals = synth.lognormal_values(60, seed=42)
+    k, pool = 9, 8
+    m = P.inim_map_create(mesh)
+    out = np.empty((64, 64), np.float32)
+    P.inim_density_pooled(m, mesh.verts_f32(), k, vals.astype(np.float32), pool, out)
+    lab, cnt, _ = O.labels_scanline(mesh.verts_f32().astype(np.float64), mesh.ring_off, mesh.ring_idx,
+                                    mesh.ring_region, mesh.n_regions, k)
+    want = O.pooled_log_density(lab, cnt, vals.astype(np.float32).astype(np.float64), pool)
+    # f32 density ratios and logs, 64 f32 additions per block
+    assert np.abs(out - want).max() < 5e-5, np.abs(out - want).max()
+    # device buffers give the same result
+    xd = torch.as_tensor(mesh.verts_f32(), device="cuda")
+    vd = torch.as_tensor(vals.astype(np.float32), device="cuda")
+    od = torch.empty((64, 64), dtype=torch.float32, device="cuda")
+    P.inim_density_pooled(m, xd, k, vd, pool, od)
+    torch.cuda.synchronize()
+    assert np.array_equal(od.cpu().numpy(), out)
+    m.close()
+
+
+def test_zero_field_warm_start_equals_cold():
+    # a network whose head is all zeros predicts a zero field: the warm-started
+    # direct step must then follow the cold one exactly
+    P = _P()
+    from paper_2604_13880_gb300 import synth
+    blob = C.he_init(7).astype(np.float32)
+    ci, co, _ = C.LAYERS[-1]
+    blob[-(co * 9 * ci + co):] = 0.0
+    P.inim_warmstart_load(blob)
+    mesh = synth.voronoi_map(40, 2000, seed=51)
+    vals = synth.lognormal_values(40, seed=52)[None].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    res = []
+    for warm in (0, 1):
+        p = P.params(log2_res=9, shape=0.5, max_iters=20, warm_start=warm)
+        outs, stats, _ = P.inim_run_series([dict(map=m, values=vals, params=p)])
+        res.append((outs[0], stats[0][0]))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1]["iters"] == res[1][1]["iters"]
+    m.close()
+
+
+def test_warm_start_argument_errors():
+    P = _P()
+    with pytest.raises(RuntimeError):
+        P.inim_warmstart_load(np.zeros(10, np.float32))

@@ -1,0 +1,77 @@
+"""Pins of the CPU oracle of the warm-start network."""
+import numpy as np
+
+from oracle import cnn_oracle as C
+
+
+def test_conv_matches_its_definition():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(2, 4, 5, 3))
+    w = rng.normal(size=(4, 9, 3))
+    b = rng.normal(size=4)
+    y = C.conv3x3(x, w, b)
+    N, H, W, Ci = x.shape
+    ref = np.zeros((N, H, W, 4))
+    for n in range(N):
+        for i in range(H):
+            for j in range(W):
+                for o in range(4):
+                    s = b[o]
+                    for dy in range(3):
+                        for dx in range(3):
+                            ii, jj = i + dy - 1, j + dx - 1
+                            if 0 <= ii < H and 0 <= jj < W:
+                                s += (x[n, ii, jj] * w[o, 3 * dy + dx]).sum()
+                    ref[n, i, j, o] = s
+    np.testing.assert_allclose(y, ref, atol=1e-12)
+
+
+def test_conv_backward_finite_differences():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(1, 5, 4, 2))
+    w = rng.normal(size=(3, 9, 2))
+    b = rng.normal(size=3)
+    gy = rng.normal(size=(1, 5, 4, 3))
+    gx, gw, gb = C.conv3x3_backward(x, w, gy)
+    f = lambda x_, w_, b_: (C.conv3x3(x_, w_, b_) * gy).sum()          # noqa: E731
+    h = 1e-6
+    for idx in [(0, 0, 0, 0), (0, 4, 3, 1), (0, 2, 1, 0)]:
+        d = np.zeros_like(x); d[idx] = h
+        assert abs((f(x + d, w, b) - f(x - d, w, b)) / (2 * h) - gx[idx]) < 1e-6
+    for idx in [(0, 0, 0), (2, 8, 1), (1, 4, 0)]:
+        d = np.zeros_like(w); d[idx] = h
+        assert abs((f(x, w + d, b) - f(x, w - d, b)) / (2 * h) - gw[idx]) < 1e-6
+    d = np.zeros_like(b); d[1] = h
+    assert abs((f(x, w, b + d) - f(x, w, b - d)) / (2 * h) - gb[1]) < 1e-6
+
+
+def test_pool_and_upsample_adjoints():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(1, 8, 6, 3))
+    y = rng.normal(size=(1, 4, 3, 3))
+    assert abs((C.pool2(x) * y).sum() - (x * C.pool2_backward(y)).sum()) < 1e-12
+    z = rng.normal(size=(1, 8, 6, 3))
+    assert abs((C.up2(y) * z).sum() - (y * C.up2_backward(z)).sum()) < 1e-12
+
+
+def test_network_gradient_finite_differences():
+    params = C.he_init(3)
+    assert params.size == C.n_params() == 1163234
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(1, 16, 16))
+    t = rng.normal(size=(1, 16, 16, 2)) * 0.1
+    loss, g = C.loss_and_grads(params, x, t)
+    # one parameter of every layer (weights and biases), central differences
+    h = 1e-5
+    off = 0
+    checked = 0
+    for ci, co, _ in C.LAYERS:
+        for k in (off + (co * 9 * ci) // 3, off + co * 9 * ci):        # a weight, the first bias
+            p1, p2 = params.copy(), params.copy()
+            p1[k] += h
+            p2[k] -= h
+            fd = (C.loss_and_grads(p1, x, t)[0] - C.loss_and_grads(p2, x, t)[0]) / (2 * h)
+            assert abs(fd - g[k]) <= 1e-6 + 1e-4 * abs(fd), (k, fd, g[k])
+            checked += 1
+        off += co * 9 * ci + co
+    assert checked == 28 and loss > 0

@@ -104,3 +104,28 @@ def test_run_direct_vs_cumulative():
     # a direct step equals a fresh single-step run on that step's values
     x1, _ = O.run(m, vals[1:2], 6, max_iters=5, xi_stop=0, stall_window=0)
     np.testing.assert_array_equal(xd[1], x1[0])
+
+
+def test_pooled_log_density_closed_forms():
+    # uniform density (s proportional to o): log(d / d0) = 0 in every block
+    m = synth.voronoi_map(12, 500, seed=4)
+    lab, cnt, _ = O.labels_scanline(m.verts, *_arrays(m), 6)
+    assert np.abs(O.pooled_log_density(lab, cnt, 3.0 * cnt, 8)).max() < 1e-12
+    # two half-plane regions: left density 3 units, right 1 unit, no
+    # background -> d0 = 2, blocks are log(3/2) on the left, log(1/2) on the right
+    N, pool = 16, 4
+    lab = np.zeros((N, N), np.int64)
+    lab[:, N // 2:] = 1
+    cnt = np.array([N * N // 2, N * N // 2])
+    out = O.pooled_log_density(lab, cnt, np.array([3.0, 1.0]) * cnt, pool)
+    assert out.shape == (N // pool, N // pool)
+    assert np.allclose(out[:, :2], np.log(1.5)) and np.allclose(out[:, 2:], np.log(0.5))
+    # a block straddling the boundary averages the logs of its pixels
+    out2 = O.pooled_log_density(lab, cnt, np.array([3.0, 1.0]) * cnt, 16)
+    assert np.isclose(out2[0, 0], 0.5 * (np.log(1.5) + np.log(0.5)))
+    # a region without pixels contributes nothing; the background takes bdv_scale * d0
+    lab3 = np.full((N, N), O.BACKGROUND)
+    lab3[:8] = 0
+    cnt3 = np.array([128, 0])
+    out3 = O.pooled_log_density(lab3, cnt3, np.array([5.0, 1.0]), 8, bdv_scale=0.25)
+    assert np.allclose(out3[0], 0.0) and np.allclose(out3[1], np.log(0.25))
