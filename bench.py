@@ -41,6 +41,19 @@ METRIC = "InIm iterations/s"
 WORKLOAD = "voronoi200_v50k_res1024_T24_it50_shapes3_direct+cumulative"
 
 
+def crossings_count(mesh, N):
+    """Crossing keys of one raster of the map at its start positions: for
+    every ring edge, the texture rows whose pixel centres it spans."""
+    y = mesh.verts[:, 1]
+    K = 0
+    for r in range(len(mesh.ring_off) - 1):
+        ids = mesh.ring_idx[mesh.ring_off[r]:mesh.ring_off[r + 1]]
+        y0, y1 = y[ids], y[np.roll(ids, -1)]
+        lo, hi = np.minimum(y0, y1), np.maximum(y0, y1)
+        K += int(np.maximum(np.ceil(hi * N - 0.5) - np.ceil(lo * N - 0.5), 0).sum())
+    return K
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -330,17 +343,18 @@ def main():
         stages = P.inim_profile_stages(reps=10)
         N = 1 << k
         Ppx = N * N
-        nb = N // 16
+        nb = -(-N // tiles["large"]["band_rows"])            # bands of the 72-solve batch's tile
         n_jobs = len(SHAPES) * T_STEPS
         E = int(P.inim_map_info(m)["n_edges"])
+        K = crossings_count(mesh, N)
         algo = {   # algorithmic bytes per launch over the whole batch (design notes)
-            "raster": n_jobs * (2 * Ppx + 2 * 8 * E),
+            "raster": n_jobs * (8 * E + 8 * V + 8 * K + 2 * Ppx),
             "density_table": n_jobs * (12 * R),
             "scan_phase1": n_jobs * (2 * Ppx + 3 * nb * N * 4),
             "scan_carry": n_jobs * (2 * 3 * nb * N * 4),
             "scan_phase3": n_jobs * (2 * Ppx + 8 * Ppx + 3 * nb * N * 4),
             "gather_move": n_jobs * 48 * V,
-            "areas_errors": n_jobs * 16 * E,
+            "areas_errors": n_jobs * (8 * E + 8 * V + 8 * R),
         }
         dom = max(stages, key=stages.get)
         pk = peaks()

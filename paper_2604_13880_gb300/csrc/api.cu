@@ -5,6 +5,7 @@
 #include <atomic>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <memory>
@@ -78,10 +79,9 @@ size_t elem_size(int precision) { return precision == INIM_FP32 ? 4 : 8; }
 constexpr int kRowsPerBlock = 8;     // rows of one k_raster_rows block (one warp each)
 
 struct Buffers {
-    int n = 0, precision = 0, R = 0, key_cap = 0, nb = 0, V = 0;
+    int n = 0, precision = 0, R = 0, nb = 0, V = 0;
     uint16_t* labels = nullptr;
     int* row_cnt = nullptr;
-    int* row_off = nullptr;
     int* big_rows = nullptr;
     uint32_t* keys = nullptr;
     int* counts = nullptr;
@@ -97,16 +97,15 @@ struct Buffers {
     double* areas = nullptr;
     float2* xy = nullptr;
 
-    cudaError_t alloc(int n_, int prec, int R_, int V_, int key_cap_, int nb_, bool interleaved) {
-        n = n_; precision = prec; R = R_; V = V_; key_cap = key_cap_; nb = nb_;
+    cudaError_t alloc(int n_, int prec, int R_, int V_, int nb_, bool interleaved) {
+        n = n_; precision = prec; R = R_; V = V_; nb = nb_;
         const size_t np = (size_t)n * n, es = elem_size(prec);
         cudaError_t e = cudaSuccess;
         auto A_ = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes < 16 ? 16 : bytes); };
         A_((void**)&labels, np * 2);
         A_((void**)&row_cnt, (size_t)n * 4);
-        A_((void**)&row_off, (size_t)(n + 1) * 4);
         A_((void**)&big_rows, (size_t)n * 4);
-        A_((void**)&keys, (size_t)key_cap * 4);
+        A_((void**)&keys, (size_t)n * kKeyStride * 4);     // one fixed-stride bucket per row
         A_((void**)&counts, (size_t)(R + 1) * 4);
         A_((void**)&dens, (size_t)(R + 1) * 4);
         A_((void**)&values, (size_t)R * 4);
@@ -124,7 +123,7 @@ struct Buffers {
         return e;
     }
     void release() {
-        dfree(labels); dfree(row_cnt); dfree(row_off); dfree(big_rows); dfree(keys); dfree(counts); dfree(dens);
+        dfree(labels); dfree(row_cnt); dfree(big_rows); dfree(keys); dfree(counts); dfree(dens);
         dfree(values); dfree(S); dfree(T); dfree(A); dfree(B); dfree(rowcum); dfree(agg);
         dfree(carry); dfree(areas); dfree(xy);
     }
@@ -168,19 +167,6 @@ bool tile_valid(int log2n, ScanTile t) {
     return pair && h && t.cpt * t.nt == n && t.H * 4 <= n;
 }
 
-int estimate_key_cap(const inim_map* m, const float* xy_host, int n) {
-    // crossings of every edge with the rows, from the start positions, with
-    // a generous margin for stretching during the iteration
-    double rows = 0.0;
-    for (int e = 0; e < m->n_edges; ++e) {
-        const int a = m->h_edge_a[e], b = m->h_edge_b[e];
-        rows += std::fabs((double)xy_host[2 * a + 1] - (double)xy_host[2 * b + 1]) * n + 1.0;
-    }
-    double cap = 4.0 * rows + 4.0 * n + 1024.0;
-    if (cap > 2.0e9) cap = 2.0e9;
-    return (int)cap;
-}
-
 // ---------------------------------------------------------------------------
 // batch: jobs + buffers + block maps (+ a captured CUDA graph)
 // ---------------------------------------------------------------------------
@@ -213,6 +199,7 @@ struct Batch {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph1 = nullptr;    // one iteration, for the tail of a fixed-length run
     int graph_iters = 0;
     std::vector<PlainWork> plain;   // per job (plain form only)
     // persistent form: all resolution groups' band / carry items, barrier words,
@@ -249,6 +236,7 @@ struct Batch {
         dfree(ws_in); dfree(ws_out); dfree(ws_ptrs);
         dfree(d_bar); dfree(d_err); dfree(all_band.d_map); dfree(all_carry.d_map);
         if (graph) cudaGraphExecDestroy(graph);
+        if (graph1) cudaGraphExecDestroy(graph1);
         for (auto& b : bufs) b.release();
         for (auto& p : plain) plain_free(p);
         dfree(d_jobs); dfree(d_states);
@@ -268,12 +256,21 @@ cudaError_t make_map(BlockMap& bm, const std::vector<int2>& entries) {
     return e;
 }
 
-int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<const float*>& start_xy_host,
+int build_batch(Batch& B, const std::vector<JobSpec>& spec,
                 int min_H = 0) {
     B.spec = spec;
     const int nj = (int)spec.size();
     B.precision = spec[0].precision;
-    CUDA_TRY(cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking));
+    // Small batches are latency-bound chains of short kernels (a cumulative
+    // series advances one iteration at a time); they get the highest stream
+    // priority so that, next to a large batch on another stream, their blocks
+    // are scheduled first and the large batch fills the remaining SMs.
+    long long total_px = 0;
+    for (auto& sp : spec) total_px += 1LL << (2 * sp.log2n);
+    int prio_least = 0, prio_greatest = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    CUDA_TRY(cudaStreamCreateWithPriority(&B.stream, cudaStreamNonBlocking,
+                                          size_class(total_px) == 0 ? prio_greatest : prio_least));
     CUDA_TRY(cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming));
     CUDA_TRY(cudaMalloc(&B.d_jobs, nj * sizeof(Job)));
     CUDA_TRY(cudaMalloc(&B.d_states, nj * sizeof(JobState)));
@@ -290,9 +287,8 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
         const ScanTile tile = tile_for(s.log2n, s.precision, size_class(group_px[s.log2n]));
         const int nb = (n + tile.H - 1) / tile.H;
         const int nb_alloc = min_H > 0 ? (n + min_H - 1) / min_H : nb;
-        const int cap = m ? estimate_key_cap(m, start_xy_host[k] ? start_xy_host[k] : m->h_xy0.data(), n) : 16;
         Buffers& b = B.bufs[k];
-        CUDA_TRY(b.alloc(n, s.precision, m ? m->n_regions : 1, m ? m->n_verts : 1, cap, nb_alloc, m != nullptr));
+        CUDA_TRY(b.alloc(n, s.precision, m ? m->n_regions : 1, m ? m->n_verts : 1, nb_alloc, m != nullptr));
         Job J{};
         J.n = n; J.log2n = s.log2n;
         if (m) {
@@ -302,8 +298,8 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
             J.reg_rings = m->reg_rings; J.ring_off = m->ring_off; J.ring_idx = m->ring_idx; J.sign0 = m->sign0;
         }
         J.xy = b.xy; J.values = b.values; J.lam = 1.0f; J.bdv_scale = 1.0f; J.precision = s.precision;
-        J.labels = b.labels; J.row_cnt = b.row_cnt; J.row_off = b.row_off; J.big_rows = b.big_rows;
-        J.keys = b.keys; J.key_cap = cap;
+        J.labels = b.labels; J.row_cnt = b.row_cnt; J.big_rows = b.big_rows;
+        J.keys = b.keys;
         J.counts = b.counts; J.dens = b.dens;
         J.S = b.S; J.T = b.T; J.A = b.A; J.B = b.B; J.rowcum = b.rowcum;
         // map jobs: one interleaved (S, T) table (S's buffer holds both halves)
@@ -314,7 +310,8 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
         if (m) {
             for (int q = 0; q < (m->n_edges + 255) / 256; ++q) eb.push_back(make_int2(k, q));
             for (int q = 0; q < (m->n_verts + 255) / 256; ++q) vb.push_back(make_int2(k, q));
-            for (int q = 0; q < (m->n_regions + 7) / 8; ++q) gb.push_back(make_int2(k, q));
+            const int rpb = 8 >> area_warps_log2(m->n_edges, m->n_regions);   // regions per area block
+            for (int q = 0; q < (m->n_regions + rpb - 1) / rpb; ++q) gb.push_back(make_int2(k, q));
         }
         jb.push_back(make_int2(k, 0));
         for (int j = 0; j < n; j += kRowsPerBlock) rb.push_back(make_int2(k, j));
@@ -345,8 +342,9 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
             if (spec[k].log2n != l) continue;
             const Job& J = B.h_jobs[k];
             for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
-            const int len = carry_qspace(J.n, J.nb, J.H);          // q values, 256 per block
-            for (int q = 0; q < (len + 255) / 256; ++q) carry.push_back(make_int2(k, q));
+            const int len = carry_qspace(J.n, J.nb, J.H);
+            const int qpb = carry_q_per_block(J.nb);
+            for (int q = 0; q < (len + qpb - 1) / qpb; ++q) carry.push_back(make_int2(k, q));
         }
         if (band.empty()) continue;
         Group g;
@@ -354,6 +352,7 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec, const std::vector<co
         g.tile = tile_for(l, B.precision, size_class(group_px[l]));
         CUDA_TRY(make_map(g.band, band));
         CUDA_TRY(make_map(g.carry, carry));
+        g.carry.q_per_block = carry_q_per_block(((1 << l) + g.tile.H - 1) / g.tile.H);
         B.groups.push_back(g);
     }
     CUDA_TRY(cudaMemcpy(B.d_jobs, B.h_jobs.data(), nj * sizeof(Job), cudaMemcpyHostToDevice));
@@ -365,7 +364,7 @@ std::mutex g_cache_mu;
 std::list<std::unique_ptr<Batch>> g_cache;
 constexpr size_t kCacheMax = 6;
 
-Batch* get_batch(const std::vector<JobSpec>& spec, const std::vector<const float*>& start_xy_host, int* status) {
+Batch* get_batch(const std::vector<JobSpec>& spec, int* status) {
     for (auto it = g_cache.begin(); it != g_cache.end(); ++it) {
         if ((*it)->spec == spec) {
             g_cache.splice(g_cache.begin(), g_cache, it);
@@ -374,7 +373,7 @@ Batch* get_batch(const std::vector<JobSpec>& spec, const std::vector<const float
         }
     }
     auto b = std::make_unique<Batch>();
-    *status = build_batch(*b, spec, start_xy_host);
+    *status = build_batch(*b, spec);
     if (*status != INIM_OK) return nullptr;
     g_cache.push_front(std::move(b));
     while (g_cache.size() > kCacheMax) g_cache.pop_back();
@@ -396,12 +395,14 @@ int retile_group(Batch& B, Group& g, ScanTile t) {
         J.nb = (J.n + t.H - 1) / t.H;
         for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
         const int len = carry_qspace(J.n, J.nb, J.H);
-        for (int q = 0; q < (len + 255) / 256; ++q) carry.push_back(make_int2(k, q));
+        const int qpb = carry_q_per_block(J.nb);
+        for (int q = 0; q < (len + qpb - 1) / qpb; ++q) carry.push_back(make_int2(k, q));
     }
     dfree(g.band.d_map);
     dfree(g.carry.d_map);
     CUDA_TRY(make_map(g.band, band));
     CUDA_TRY(make_map(g.carry, carry));
+    g.carry.q_per_block = carry_q_per_block((1 << g.log2n) / t.H);
     g.tile = t;
     CUDA_TRY(cudaMemcpyAsync(B.d_jobs, B.h_jobs.data(), B.h_jobs.size() * sizeof(Job), cudaMemcpyHostToDevice,
                              B.stream));
@@ -423,11 +424,10 @@ void purge_map(const inim_map* m) {
 // ---------------------------------------------------------------------------
 // the first iteration of a run needs the row histogram of the start positions
 cudaError_t enqueue_prologue(Batch& B, cudaStream_t s) {
-    return launch_raster_prologue(B.d_jobs, B.edge_blocks, s);
+    return launch_raster_prologue(B.d_jobs, (int)B.spec.size(), B.edge_blocks, s);
 }
 
-// one fused iteration; its area kernel leaves the next iteration's row
-// histogram and offsets in place
+// one fused iteration
 cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s) {
     cudaError_t e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, s);
     if (e == cudaSuccess) e = launch_density_table(B.d_jobs, (int)B.spec.size(), s);
@@ -438,7 +438,7 @@ cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s) {
         else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
     }
     if (e == cudaSuccess) e = launch_gather(B.d_jobs, B.vert_blocks, B.precision, s);
-    if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, (int)B.spec.size(), B.region_blocks, 1, 1, s);
+    if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, B.region_blocks, 1, s);
     return e;
 }
 
@@ -446,30 +446,66 @@ constexpr int kGraphIters = 8;
 
 std::atomic<long long> g_launches{0};
 
+}  // namespace
+
+bool inim::pdl_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("INIM_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+namespace {
+
 int kernels_per_fused_iteration(const Batch& B) {
-    int k = 1 + (B.edge_blocks.n_blocks ? 1 : 0);          // crossings, rows
+    int k = 1 + (B.edge_blocks.n_blocks ? 1 : 0);          // crossing keys, rows
     k += 1;                                                  // density table (+ big rows)
     k += 3 * (int)B.groups.size();                           // scan phases 1-3
     k += B.vert_blocks.n_blocks ? 1 : 0;                     // gather / move
-    k += B.region_blocks.n_blocks ? 1 : 0;                   // areas + errors + next histogram
+    k += B.region_blocks.n_blocks ? 1 : 0;                   // areas + errors + stop rule
     return k;
 }
 constexpr int kKernelsPerPlainIteration = 15;
 
-int ensure_graph(Batch& B) {
-    if (B.graph) return INIM_OK;
+cudaError_t capture_iterations(Batch& B, int iters, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
-    CUDA_TRY(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = enqueue_fused_iteration(B, B.stream);
-    cudaError_t e2 = cudaStreamEndCapture(B.stream, &g);
-    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail(INIM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e)); }
-    if (e2 != cudaSuccess) return fail(INIM_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
-    e = cudaGraphInstantiate(&B.graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { B.graph = nullptr; return fail(INIM_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+    cudaError_t e = cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) e = enqueue_fused_iteration(B, B.stream);
+    const cudaError_t e2 = cudaStreamEndCapture(B.stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) *out = nullptr;
+    return e;
+}
+
+int ensure_graph(Batch& B) {
+    if (B.graph && B.graph1) return INIM_OK;
+    cudaError_t e = capture_iterations(B, kGraphIters, &B.graph);
+    if (e == cudaSuccess) e = capture_iterations(B, 1, &B.graph1);
+    if (e != cudaSuccess) return fail(INIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     B.graph_iters = kGraphIters;
     return INIM_OK;
+}
+
+// launch the graphs for `iters` more iterations: full replays, then the
+// one-iteration graph for the remainder (no idle iterations at the end)
+cudaError_t launch_iterations(Batch& B, int iters) {
+    const int per = kernels_per_fused_iteration(B);
+    while (iters >= B.graph_iters) {
+        cudaError_t e = cudaGraphLaunch(B.graph, B.stream);
+        if (e != cudaSuccess) return e;
+        g_launches += (long long)B.graph_iters * per;
+        iters -= B.graph_iters;
+    }
+    for (; iters > 0; --iters) {
+        cudaError_t e = cudaGraphLaunch(B.graph1, B.stream);
+        if (e != cudaSuccess) return e;
+        g_launches += per;
+    }
+    return cudaSuccess;
 }
 
 JobState initial_state(const inim_params& p, int stop_on_rule, int max_iters) {
@@ -551,11 +587,8 @@ int enqueue_fused_async(Batch& B, int max_iters) {
     int st = ensure_graph(B);
     if (st != INIM_OK) return st;
     CUDA_TRY(enqueue_prologue(B, B.stream));
-    g_launches += B.edge_blocks.n_blocks ? 1 : 0;
-    for (int done = 0; done < max_iters; done += B.graph_iters) {
-        CUDA_TRY(cudaGraphLaunch(B.graph, B.stream));
-        g_launches += (long long)B.graph_iters * kernels_per_fused_iteration(B);
-    }
+    g_launches += 1;                                       // bucket reset
+    CUDA_TRY(launch_iterations(B, max_iters));
     return INIM_OK;
 }
 
@@ -570,12 +603,12 @@ int run_fused(Batch& B, int max_iters, bool poll) {
     int st = ensure_graph(B);
     if (st != INIM_OK) return st;
     CUDA_TRY(enqueue_prologue(B, B.stream));
-    g_launches += B.edge_blocks.n_blocks ? 1 : 0;
+    g_launches += 1;                                       // bucket reset
     int done = 0;
     while (done < max_iters) {
-        CUDA_TRY(cudaGraphLaunch(B.graph, B.stream));
-        g_launches += (long long)B.graph_iters * kernels_per_fused_iteration(B);
-        done += B.graph_iters;
+        const int step = std::min(B.graph_iters, max_iters - done);
+        CUDA_TRY(launch_iterations(B, step));
+        done += step;
         if (poll && done < max_iters) {
             CUDA_TRY(cudaMemcpyAsync(B.h_states.data(), B.d_states, nj * sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
             CUDA_TRY(cudaStreamSynchronize(B.stream));
@@ -600,11 +633,11 @@ int run_plain(Batch& B, int max_iters) {
     for (int k = 0; k < nj; ++k) {
         const Job* dj = B.d_jobs + k;
         for (int it = 0; it < max_iters; ++it) {
-            CUDA_TRY(launch_raster_prologue(B.d_jobs, B.edge_blocks, B.stream));
+            CUDA_TRY(launch_raster_prologue(B.d_jobs, (int)B.spec.size(), B.edge_blocks, B.stream));
             CUDA_TRY(launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream));
             CUDA_TRY(launch_density_table(dj, 1, B.stream));
             CUDA_TRY(plain_iteration(dj, B.h_jobs[k], B.plain[k], B.stream));
-            CUDA_TRY(launch_areas_errors(B.d_jobs, nj, B.region_blocks, 1, 0, B.stream));
+            CUDA_TRY(launch_areas_errors(B.d_jobs, B.region_blocks, 1, B.stream));
             g_launches += kKernelsPerPlainIteration;
             CUDA_TRY(cudaMemcpyAsync(&B.h_states[k], B.d_states + k, sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
             CUDA_TRY(cudaStreamSynchronize(B.stream));
@@ -705,16 +738,15 @@ int run_series_impl(const inim_series* S, int n) {
     struct Ref { int series, t; };
     std::vector<JobSpec> dspec, cspec;
     std::vector<Ref> dref, cref;
-    std::vector<const float*> dcap, ccap;
     for (int i = 0; i < n; ++i) {
         const inim_series& x = S[i];
         const JobSpec sp{x.map, x.params.log2_res, x.params.precision};
         if (x.params.mode == INIM_DIRECT) {
             for (int t = 0; t < x.T; ++t) {
-                dspec.push_back(sp); dref.push_back({i, t}); dcap.push_back(x.map->h_xy0.data());
+                dspec.push_back(sp); dref.push_back({i, t});
             }
         } else {
-            cspec.push_back(sp); cref.push_back({i, 0}); ccap.push_back(x.map->h_xy0.data());
+            cspec.push_back(sp); cref.push_back({i, 0});
         }
     }
     int st = INIM_OK;
@@ -737,7 +769,7 @@ int run_series_impl(const inim_series* S, int n) {
     Batch* D = nullptr;
     bool d_async = false;
     if (!dspec.empty()) {
-        D = get_batch(dspec, dcap, &st);
+        D = get_batch(dspec, &st);
         if (!D) return st;
         int max_it = 1;
         bool poll = false;
@@ -787,7 +819,7 @@ int run_series_impl(const inim_series* S, int n) {
         if (st != INIM_OK) return st;
     }
     if (!cspec.empty()) {
-        Batch* B = get_batch(cspec, ccap, &st);
+        Batch* B = get_batch(cspec, &st);
         if (!B) return st;
         const int nc = (int)cspec.size();
         int rounds = 1, max_it = 1;
@@ -1035,8 +1067,7 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
     }
     const int nj = (direct && !plain) ? T : 1;
     std::vector<JobSpec> spec(nj, JobSpec{map, params->log2_res, params->precision});
-    std::vector<const float*> starts(nj, map->h_xy0.data());
-    Batch* B = get_batch(spec, starts, &st);
+    Batch* B = get_batch(spec, &st);
     if (!B) return st;
     int result = INIM_OK;
     const int rounds = (nj == T) ? 1 : T;
@@ -1107,7 +1138,7 @@ int inim_persistent_phase_times(int32_t enable, double* ms, int32_t n) {
 int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
     if (!jobs || n_jobs < 1) return fail(INIM_E_ARG, "no jobs");
     std::vector<JobSpec> spec(n_jobs);
-    std::vector<const float*> cap_ptr(n_jobs), start_ptr(n_jobs);
+    std::vector<const float*> start_ptr(n_jobs);
     bool poll = false;
     for (int k = 0; k < n_jobs; ++k) {
         const inim_job& j = jobs[k];
@@ -1120,7 +1151,6 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
             st = check_values(j.values, j.map->n_regions);
             if (st != INIM_OK) return st;
         }
-        cap_ptr[k] = j.map->h_xy0.data();   // capacity estimate from the map (4x margin)
         start_ptr[k] = j.init_xy ? j.init_xy : (const float*)j.map->xy0;   // the map's device copy
         spec[k] = JobSpec{j.map, j.params.log2_res, j.params.precision};
         poll |= needs_poll(j.params);
@@ -1128,7 +1158,7 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
     if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;
-    Batch* B = get_batch(spec, cap_ptr, &st);
+    Batch* B = get_batch(spec, &st);
     if (!B) return st;
     int max_it = 1;
     for (int k = 0; k < n_jobs; ++k) {
@@ -1160,12 +1190,10 @@ int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t
     if (!map || !xy || !labels || !counts) return fail(INIM_E_ARG, "NULL argument");
     if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
     if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    std::vector<float> hxy = to_host(xy, (size_t)map->n_verts * 2);
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;
     std::vector<JobSpec> spec{JobSpec{map, log2_res, INIM_FP32}};
-    std::vector<const float*> starts{hxy.data()};
-    Batch* B = get_batch(spec, starts, &st);
+    Batch* B = get_batch(spec, &st);
     if (!B) return st;
     inim_params p;
     inim_params_default(&p);
@@ -1179,7 +1207,7 @@ int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, xy, (size_t)map->n_verts * 8, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
-    CUDA_TRY(launch_raster_prologue(B->d_jobs, B->edge_blocks, B->stream));
+    CUDA_TRY(launch_raster_prologue(B->d_jobs, (int)B->spec.size(), B->edge_blocks, B->stream));
     CUDA_TRY(launch_raster_main(B->d_jobs, B->edge_blocks, B->row_blocks, B->max_n, B->stream));
     CUDA_TRY(launch_density_table(B->d_jobs, 1, B->stream));
     CUDA_TRY(cudaMemcpyAsync(labels, B->bufs[0].labels, (size_t)n * n * 2, cudaMemcpyDeviceToDevice, B->stream));
@@ -1200,8 +1228,7 @@ int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, 
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;
     std::vector<JobSpec> spec{JobSpec{map, log2_res, INIM_FP32}};
-    std::vector<const float*> starts{map->h_xy0.data()};
-    Batch* B = get_batch(spec, starts, &st);
+    Batch* B = get_batch(spec, &st);
     if (!B) return st;
     inim_params p;
     inim_params_default(&p);
@@ -1211,7 +1238,7 @@ int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, 
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, xy, (size_t)map->n_verts * 8, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
-    CUDA_TRY(launch_raster_prologue(B->d_jobs, B->edge_blocks, B->stream));
+    CUDA_TRY(launch_raster_prologue(B->d_jobs, (int)B->spec.size(), B->edge_blocks, B->stream));
     CUDA_TRY(launch_raster_main(B->d_jobs, B->edge_blocks, B->row_blocks, B->max_n, B->stream));
     CUDA_TRY(launch_density_table(B->d_jobs, 1, B->stream));
     const int m = (1 << log2_res) / pool;
@@ -1228,8 +1255,7 @@ int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, 
 static int texture_batch(int log2_res, int precision, int frac_bits, const float* density, Batch** out) {
     int st = INIM_OK;
     std::vector<JobSpec> spec{JobSpec{nullptr, log2_res, precision}};
-    std::vector<const float*> starts{nullptr};
-    Batch* B = get_batch(spec, starts, &st);
+    Batch* B = get_batch(spec, &st);
     if (!B) return st;
     inim_params p;
     inim_params_default(&p);
@@ -1295,8 +1321,7 @@ int inim_iterate(const inim_map* map, float* xy, const float* values, const inim
     std::vector<float> hxy = to_host(xy, (size_t)map->n_verts * 2);
     std::lock_guard<std::mutex> lk(g_cache_mu);
     std::vector<JobSpec> spec{JobSpec{map, params->log2_res, params->precision}};
-    std::vector<const float*> starts{hxy.data()};
-    Batch* B = get_batch(spec, starts, &st);
+    Batch* B = get_batch(spec, &st);
     if (!B) return st;
     Job& J = B->h_jobs[0];
     J.lam = 1.0f - params->shape;
@@ -1329,8 +1354,7 @@ int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;
     std::vector<JobSpec> spec{JobSpec{map, kMinLog2, INIM_FP32}};
-    std::vector<const float*> starts{hxy.data()};
-    Batch* B = get_batch(spec, starts, &st);
+    Batch* B = get_batch(spec, &st);
     if (!B) return st;
     inim_params p;
     inim_params_default(&p);
@@ -1338,7 +1362,7 @@ int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, hxy.data(), hxy.size() * 4, cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_states, B->h_states.data(), sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
-    CUDA_TRY(launch_areas_errors(B->d_jobs, 1, B->region_blocks, -1, 0, B->stream));
+    CUDA_TRY(launch_areas_errors(B->d_jobs, B->region_blocks, -1, B->stream));
     CUDA_TRY(cudaMemcpyAsync(areas, B->bufs[0].areas, (size_t)map->n_regions * 8, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaStreamSynchronize(B->stream));
     return INIM_OK;
@@ -1370,7 +1394,6 @@ int inim_get_scan_tile(int32_t log2_res, int32_t precision, int32_t large, int32
 int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
     if (!jobs || n_jobs < 1 || reps < 1) return fail(INIM_E_ARG, "bad arguments");
     std::vector<JobSpec> spec(n_jobs);
-    std::vector<const float*> cap_ptr(n_jobs);
     for (int k = 0; k < n_jobs; ++k) {
         const inim_job& j = jobs[k];
         if (!j.map || !j.values) return fail(INIM_E_ARG, "job with NULL map or values");
@@ -1378,10 +1401,9 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
         if (st != INIM_OK) return st;
         if (j.params.precision != jobs[0].params.precision) return fail(INIM_E_ARG, "all jobs need one precision");
         spec[k] = JobSpec{j.map, j.params.log2_res, j.params.precision};
-        cap_ptr[k] = j.map->h_xy0.data();
     }
     Batch B;
-    int st = build_batch(B, spec, cap_ptr, kTileHeights[0]);
+    int st = build_batch(B, spec, kTileHeights[0]);
     if (st != INIM_OK) return st;
     for (int k = 0; k < n_jobs; ++k) {
         const inim_job& j = jobs[k];
@@ -1395,7 +1417,7 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
     CUDA_TRY(cudaMemcpyAsync(B.d_jobs, B.h_jobs.data(), n_jobs * sizeof(Job), cudaMemcpyHostToDevice, B.stream));
     CUDA_TRY(cudaMemcpyAsync(B.d_states, B.h_states.data(), n_jobs * sizeof(JobState), cudaMemcpyHostToDevice, B.stream));
     // labels and densities of the start positions
-    CUDA_TRY(launch_raster_prologue(B.d_jobs, B.edge_blocks, B.stream));
+    CUDA_TRY(launch_raster_prologue(B.d_jobs, (int)B.spec.size(), B.edge_blocks, B.stream));
     CUDA_TRY(launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream));
     CUDA_TRY(launch_density_table(B.d_jobs, n_jobs, B.stream));
     cudaEvent_t e0, e1;
@@ -1477,7 +1499,7 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
                 return e;
             }
             case 5: return launch_gather(B.d_jobs, B.vert_blocks, B.precision, B.stream);
-            default: return launch_areas_errors(B.d_jobs, nj, B.region_blocks, 0, 1, B.stream);
+            default: return launch_areas_errors(B.d_jobs, B.region_blocks, 0, B.stream);
         }
     };
     int rc = INIM_OK;

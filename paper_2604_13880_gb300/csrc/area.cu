@@ -18,22 +18,20 @@ namespace inim {
 namespace {
 
 __global__ void __launch_bounds__(256) k_areas_errors(const Job* __restrict__ jobs, const int2* __restrict__ bmap,
-                                                      int update_state, int next_hist) {
+                                                      int update_state) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
-    areas_item(J, m.y, update_state, next_hist);
+    areas_item(J, m.y, update_state);
 }
 
 }  // namespace
 
-cudaError_t launch_areas_errors(const Job* d_jobs, int n_jobs, const BlockMap& region_blocks,
-                                int update_state, int next_hist, cudaStream_t s) {
-    (void)n_jobs;
-    if (region_blocks.n_blocks)
-        k_areas_errors<<<region_blocks.n_blocks, 256, 0, s>>>(d_jobs, region_blocks.d_map, update_state,
-                                                              update_state < 0 ? 0 : next_hist);
-    return cudaGetLastError();
+cudaError_t launch_areas_errors(const Job* d_jobs, const BlockMap& region_blocks, int update_state,
+                                cudaStream_t s) {
+    return launch_pdl(k_areas_errors, region_blocks.n_blocks, 256, 0, s, d_jobs, (const int2*)region_blocks.d_map,
+                      update_state);
 }
 
 }  // namespace inim

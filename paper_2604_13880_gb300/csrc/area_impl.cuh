@@ -71,39 +71,61 @@ __device__ inline void errors_and_stop(const Job& J, int update_state) {
     }
 }
 
+// Compensated FP32 accumulation of one shoelace term x_a y_b - x_b y_a: each
+// product is split exactly into p + e (e = fma(x, y, -p)) and summed with
+// two-sum into a (hi, lo) pair.
+__device__ __forceinline__ void shoelace_add(float& hi, float& lo, float2 p, float2 q) {
+    const float p1 = __fmul_rn(p.x, q.y), e1p = __fmaf_rn(p.x, q.y, -p1);
+    const float p2 = __fmul_rn(q.x, p.y), e2p = __fmaf_rn(q.x, p.y, -p2);
+    float s = __fadd_rn(hi, p1);
+    float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p1, bb)), e1p));
+    hi = s;
+    s = __fadd_rn(hi, -p2);
+    bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fsub_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-p2, bb)), e2p));
+    hi = s;
+}
+
 // update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only.
-// next_hist: the moved vertices are the next iteration's raster input, so the
-// same edge pass also builds its row histogram (and the last block its row
-// offsets), saving the rasteriser two launches.
-__device__ inline void areas_item(const Job& J, int item, int update_state, int next_hist) {
-    const int v = item * kRegionsPerBlock + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+// A block (8 warps) holds 8 >> lw regions, 1 << lw warps each; a warp's lanes
+// take every (32 << lw)-th edge of the region, four edges' loads in flight.
+__device__ inline void areas_item(const Job& J, int item, int update_state) {
+    __shared__ double wpart[kRegionsPerBlock];
+    const int lw = area_warps_log2(J.n_edges, J.n_regions);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = item * (kRegionsPerBlock >> lw) + (warp >> lw);
+    const int wr = warp & ((1 << lw) - 1);
+    double acc = 0.0;
     if (v < J.n_regions) {
-        // shoelace terms x_a y_b - x_b y_a: each product is split exactly into
-        // p + e (e = fma(x, y, -p)) and summed with two-sum into a (hi, lo)
-        // pair, all in FP32; one conversion to double per lane at the end
         float hi = 0.0f, lo = 0.0f;
         const int e1 = J.reg_edge_off[v + 1];
-        for (int e = J.reg_edge_off[v] + lane; e < e1; e += 32) {
-            if (next_hist) row_hist_edge(J, e);
-            const int2 ab = J.edges[e];
-            const float2 p = J.xy[ab.x];
-            const float2 q = J.xy[ab.y];
-            const float p1 = __fmul_rn(p.x, q.y), e1p = __fmaf_rn(p.x, q.y, -p1);
-            const float p2 = __fmul_rn(q.x, p.y), e2p = __fmaf_rn(q.x, p.y, -p2);
-            float s = __fadd_rn(hi, p1);
-            float bb = __fsub_rn(s, hi);
-            lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p1, bb)), e1p));
-            hi = s;
-            s = __fadd_rn(hi, -p2);
-            bb = __fsub_rn(s, hi);
-            lo = __fadd_rn(lo, __fsub_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-p2, bb)), e2p));
-            hi = s;
+        const int stride = 32 << lw;
+        int e = J.reg_edge_off[v] + wr * 32 + lane;
+        for (; e + 3 * stride < e1; e += 4 * stride) {
+            int2 ab[4];
+            float2 p[4], q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ab[u] = __ldg(J.edges + e + u * stride);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { p[u] = J.xy[ab[u].x]; q[u] = J.xy[ab[u].y]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) shoelace_add(hi, lo, p[u], q[u]);
         }
-        double acc = (double)hi + (double)lo;
+        for (; e < e1; e += stride) {
+            const int2 ab = __ldg(J.edges + e);
+            shoelace_add(hi, lo, J.xy[ab.x], J.xy[ab.y]);
+        }
+        acc = (double)hi + (double)lo;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) J.areas[v] = 0.5 * acc;
+    }
+    if (lane == 0) wpart[warp] = acc;
+    __syncthreads();
+    if (v < J.n_regions && wr == 0 && lane == 0) {
+        double a = 0.0;
+        for (int k = 0; k < (1 << lw); ++k) a += wpart[warp + k];      // fixed order
+        J.areas[v] = 0.5 * a;
     }
     if (update_state < 0) return;
     // the last block of this job reduces the errors
@@ -111,7 +133,8 @@ __device__ inline void areas_item(const Job& J, int item, int update_state, int 
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const int nblk = (J.n_regions + kRegionsPerBlock - 1) / kRegionsPerBlock;
+        const int rpb = kRegionsPerBlock >> area_warps_log2(J.n_edges, J.n_regions);
+        const int nblk = (J.n_regions + rpb - 1) / rpb;
         const int ticket = atomicAdd(&J.st->blocks_done, 1);
         last = (ticket == nblk - 1);
         if (last) J.st->blocks_done = 0;
@@ -120,7 +143,6 @@ __device__ inline void areas_item(const Job& J, int item, int update_state, int 
     if (!last) return;
     __threadfence();
     errors_and_stop(J, update_state);
-    if (next_hist) row_offsets_block(J);
 }
 
 }  // namespace inim

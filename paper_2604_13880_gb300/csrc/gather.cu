@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(256) k_gather_move(const Job* __restrict__ job
                                                      const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
     gather_vertex<Acc>(J, m.y * blockDim.x + threadIdx.x);
 }
@@ -103,10 +104,10 @@ cudaError_t launch_apply_field(const Job* d_jobs, const BlockMap& vert_blocks, c
 
 cudaError_t launch_gather(const Job* d_jobs, const BlockMap& vert_blocks, int precision, cudaStream_t s) {
     if (!vert_blocks.n_blocks) return cudaSuccess;
-    if (precision == INIM_FIX64) k_gather_move<AccFix><<<vert_blocks.n_blocks, 256, 0, s>>>(d_jobs, vert_blocks.d_map);
-    else if (precision == INIM_KAHAN) k_gather_move<AccKahan><<<vert_blocks.n_blocks, 256, 0, s>>>(d_jobs, vert_blocks.d_map);
-    else k_gather_move<AccF32><<<vert_blocks.n_blocks, 256, 0, s>>>(d_jobs, vert_blocks.d_map);
-    return cudaGetLastError();
+    const int2* bm = vert_blocks.d_map;
+    if (precision == INIM_FIX64) return launch_pdl(k_gather_move<AccFix>, vert_blocks.n_blocks, 256, 0, s, d_jobs, bm);
+    if (precision == INIM_KAHAN) return launch_pdl(k_gather_move<AccKahan>, vert_blocks.n_blocks, 256, 0, s, d_jobs, bm);
+    return launch_pdl(k_gather_move<AccF32>, vert_blocks.n_blocks, 256, 0, s, d_jobs, bm);
 }
 
 cudaError_t launch_displacement(const Job* d_job, const float* xy, int n, float* delta, int precision,

@@ -13,6 +13,7 @@ namespace inim {
 constexpr int kSubBits = 8;          // sub-pixel bits of the fixed-point raster
 constexpr int kMaxLog2 = 12;         // N <= 4096
 constexpr int kMinLog2 = 8;          // N >= 256
+constexpr int kKeyStride = 2048;     // crossing keys one texture row can hold (fixed-stride buckets)
 
 // Per-solve state living in device memory: the stop rule (Sec. 4.1 defaults)
 // and the statistics of the last iteration.
@@ -37,7 +38,6 @@ struct JobState {
     int   stop_on_rule;  // 0: run exactly max_iters (no early stop)
     int   blocks_done;   // area blocks finished in this iteration (last one reduces)
     int   n_big;         // rows of this iteration with more crossings than a warp holds
-    int   hist_done;     // edge blocks of the prologue finished (last one scans)
 };
 
 // Everything a kernel needs to work on one job.  Lives in device memory; one
@@ -63,11 +63,9 @@ struct Job {
     int   precision;           // INIM_FP32 / INIM_FIX64 / INIM_KAHAN
     // raster workspace
     uint16_t* labels;          // [n*n]
-    int*      row_cnt;         // [n]   crossings per row (zero between uses)
-    int*      row_off;         // [n+1] exclusive prefix of row_cnt
+    int*      row_cnt;         // [n] crossing keys in each row's bucket (reset by the row rasteriser)
     int*      big_rows;        // [n] rows left to the block-per-row path
-    uint32_t* keys;            // [key_cap] (region << 16 | column)
-    int       key_cap;
+    uint32_t* keys;            // [n][kKeyStride] (region << 16 | column), row j's bucket at j * kKeyStride
     int*      counts;          // [n_regions+1] pixel areas o(v); last = background
     float*    dens;            // [n_regions+1] density relative to d0
     // integral images (element type by precision)
@@ -85,6 +83,45 @@ struct Job {
     double*   areas;           // [n_regions] signed shoelace areas
     JobState* st;
 };
+
+// Warps per region (log2) of a job: about 128 edges per warp, 1..8 warps.
+// A property of the map alone, so a job's areas do not depend on the batch.
+__host__ __device__ inline int area_warps_log2(int n_edges, int n_regions) {
+    const int per = n_regions > 0 ? n_edges / n_regions : 0;
+    int lw = 0;
+    while (lw < 3 && (128 << lw) < per) ++lw;
+    return lw;
+}
+
+// ---------------------------------------------------------------------------
+// programmatic dependent launch: the kernels of one iteration are launched so
+// that the next kernel's grid is set up while the current one runs; every such
+// kernel first waits for its predecessor to complete (and its writes to be
+// visible), then lets its own successor launch.  Without the launch attribute
+// both instructions return at once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool pdl_enabled();   // INIM_PDL=0 in the environment turns the attribute off
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t s, Args... args) {
+    if (grid == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // integer helpers (exact rasterisation rule, Sec. 4.1 step 2 reading)
@@ -176,12 +213,13 @@ __device__ __forceinline__ float2 t_uniform(int i, int j, int n) {
 struct BlockMap {            // block -> (job, first item) tables for one kernel
     int2* d_map = nullptr;   // device [n_blocks]
     int   n_blocks = 0;
+    int   q_per_block = 256; // carry maps: q values per block (32 = the grouped carry kernel)
 };
 
 struct ScanTile { int H; int cpt; int nt; };   // band height, columns/thread, threads
 
 cudaError_t raster_setup(int max_n);   // once per process
-cudaError_t launch_raster_prologue(const Job* d_jobs, const BlockMap& edge_blocks, cudaStream_t s);
+cudaError_t launch_raster_prologue(const Job* d_jobs, int n_jobs, const BlockMap& edge_blocks, cudaStream_t s);
 cudaError_t launch_raster_main(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& row_blocks,
                                int max_n, cudaStream_t s);
 cudaError_t launch_density_table(const Job* d_jobs, int n_jobs, cudaStream_t s);
@@ -193,10 +231,9 @@ cudaError_t launch_scan_kahan(const Job* d_jobs, const BlockMap& band, const Blo
                               ScanTile tile, const float* dtex, cudaStream_t s, int phase = 0);
 cudaError_t launch_gather(const Job* d_jobs, const BlockMap& vert_blocks, int precision,
                           cudaStream_t s);
-// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only;
-// next_hist: also build the next iteration's row histogram and offsets
-cudaError_t launch_areas_errors(const Job* d_jobs, int n_jobs, const BlockMap& region_blocks,
-                                int update_state, int next_hist, cudaStream_t s);
+// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only
+cudaError_t launch_areas_errors(const Job* d_jobs, const BlockMap& region_blocks, int update_state,
+                                cudaStream_t s);
 cudaError_t launch_displacement(const Job* d_job, const float* xy, int n, float* delta,
                                 int precision, cudaStream_t s);
 cudaError_t launch_finalize_B(const Job* d_job, int precision, cudaStream_t s);

@@ -4,8 +4,8 @@
 // per-iteration cost is a few barriers instead of eight kernel launches.
 //
 // Phases per iteration (the same device bodies as the per-step kernels):
-//   crossings | rows | big rows + density table | scan 1 | carries | scan 3 |
-//   gather + move | areas, errors, stop rule, next row histogram + offsets
+//   crossing keys | rows | big rows + density table | scan 1 | carries |
+//   scan 3 | gather + move | areas, errors, stop rule
 // The barrier is a generation counter with a bounded spin: a wait that
 // exceeds its cap records INIM_E_TIMEOUT and the kernel returns (a cooperative
 // launch makes every block resident, so the cap is only a safety net).
@@ -116,11 +116,16 @@ __device__ void scan_phase(const PersistPlan& P, unsigned char* smem) {
 __device__ bool one_iteration(const PersistPlan& P, unsigned char* smem) {
     const int tid = threadIdx.x;
     unsigned long long t_prev = (P.phase_ns && blockIdx.x == 0 && tid == 0) ? global_ns() : 0ull;
-    // crossings
+    // crossing keys into the row buckets; pixel counts cleared
     for (int it = blockIdx.x; it < P.n_edge_items; it += gridDim.x) {
         const int2 m = P.edge_items[it];
         const Job& J = P.jobs[m.x];
-        if (active(J)) crossings_edge(J, m.y * kPersistThreads + tid);
+        const int e = m.y * kPersistThreads + tid;
+        if (active(J) && e < J.n_edges) emit_crossings_edge(J, e);
+    }
+    for (int j = blockIdx.x; j < P.n_jobs; j += gridDim.x) {
+        const Job& J = P.jobs[j];
+        if (active(J)) reset_raster_block(J);
     }
     if (!grid_barrier(P)) return false;
     phase_mark(P, 0, t_prev);
@@ -168,7 +173,7 @@ __device__ bool one_iteration(const PersistPlan& P, unsigned char* smem) {
     for (int it = blockIdx.x; it < P.n_region_items; it += gridDim.x) {
         const int2 m = P.region_items[it];
         const Job& J = P.jobs[m.x];
-        if (active(J)) areas_item(J, m.y, 1, 1);
+        if (active(J)) areas_item(J, m.y, 1);
         __syncthreads();
     }
     const bool ok = grid_barrier(P);
@@ -180,19 +185,6 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persistent(PersistPlan P
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     for (int round = 0; round < P.rounds; ++round) {
-        // row histogram and offsets of the start positions of this round
-        for (int it = blockIdx.x; it < P.n_edge_items; it += gridDim.x) {
-            const int2 m = P.edge_items[it];
-            const Job& J = P.jobs[m.x];
-            const int e = m.y * kPersistThreads + tid;
-            if (active(J) && e < J.n_edges) row_hist_edge(J, e);
-        }
-        if (!grid_barrier(P)) return;
-        for (int j = blockIdx.x; j < P.n_jobs; j += gridDim.x) {
-            const Job& J = P.jobs[j];
-            if (active(J)) row_offsets_block(J);
-        }
-        if (!grid_barrier(P)) return;
         for (int k = 0; k < P.iters; ++k) {
             bool any = false;
             for (int j = 0; j < P.n_jobs; ++j) any |= active(P.jobs[j]);

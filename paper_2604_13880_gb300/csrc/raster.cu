@@ -11,11 +11,9 @@
 // regions it takes the smallest id and the overlap flag is raised.
 //
 // Kernels (edge-parallel, then row-parallel; no per-pixel atomics):
-//   row histogram + offsets   per edge, then one block per job: crossings per
-//                             row and their exclusive prefix (k_raster_prologue
-//                             for the start positions; afterwards fused into
-//                             the area kernel of the previous iteration)
-//   k_crossings    per edge: scatter (region << 16 | c) keys into row buckets
+//   k_crossings    per edge: (region << 16 | c) appended to the fixed-stride
+//                  bucket of every row the edge crosses (no histogram or
+//                  prefix pass: each bucket holds up to 2048 keys)
 //   k_raster_rows  warp per row: sort the row's keys in registers, pair them
 //                  into spans, paint them into a shared-memory copy of the row
 //                  in region order, write the row once; rows with more than
@@ -27,36 +25,24 @@ namespace inim {
 
 namespace {
 
-// Histogram + offsets of the current vertex positions (the first iteration
-// of a run; later iterations get them from the area kernel).  One ticket per
-// job: the last edge block of a job computes its offsets.
-__global__ void __launch_bounds__(256) k_raster_prologue(const Job* __restrict__ jobs,
-                                                         const int2* __restrict__ bmap) {
-    const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
+// Empty buckets (a block per job) at the start of a run.
+__global__ void __launch_bounds__(256) k_raster_reset(const Job* __restrict__ jobs) {
+    const Job& J = jobs[blockIdx.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
-    const int e = m.y * blockDim.x + threadIdx.x;
-    if (e < J.n_edges) row_hist_edge(J, e);
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nblk = (J.n_edges + 255) / 256;
-        const int ticket = atomicAdd(&J.st->hist_done, 1);
-        last = (ticket == nblk - 1);
-        if (last) J.st->hist_done = 0;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    row_offsets_block(J);
+    reset_buckets_block(J);
 }
 
+// The crossing keys of the current vertex positions, one thread per edge; the
+// first edge block of a job also clears its pixel counts and big-row list.
 __global__ void __launch_bounds__(256) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
-    crossings_edge(J, m.y * blockDim.x + threadIdx.x);
+    const int e = m.y * blockDim.x + threadIdx.x;
+    if (e < J.n_edges) emit_crossings_edge(J, e);
+    if (m.y == 0) reset_raster_block(J);
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_raster_rows(const Job* __restrict__ jobs,
@@ -64,6 +50,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_raster_rows(const Job* 
     extern __shared__ __align__(16) uint16_t rows_smem[];
     const int2 m = bmap[blockIdx.x];                 // (job, first row)
     const Job& J = jobs[m.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
     raster_rows_item(J, m.y, rows_smem);
 }
@@ -73,6 +60,7 @@ __global__ void __launch_bounds__(kRowThreads) k_density_table(const Job* __rest
     __shared__ double ss[32];
     __shared__ long long so[32];
     const Job& J = jobs[blockIdx.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
     density_table_body(J, rsh, ss, so);
 }
@@ -90,24 +78,24 @@ cudaError_t raster_setup(int max_n) {
     return e;
 }
 
-cudaError_t launch_raster_prologue(const Job* d_jobs, const BlockMap& edge_blocks, cudaStream_t s) {
-    if (edge_blocks.n_blocks) k_raster_prologue<<<edge_blocks.n_blocks, 256, 0, s>>>(d_jobs, edge_blocks.d_map);
-    return cudaGetLastError();
+cudaError_t launch_raster_prologue(const Job* d_jobs, int n_jobs, const BlockMap& edge_blocks, cudaStream_t s) {
+    (void)edge_blocks;
+    return launch_pdl(k_raster_reset, n_jobs, 256, 0, s, d_jobs);
 }
 
-// crossings + rows; the histogram and offsets must be in place (prologue or
-// the previous iteration's area kernel); big rows finish in the density kernel
+// crossing keys into the row buckets, then the rows; big rows finish in the
+// density kernel
 cudaError_t launch_raster_main(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& row_blocks,
                                int max_n, cudaStream_t s) {
-    if (edge_blocks.n_blocks) k_crossings<<<edge_blocks.n_blocks, 256, 0, s>>>(d_jobs, edge_blocks.d_map);
-    k_raster_rows<<<row_blocks.n_blocks, kWarpsPerBlock * 32, kWarpsPerBlock * max_n * 2, s>>>(d_jobs,
-                                                                                            row_blocks.d_map);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_crossings, edge_blocks.n_blocks, 256, 0, s, d_jobs, (const int2*)edge_blocks.d_map);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_raster_rows, row_blocks.n_blocks, kWarpsPerBlock * 32, (size_t)kWarpsPerBlock * max_n * 2, s,
+                       d_jobs, (const int2*)row_blocks.d_map);
+    return e;
 }
 
 cudaError_t launch_density_table(const Job* d_jobs, int n_jobs, cudaStream_t s) {
-    k_density_table<<<n_jobs, 256, 0, s>>>(d_jobs);
-    return cudaGetLastError();
+    return launch_pdl(k_density_table, n_jobs, 256, 0, s, d_jobs);
 }
 
 }  // namespace inim

@@ -1,6 +1,6 @@
-// Device helpers shared by the rasteriser and the area kernel (which builds
-// the next iteration's row histogram): the exact fixed-point edge setup, the
-// per-edge row histogram and the block-level row offsets.
+// Device helpers of the rasteriser (per-step kernels and persistent form):
+// the exact fixed-point edge setup, the key emission into fixed-stride row
+// buckets and the per-job resets.
 #pragma once
 
 #include "inim_internal.cuh"
@@ -12,10 +12,7 @@ struct EdgeFix {
     int jlo, jhi;
 };
 
-__device__ __forceinline__ bool edge_rows(const Job& J, int e, EdgeFix& f) {
-    int2 ab = J.edges[e];
-    float2 p = J.xy[ab.x];
-    float2 q = J.xy[ab.y];
+__device__ __forceinline__ bool edge_rows_pts(const Job& J, float2 p, float2 q, EdgeFix& f) {
     const float scale = (float)(1 << (J.log2n + kSubBits));
     long long X0 = snap_coord(p.x, scale), Y0 = snap_coord(p.y, scale);
     long long X1 = snap_coord(q.x, scale), Y1 = snap_coord(q.y, scale);
@@ -35,58 +32,61 @@ __device__ __forceinline__ bool edge_rows(const Job& J, int e, EdgeFix& f) {
 }
 
 
-// crossings per row of one edge (the histogram the keys are scattered by)
-__device__ __forceinline__ void row_hist_edge(const Job& J, int e) {
-    EdgeFix f;
-    if (!edge_rows(J, e, f)) return;
-    for (int j = f.jlo; j <= f.jhi; ++j) atomicAdd(&J.row_cnt[j], 1);
+__device__ __forceinline__ bool edge_rows(const Job& J, int e, EdgeFix& f) {
+    const int2 ab = J.edges[e];
+    return edge_rows_pts(J, J.xy[ab.x], J.xy[ab.y], f);
 }
 
-// Exclusive prefix of the per-row crossing counts of one job, done by one
-// block (blockDim >= 256, N <= 4096); clears the counters (reused as fill
-// cursors by k_crossings), the pixel counts and the big-row list, and checks
-// the key capacity.
-__device__ __forceinline__ void row_offsets_block(const Job& J) {
-    __shared__ int wsum[32];
-    const int n = J.n, nt = blockDim.x;
-    const int per = (n + nt - 1) / nt;
-    const int base = threadIdx.x * per;
-    int s = 0;
-    for (int k = 0; k < per; ++k) {
-        const int idx = base + k;
-        if (idx < n) s += __ldcg(J.row_cnt + idx);
+// min(max(ceil(num / den), 0), n) exactly, for den > 0, without a 64-bit
+// division: a float estimate of the quotient (only needed in [0, n], n <=
+// 4096, where it is off by less than one) corrected by exact int64 products.
+__device__ __forceinline__ int clamped_ceil_div(long long num, long long den, int n) {
+    if (num <= 0) return 0;                              // ceil <= 0
+    if (num > (long long)n * den) return n;              // ceil > n
+    long long q = (long long)floorf(__fdiv_rn((float)num, (float)den));
+    long long r = num - q * den;
+    while (r < 0) { --q; r += den; }
+    while (r >= den) { ++q; r -= den; }
+    const long long c = q + (r > 0 ? 1 : 0);
+    return (int)(c > n ? n : c);
+}
+
+// The crossings of one edge of region `reg` with the texture rows it spans:
+// (reg << 16 | first counted column) keys appended to the rows' fixed-stride
+// buckets.  A bucket that would overflow raises the capacity error (its row
+// is then written as background).
+__device__ __forceinline__ void emit_crossings_pts(const Job& J, unsigned reg, float2 p, float2 q) {
+    EdgeFix f;
+    if (!edge_rows_pts(J, p, q, f)) return;
+    const long long dY = f.Y1 - f.Y0;
+    const long long dX = f.X1 - f.X0;
+    const long long den = 256 * dY;
+    for (int j = f.jlo; j <= f.jhi; ++j) {
+        const long long Yc = 256LL * j + 128;
+        const int c = clamped_ceil_div(dX * (Yc - f.Y0) + (f.X0 - 128) * dY, den, J.n);
+        const int slot = atomicAdd(&J.row_cnt[j], 1);
+        if (slot < kKeyStride) J.keys[(size_t)j * kKeyStride + slot] = (reg << 16) | (unsigned)c;
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[w] = incl;
+}
+__device__ __forceinline__ void emit_crossings_edge(const Job& J, int e) {
+    const int2 ab = J.edges[e];
+    emit_crossings_pts(J, (unsigned)J.edge_region[e], J.xy[ab.x], J.xy[ab.y]);
+}
+
+// Per job, while the keys of an iteration are being emitted (one block):
+// clear the pixel counts and the big-row list the row rasteriser fills.
+__device__ __forceinline__ void reset_raster_block(const Job& J) {
+    if (threadIdx.x == 0) J.st->n_big = 0;
+    for (int v = threadIdx.x; v <= J.n_regions; v += blockDim.x) J.counts[v] = 0;
     __syncthreads();
-    int woff = 0, tot = 0;
-    for (int k = 0; k < (nt >> 5); ++k) {
-        if (k < w) woff += wsum[k];
-        tot += wsum[k];
-    }
-    int run = woff + incl - s;
-    for (int k = 0; k < per; ++k) {
-        const int idx = base + k;
-        if (idx < n) {
-            const int v = __ldcg(J.row_cnt + idx);
-            J.row_off[idx] = run;
-            run += v;
-            J.row_cnt[idx] = 0;
-        }
-    }
-    if (threadIdx.x == 0) {
-        J.row_off[n] = tot;
-        J.st->n_big = 0;
-        if (tot > J.key_cap) atomicExch(&J.st->error, INIM_E_CAPACITY);
-    }
-    for (int v = threadIdx.x; v <= J.n_regions; v += nt) J.counts[v] = 0;
-    __syncthreads();
+}
+
+// Per job, at the start of a run (one block): empty every row bucket.  The
+// row rasteriser empties each bucket it reads, so this only guards against
+// an earlier run that stopped on an error between emission and rows.
+__device__ __forceinline__ void reset_buckets_block(const Job& J) {
+    for (int j = threadIdx.x; j < J.n; j += blockDim.x) J.row_cnt[j] = 0;
+    reset_raster_block(J);
 }
 
 }  // namespace inim

@@ -9,41 +9,7 @@ namespace inim {
 
 
 constexpr int kRowThreads = 256;
-constexpr int kRowKeyCap = 2048;   // crossings one row can hold in shared memory
-
-// min(max(ceil(num / den), 0), n) exactly, for den > 0, without a 64-bit
-// division: a float estimate of the quotient (only needed in [0, n], n <=
-// 4096, where it is off by less than one) corrected by exact int64 products.
-__device__ __forceinline__ int clamped_ceil_div(long long num, long long den, int n) {
-    if (num <= 0) return 0;                              // ceil <= 0
-    if (num > (long long)n * den) return n;              // ceil > n
-    long long q = (long long)floorf(__fdiv_rn((float)num, (float)den));
-    long long r = num - q * den;
-    while (r < 0) { --q; r += den; }
-    while (r >= den) { ++q; r -= den; }
-    const long long c = q + (r > 0 ? 1 : 0);
-    return (int)(c > n ? n : c);
-}
-
-
-// crossings of one edge: (region << 16 | first counted column) keys into the
-// buckets of the rows it crosses
-__device__ __forceinline__ void crossings_edge(const Job& J, int e) {
-    if (e >= J.n_edges) return;
-    EdgeFix f;
-    if (!edge_rows(J, e, f)) return;
-    const unsigned reg = (unsigned)J.edge_region[e] << 16;
-    const long long dY = f.Y1 - f.Y0;
-    const long long dX = f.X1 - f.X0;
-    const long long den = 256 * dY;
-    for (int j = f.jlo; j <= f.jhi; ++j) {
-        const long long Yc = 256LL * j + 128;
-        const int c = clamped_ceil_div(dX * (Yc - f.Y0) + (f.X0 - 128) * dY, den, J.n);
-        const int slot = atomicAdd(&J.row_cnt[j], 1);
-        const int idx = J.row_off[j] + slot;
-        if (idx < J.key_cap) J.keys[idx] = reg | (unsigned)c;
-    }
-}
+constexpr int kRowKeyCap = kKeyStride;   // crossings one row can hold in shared memory
 
 template <int CPT>
 __device__ __forceinline__ void store_labels(uint16_t* dst, const uint16_t (&lab)[CPT]) {
@@ -84,11 +50,11 @@ __device__ inline void raster_row(const Job& J, int j, RowShared& sh) {
     const int n = J.n;
     const int R = J.n_regions;
     const int tid = threadIdx.x;
-    const int k0 = J.row_off[j];
-    const int k1 = J.row_off[j + 1];
-    const int cnt = k1 - k0;
-    const bool bad = (k1 > J.key_cap) || (cnt > kRowKeyCap);
-    if (bad) {   // capacity error already (or now) flagged; write background
+    const uint32_t* bucket = J.keys + (size_t)j * kKeyStride;
+    const int cnt = __ldcg(J.row_cnt + j);
+    __syncthreads();                      // every thread has read the count before it is reset
+    const bool bad = cnt > kRowKeyCap;
+    if (bad) {   // bucket overflow: flag the capacity error, write background
         if (tid == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
         uint16_t lab[CPT];
 #pragma unroll
@@ -96,7 +62,7 @@ __device__ inline void raster_row(const Job& J, int j, RowShared& sh) {
         store_labels<CPT>(J.labels + (size_t)j * n + tid * CPT, lab);
         return;
     }
-    for (int k = tid; k < cnt; k += blockDim.x) sh.keys[k] = J.keys[k0 + k];
+    for (int k = tid; k < cnt; k += blockDim.x) sh.keys[k] = bucket[k];
     for (int k = tid; k <= n; k += blockDim.x) sh.diff[k] = 0u;
     __syncthreads();
     // rank sort (ties broken by position): sorted by (region, column)
@@ -252,12 +218,12 @@ template <int KPL>
 __device__ inline void raster_row_warp(const Job& J, int j, int cnt, uint16_t* row, int lane) {
     const int n = J.n;
     const unsigned R = (unsigned)J.n_regions;
-    const int k0 = J.row_off[j];
+    const uint32_t* bucket = J.keys + (size_t)j * kKeyStride;
     unsigned key[KPL];
 #pragma unroll
     for (int e = 0; e < KPL; ++e) {
         const int idx = lane * KPL + e;
-        key[e] = idx < cnt ? J.keys[k0 + idx] : 0xffffffffu;
+        key[e] = idx < cnt ? bucket[idx] : 0xffffffffu;
     }
     // background fill of the row copy
     unsigned* row32 = reinterpret_cast<unsigned*>(row);
@@ -325,10 +291,9 @@ __device__ __forceinline__ void raster_rows_item(const Job& J, int first_row, ui
     const int j = first_row + warp;
     if (warp >= kWarpsPerBlock || j >= J.n) return;
     uint16_t* row = rows_smem + (size_t)warp * J.n;
-    const int k0 = J.row_off[j];
-    const int k1 = J.row_off[j + 1];
-    const int cnt = k1 - k0;
-    if (k1 > J.key_cap) {                            // capacity error already flagged
+    const int cnt = J.row_cnt[j];
+    __syncwarp();                                    // every lane has the count before lane 0 resets it
+    if (cnt > kKeyStride) {                          // bucket overflow
         if (lane == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
         return;
     }

@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
     __shared__ ScanShared<Acc, NT> sh;
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
     scan_band_body<Acc, CPT, NT, PHASE>(J, m.y, dtex, sh);
 }
@@ -456,8 +457,89 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
                                                     const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
+    pdl_wait_and_release();
     if (!J.st->active) return;
     scan_carry_body<Acc>(J, m.y * blockDim.x + threadIdx.x);
+}
+
+// Two-level form of the same carries, for many short bands: a block covers
+// 32 consecutive q (the lanes, so loads and stores stay coalesced) times 8
+// groups of consecutive bands (the warps).  Each thread sums the terms of its
+// group's bands, the 8 group totals are scanned in shared memory, and each
+// thread then writes the exclusive prefixes of its own bands.  The same sums
+// as the serial walk, associated by group, with 1/8 of its dependent chain.
+constexpr int kCarryGroups = 8;
+
+// q values per carry block: the grouped form pays off once there are many
+// bands (its dependent chain is nb / 8 loads instead of nb)
+__host__ __device__ inline int carry_q_per_block(int nb) { return nb >= 32 ? 32 : 256; }
+
+template <class Acc>
+__device__ __forceinline__ typename Acc::T carry_term(const Job& J, const typename Acc::T* a, int kind, int q,
+                                                      int b) {
+    const int n = J.n, H = J.H;
+    if (kind == 0) return a[(size_t)b * n + q];
+    if (kind == 1) {
+        const int xp = q - (b + 1) * H;
+        if (xp >= n) return reinterpret_cast<const typename Acc::T*>(J.agg)[(size_t)b * n + (n - 1)];
+        return xp >= 0 ? a[(size_t)b * n + xp] : Acc::zero();
+    }
+    const int xp = q + (b + 1) * H;
+    return (xp >= 0 && xp < n) ? a[(size_t)b * n + xp] : Acc::zero();
+}
+
+template <class Acc>
+__global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const Job* __restrict__ jobs,
+                                                                           const int2* __restrict__ bmap) {
+    using T = typename Acc::T;
+    __shared__ T tot[kCarryGroups][32];
+    const int2 m = bmap[blockIdx.x];
+    const Job& J = jobs[m.x];
+    pdl_wait_and_release();
+    if (!J.st->active) return;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int n = J.n, H = J.H, nb = J.nb;
+    const int span = n + (nb - 1) * H;
+    int q = m.y * 32 + lane;
+    int kind = -1;
+    if (q < n) kind = 0;
+    else if ((q -= n) < span) kind = 1;
+    else if ((q -= span) < span) { kind = 2; q -= (nb - 1) * H; }
+    const T* a = reinterpret_cast<const T*>(J.agg) + (size_t)(kind < 0 ? 0 : kind) * nb * n;
+    T* c = reinterpret_cast<T*>(J.carry) + (size_t)(kind < 0 ? 0 : kind) * nb * n;
+    const int cb = (nb + kCarryGroups - 1) / kCarryGroups;
+    const int b_lo = min(nb, g * cb), b_hi = min(nb, b_lo + cb);
+    T v[kCarryU];
+    T s = Acc::zero();
+    if (kind >= 0) {
+        for (int b0 = b_lo; b0 < b_hi; b0 += kCarryU) {
+#pragma unroll
+            for (int u = 0; u < kCarryU; ++u) v[u] = (b0 + u < b_hi) ? carry_term<Acc>(J, a, kind, q, b0 + u) : Acc::zero();
+#pragma unroll
+            for (int u = 0; u < kCarryU; ++u) if (b0 + u < b_hi) s = Acc::add(s, v[u]);
+        }
+    }
+    tot[g][lane] = s;
+    __syncthreads();
+    if (kind < 0) return;
+    T acc = Acc::zero();
+    for (int k = 0; k < g; ++k) acc = Acc::add(acc, tot[k][lane]);
+    const bool held = (b_hi - b_lo) <= kCarryU;      // the terms are still in v
+    for (int b0 = b_lo; b0 < b_hi; b0 += kCarryU) {
+        if (!held) {
+#pragma unroll
+            for (int u = 0; u < kCarryU; ++u) v[u] = (b0 + u < b_hi) ? carry_term<Acc>(J, a, kind, q, b0 + u) : Acc::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < kCarryU; ++u) {
+            const int b = b0 + u;
+            if (b < b_hi) {
+                const int x = kind == 0 ? q : (kind == 1 ? q - b * H : q + b * H);
+                if (x >= 0 && x < n) c[(size_t)b * n + x] = acc;
+                acc = Acc::add(acc, v[u]);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -466,10 +548,17 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
 template <class Acc, int CPT, int NT>
 cudaError_t launch_scan_tile(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
                              const float* dtex, int phase, cudaStream_t s) {
-    if (phase == 0 || phase == 1) k_scan_band<Acc, CPT, NT, 1><<<band.n_blocks, NT, 0, s>>>(d_jobs, band.d_map, dtex);
-    if (phase == 0 || phase == 2) k_scan_carry<Acc><<<carry.n_blocks, 256, 0, s>>>(d_jobs, carry.d_map);
-    if (phase == 0 || phase == 3) k_scan_band<Acc, CPT, NT, 3><<<band.n_blocks, NT, 0, s>>>(d_jobs, band.d_map, dtex);
-    return cudaGetLastError();
+    const int2* bm = band.d_map;
+    const int2* cm = carry.d_map;
+    cudaError_t e = cudaSuccess;
+    if (phase == 0 || phase == 1) e = launch_pdl(k_scan_band<Acc, CPT, NT, 1>, band.n_blocks, NT, 0, s, d_jobs, bm, dtex);
+    if (e == cudaSuccess && (phase == 0 || phase == 2)) {
+        if (carry.q_per_block == 32) e = launch_pdl(k_scan_carry_grouped<Acc>, carry.n_blocks, 32 * kCarryGroups, 0, s, d_jobs, cm);
+        else e = launch_pdl(k_scan_carry<Acc>, carry.n_blocks, 256, 0, s, d_jobs, cm);
+    }
+    if (e == cudaSuccess && (phase == 0 || phase == 3))
+        e = launch_pdl(k_scan_band<Acc, CPT, NT, 3>, band.n_blocks, NT, 0, s, d_jobs, bm, dtex);
+    return e;
 }
 
 template <class Acc>

@@ -181,3 +181,22 @@ def test_warm_start_argument_errors():
     P = _P()
     with pytest.raises(RuntimeError):
         P.inim_warmstart_load(np.zeros(10, np.float32))
+
+
+@pytest.mark.slow
+def test_trained_warm_start_beats_cold_start():
+    # a network trained on fields the method itself generates (2048 maps of
+    # 50-300 regions at 512^2) must start held-out maps closer to equal
+    # density than the plain start and reach eps = 0.2 in fewer iterations
+    from paper_2604_13880_gb300 import warmstart as W
+    train_maps = W.generate_maps(range(50000, 52048), workers=8)
+    test_maps = W.generate_maps(range(60000, 60064), workers=8)
+    X, Y, _ = W.build_dataset(train_maps, eps_target=0.05, max_iters=512)
+    net, hist = W.train(X, Y, epochs=15)
+    assert hist["loss"][-1] < 0.5 * hist["loss"][0], hist["loss"]
+    curve = W.eps_curve(net, test_maps, [1])
+    assert curve["warm_mean"][0] < 0.8 * curve["cold_mean"][0], curve
+    res = W.evaluate(net, test_maps, eps_target=0.2)
+    assert res["warm"]["reached"] >= res["cold"]["reached"] - 1, res
+    assert res["warm"]["iters_mean"] < 0.8 * res["cold"]["iters_mean"], res
+    net.close()
