@@ -348,7 +348,8 @@ def main():
         E = int(P.inim_map_info(m)["n_edges"])
         K = crossings_count(mesh, N)
         algo = {   # algorithmic bytes per launch over the whole batch (design notes)
-            "raster": n_jobs * (8 * E + 8 * V + 8 * K + 2 * Ppx),
+            "crossings": n_jobs * (8 * E + 8 * V + 4 * K),
+            "raster_rows": n_jobs * (4 * K + 2 * Ppx),
             "density_table": n_jobs * (12 * R),
             "scan_phase1": n_jobs * (2 * Ppx + 3 * nb * N * 4),
             "scan_carry": n_jobs * (2 * 3 * nb * N * 4),

@@ -357,10 +357,12 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps);
  * batch used most recently by inim_run / inim_run_batch / inim_iterate: each
  * stage is launched `reps` times back to back between two CUDA events on the
  * library's stream (ms[i] = elapsed / reps).  Stages, in iteration order:
- * raster, density_table, scan_phase1, scan_carry, scan_phase3, gather_move,
- * areas_errors (names from inim_stage_name).  The batch's vertices move while
- * it runs; the next run resets them.  ms must hold >= 7 floats; *n_stages
- * receives 7.  INIM_E_STATE if no map batch ran yet.
+ * crossings, raster_rows, density_table, scan_phase1, scan_carry,
+ * scan_phase3, gather_move, areas_errors (names from inim_stage_name); the
+ * two raster kernels run as pairs, each timed between its own events.  The
+ * batch's vertices move while it runs; the next run resets them.  ms must
+ * hold >= 8 floats; *n_stages receives 8.  INIM_E_STATE if no map batch ran
+ * yet.
  */
 int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_stages);
 const char* inim_stage_name(int32_t i);

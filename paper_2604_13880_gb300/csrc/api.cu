@@ -1460,9 +1460,9 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
     return INIM_OK;
 }
 
-static const char* kStageNames[] = {"raster", "density_table", "scan_phase1", "scan_carry", "scan_phase3",
-                                     "gather_move", "areas_errors"};
-constexpr int kNumStages = 7;
+static const char* kStageNames[] = {"crossings", "raster_rows", "density_table", "scan_phase1", "scan_carry",
+                                     "scan_phase3", "gather_move", "areas_errors"};
+constexpr int kNumStages = 8;
 
 const char* inim_stage_name(int32_t i) {
     return (i >= 0 && i < kNumStages) ? kStageNames[i] : "";
@@ -1486,24 +1486,48 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
     CUDA_TRY(cudaEventCreate(&e1));
     auto stage = [&](int i) -> cudaError_t {
         switch (i) {
-            case 0: return launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream);
-            case 1: return launch_density_table(B.d_jobs, nj, B.stream);
-            case 2: case 3: case 4: {
+            case 2: return launch_density_table(B.d_jobs, nj, B.stream);
+            case 3: case 4: case 5: {
                 cudaError_t e = cudaSuccess;
                 for (auto& g : B.groups) {
-                    if (B.precision == INIM_FIX64) e = launch_scan_fix64(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 1);
-                    else if (B.precision == INIM_KAHAN) e = launch_scan_kahan(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 1);
-                    else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 1);
+                    if (B.precision == INIM_FIX64) e = launch_scan_fix64(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 2);
+                    else if (B.precision == INIM_KAHAN) e = launch_scan_kahan(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 2);
+                    else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 2);
                     if (e != cudaSuccess) break;
                 }
                 return e;
             }
-            case 5: return launch_gather(B.d_jobs, B.vert_blocks, B.precision, B.stream);
+            case 6: return launch_gather(B.d_jobs, B.vert_blocks, B.precision, B.stream);
             default: return launch_areas_errors(B.d_jobs, B.region_blocks, 0, B.stream);
         }
     };
     int rc = INIM_OK;
-    for (int i = 0; i < kNumStages && rc == INIM_OK; ++i) {
+    // the rasteriser's two kernels only run as a pair (the rows empty the
+    // buckets the crossings fill): events around each, summed over the pairs
+    {
+        cudaEvent_t ev[3];
+        for (auto& x : ev) CUDA_TRY(cudaEventCreate(&x));
+        cudaError_t e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream);   // warm
+        float tc = 0.0f, tr = 0.0f;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(ev[0], B.stream);
+            if (e == cudaSuccess) e = launch_raster_crossings(B.d_jobs, B.edge_blocks, B.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], B.stream);
+            if (e == cudaSuccess) e = launch_raster_rows(B.d_jobs, B.row_blocks, B.max_n, B.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2], B.stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+            float a = 0.0f, b = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+            tc += a;
+            tr += b;
+        }
+        for (auto& x : ev) cudaEventDestroy(x);
+        if (e != cudaSuccess) rc = fail(INIM_E_CUDA, std::string("profile: ") + cudaGetErrorString(e));
+        ms[0] = tc / (float)reps;
+        ms[1] = tr / (float)reps;
+    }
+    for (int i = 2; i < kNumStages && rc == INIM_OK; ++i) {
         cudaError_t e = stage(i);                       // warm
         if (e == cudaSuccess) e = cudaEventRecord(e0, B.stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = stage(i);

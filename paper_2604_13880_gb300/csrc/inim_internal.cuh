@@ -222,6 +222,8 @@ cudaError_t raster_setup(int max_n);   // once per process
 cudaError_t launch_raster_prologue(const Job* d_jobs, int n_jobs, const BlockMap& edge_blocks, cudaStream_t s);
 cudaError_t launch_raster_main(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& row_blocks,
                                int max_n, cudaStream_t s);
+cudaError_t launch_raster_crossings(const Job* d_jobs, const BlockMap& edge_blocks, cudaStream_t s);
+cudaError_t launch_raster_rows(const Job* d_jobs, const BlockMap& row_blocks, int max_n, cudaStream_t s);
 cudaError_t launch_density_table(const Job* d_jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_scan_fp32(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
                              ScanTile tile, const float* dtex, cudaStream_t s, int phase = 0);

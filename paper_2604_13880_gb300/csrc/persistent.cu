@@ -121,7 +121,7 @@ __device__ bool one_iteration(const PersistPlan& P, unsigned char* smem) {
         const int2 m = P.edge_items[it];
         const Job& J = P.jobs[m.x];
         const int e = m.y * kPersistThreads + tid;
-        if (active(J) && e < J.n_edges) emit_crossings_edge(J, e);
+        if (active(J)) emit_crossings_warp(J, e, e < J.n_edges);
     }
     for (int j = blockIdx.x; j < P.n_jobs; j += gridDim.x) {
         const Job& J = P.jobs[j];

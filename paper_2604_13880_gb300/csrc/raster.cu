@@ -33,15 +33,16 @@ __global__ void __launch_bounds__(256) k_raster_reset(const Job* __restrict__ jo
     reset_buckets_block(J);
 }
 
-// The crossing keys of the current vertex positions, one thread per edge; the
-// first edge block of a job also clears its pixel counts and big-row list.
+// The crossing keys of the current vertex positions, one lane per edge, the
+// crossings spread over each warp; the first edge block of a job also clears
+// its pixel counts and big-row list.
 __global__ void __launch_bounds__(256) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
     pdl_wait_and_release();
     if (!J.st->active) return;
     const int e = m.y * blockDim.x + threadIdx.x;
-    if (e < J.n_edges) emit_crossings_edge(J, e);
+    emit_crossings_warp(J, e, e < J.n_edges);
     if (m.y == 0) reset_raster_block(J);
 }
 
@@ -83,14 +84,21 @@ cudaError_t launch_raster_prologue(const Job* d_jobs, int n_jobs, const BlockMap
     return launch_pdl(k_raster_reset, n_jobs, 256, 0, s, d_jobs);
 }
 
+cudaError_t launch_raster_crossings(const Job* d_jobs, const BlockMap& edge_blocks, cudaStream_t s) {
+    return launch_pdl(k_crossings, edge_blocks.n_blocks, 256, 0, s, d_jobs, (const int2*)edge_blocks.d_map);
+}
+
+cudaError_t launch_raster_rows(const Job* d_jobs, const BlockMap& row_blocks, int max_n, cudaStream_t s) {
+    return launch_pdl(k_raster_rows, row_blocks.n_blocks, kWarpsPerBlock * 32, (size_t)kWarpsPerBlock * max_n * 2, s,
+                      d_jobs, (const int2*)row_blocks.d_map);
+}
+
 // crossing keys into the row buckets, then the rows; big rows finish in the
 // density kernel
 cudaError_t launch_raster_main(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& row_blocks,
                                int max_n, cudaStream_t s) {
-    cudaError_t e = launch_pdl(k_crossings, edge_blocks.n_blocks, 256, 0, s, d_jobs, (const int2*)edge_blocks.d_map);
-    if (e == cudaSuccess)
-        e = launch_pdl(k_raster_rows, row_blocks.n_blocks, kWarpsPerBlock * 32, (size_t)kWarpsPerBlock * max_n * 2, s,
-                       d_jobs, (const int2*)row_blocks.d_map);
+    cudaError_t e = launch_raster_crossings(d_jobs, edge_blocks, s);
+    if (e == cudaSuccess) e = launch_raster_rows(d_jobs, row_blocks, max_n, s);
     return e;
 }
 

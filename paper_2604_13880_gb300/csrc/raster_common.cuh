@@ -51,26 +51,58 @@ __device__ __forceinline__ int clamped_ceil_div(long long num, long long den, in
     return (int)(c > n ? n : c);
 }
 
-// The crossings of one edge of region `reg` with the texture rows it spans:
-// (reg << 16 | first counted column) keys appended to the rows' fixed-stride
-// buckets.  A bucket that would overflow raises the capacity error (its row
-// is then written as background).
-__device__ __forceinline__ void emit_crossings_pts(const Job& J, unsigned reg, float2 p, float2 q) {
-    EdgeFix f;
-    if (!edge_rows_pts(J, p, q, f)) return;
-    const long long dY = f.Y1 - f.Y0;
-    const long long dX = f.X1 - f.X0;
-    const long long den = 256 * dY;
-    for (int j = f.jlo; j <= f.jhi; ++j) {
-        const long long Yc = 256LL * j + 128;
-        const int c = clamped_ceil_div(dX * (Yc - f.Y0) + (f.X0 - 128) * dY, den, J.n);
-        const int slot = atomicAdd(&J.row_cnt[j], 1);
-        if (slot < kKeyStride) J.keys[(size_t)j * kKeyStride + slot] = (reg << 16) | (unsigned)c;
+// The crossings of 32 edges with the texture rows they span, one edge per
+// lane of a full warp (lanes with valid == false take part with no
+// crossings): (region << 16 | first counted column) keys appended to the
+// rows' fixed-stride buckets; a bucket that would overflow raises the
+// capacity error when its row is rasterised.  A stretched edge can span
+// hundreds of rows; instead of one lane walking them all, the warp numbers
+// the crossings of its 32 edges with a prefix sum and hands them out 32 at a
+// time: crossing i belongs to the last lane whose exclusive prefix is <= i
+// (found by a binary search over the lanes' prefixes), which supplies the
+// edge through shuffles.  The warp's serial work is total / 32 crossings
+// instead of the longest edge's row count.
+__device__ __forceinline__ void emit_crossings_warp(const Job& J, int e, bool valid) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    EdgeFix f{};
+    unsigned reg = 0;
+    int cnt = 0;
+    if (valid) {
+        const int2 ab = J.edges[e];
+        reg = (unsigned)J.edge_region[e];
+        if (edge_rows_pts(J, J.xy[ab.x], J.xy[ab.y], f)) cnt = f.jhi - f.jlo + 1;
     }
-}
-__device__ __forceinline__ void emit_crossings_edge(const Job& J, int e) {
-    const int2 ab = J.edges[e];
-    emit_crossings_pts(J, (unsigned)J.edge_region[e], J.xy[ab.x], J.xy[ab.y]);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(full, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+        const int i = base + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = owner + step;
+            if (__shfl_sync(full, excl, cand) <= i) owner = cand;
+        }
+        const long long X0 = __shfl_sync(full, f.X0, owner), Y0 = __shfl_sync(full, f.Y0, owner);
+        const long long X1 = __shfl_sync(full, f.X1, owner), Y1 = __shfl_sync(full, f.Y1, owner);
+        const int jlo = __shfl_sync(full, f.jlo, owner);
+        const int first = __shfl_sync(full, excl, owner);
+        const unsigned r = __shfl_sync(full, reg, owner);
+        if (i < total) {
+            const int j = jlo + (i - first);
+            const long long dY = Y1 - Y0, dX = X1 - X0;
+            const long long Yc = 256LL * j + 128;
+            const int c = clamped_ceil_div(dX * (Yc - Y0) + (X0 - 128) * dY, 256 * dY, J.n);
+            const int slot = atomicAdd(&J.row_cnt[j], 1);
+            if (slot < kKeyStride) J.keys[(size_t)j * kKeyStride + slot] = (r << 16) | (unsigned)c;
+        }
+    }
 }
 
 // Per job, while the keys of an iteration are being emitted (one block):

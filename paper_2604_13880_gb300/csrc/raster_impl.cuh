@@ -138,8 +138,20 @@ __device__ inline void raster_row(const Job& J, int j, RowShared& sh) {
                 }
                 lab[k] = (uint16_t)best;
             }
-            if (lab[k] != (uint16_t)R) atomicAdd(&J.counts[lab[k]], 1);
         }
+        // counts as run lengths over this thread's CPT pixels
+        unsigned cur = lab[0];
+        int run = 0;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            if (lab[k] != cur) {
+                if (cur != (unsigned)R) atomicAdd(&J.counts[cur], run);
+                cur = lab[k];
+                run = 0;
+            }
+            ++run;
+        }
+        if (cur != (unsigned)R) atomicAdd(&J.counts[cur], run);
         if (tid == 0) atomicExch(&J.st->overlap, 1);
     } else {
         for (int p = tid; p < nspan; p += blockDim.x) {
@@ -272,9 +284,23 @@ __device__ inline void raster_row_warp(const Job& J, int j, int cnt, uint16_t* r
             }
         }
     } else {
-        // fold-over in this row: counts from the resolved labels
-        for (int i = lane; i < n; i += 32)
-            if (row[i] != (uint16_t)R) atomicAdd(&J.counts[row[i]], 1);
+        // fold-over in this row: counts from the resolved labels, as run
+        // lengths over each lane's n/32 contiguous pixels (one atomic per run
+        // instead of one per pixel on a few hot counters)
+        const int per = n >> 5;
+        const int p0 = lane * per;
+        unsigned cur = row[p0];
+        int run = 0;
+        for (int i = p0; i < p0 + per; ++i) {
+            const unsigned l = row[i];
+            if (l != cur) {
+                if (cur != R) atomicAdd(&J.counts[cur], run);
+                cur = l;
+                run = 0;
+            }
+            ++run;
+        }
+        if (cur != R) atomicAdd(&J.counts[cur], run);
         if (lane == 0) atomicExch(&J.st->overlap, 1);
     }
     // write the row
