@@ -174,6 +174,43 @@ def precision_study(args):
 
 
 # ---------------------------------------------------------------------------
+# small fixed cases for profiler captures (ncu): one batch, two iterations
+# ---------------------------------------------------------------------------
+def ncu_case(args):
+    """direct72: the sweep's 72-solve direct batch; chain3: the 3-solve batch
+    of its cumulative series.  Scan tiles fixed to the ones the autotuner
+    picks for the sweep (64/4/256 for the 72-solve batch, 8/4/256 for the
+    3-solve batch).  Per iteration the batch launches, in order: k_crossings,
+    k_raster_rows, k_density_table, k_scan_band<...,1>, k_scan_carry*,
+    k_scan_band<...,3>, k_gather_move, k_areas_errors (after k_raster_reset)."""
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import _lib, synth
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = np.ascontiguousarray(w["values"].astype(np.float32))
+    m = P.inim_map_create(mesh)
+    P.inim_set_scan_tile(k, P.INIM_FP32, 1, 64, 4, 256)
+    P.inim_set_scan_tile(k, P.INIM_FP32, 0, 8, 4, 256)
+    steps = range(T_STEPS) if args.ncu_case == "direct72" else range(1)
+    jobs = [(sh, t) for sh in SHAPES for t in steps]
+    arr = (P.inim_job * len(jobs))()
+    outs = [np.empty((mesh.n_verts, 2), np.float32) for _ in jobs]
+    for q, (sh, t) in enumerate(jobs):
+        arr[q].map = m.handle
+        arr[q].values = vals[t].ctypes.data
+        arr[q].init_xy = None
+        arr[q].out_xy = outs[q].ctypes.data
+        arr[q].params = P.params(log2_res=k, shape=sh, max_iters=2, xi_stop=0.0, stall_window=0)
+        arr[q].stats = None
+    _lib.check(_lib.load().inim_run_batch(arr, len(arr), None), "ncu case")
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "jobs": len(jobs), "iterations": 2}))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -187,12 +224,16 @@ def main():
                     help="instead of the sweep: K iterations of the 4096^2 precision workload in FP32, "
                          "FIX64 and compensated sums; results to --study-out for the FP64 oracle comparison")
     ap.add_argument("--study-out", default="precision_study.npz")
+    ap.add_argument("--ncu-case", choices=["direct72", "chain3"], default=None,
+                    help="instead of the sweep: one batch for two iterations (small profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
     if args.precision_study:
         return precision_study(args)
+    if args.ncu_case:
+        return ncu_case(args)
 
     import torch
     import paper_2604_13880_gb300 as P

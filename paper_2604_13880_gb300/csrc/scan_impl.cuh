@@ -31,6 +31,7 @@
 #pragma once
 
 #include "inim_internal.cuh"
+#include "tma.cuh"
 
 namespace inim {
 
@@ -211,10 +212,41 @@ struct ScanShared {
     float dens[kDensSmem];
 };
 
+// Label rows staged by bulk copies: a ring of DEPTH rows in shared memory, one
+// mbarrier per slot; row r lives in slot r % DEPTH and completes the slot's
+// barrier phase r / DEPTH.
+template <int DEPTH>
+struct LabelRing {
+    uint16_t* rows;            // [DEPTH][N] (dynamic shared memory)
+    uint64_t* bars;            // [DEPTH]
+};
+constexpr int kLabelDepth = 4;
+
+template <int CPT>
+__device__ __forceinline__ LabelWords<CPT> smem_labels(const uint16_t* row, int i0) {
+    LabelWords<CPT> L;
+    const uint16_t* src = row + i0;
+    if constexpr (CPT == 8) {
+        const uint4 v = *reinterpret_cast<const uint4*>(src);
+        L.w[0] = v.x; L.w[1] = v.y; L.w[2] = v.z; L.w[3] = v.w;
+    } else if constexpr (CPT == 4) {
+        const uint2 v = *reinterpret_cast<const uint2*>(src);
+        L.w[0] = v.x; L.w[1] = v.y;
+    } else if constexpr (CPT == 2) {
+        L.w[0] = *reinterpret_cast<const unsigned*>(src);
+    } else {
+        L.w[0] = src[0];
+    }
+    return L;
+}
+
 // phase 1 (PHASE == 1) or phase 3 (PHASE == 3) of one band, by a block of NT
-// threads; the caller provides the shared memory
-template <class Acc, int CPT, int NT, int PHASE>
-__device__ inline void scan_band_body(const Job& J, int band, const float* __restrict__ dtex, ScanShared<Acc, NT>& sh) {
+// threads; the caller provides the shared memory.  DEPTH > 0: the label rows
+// arrive through a ring of bulk copies issued DEPTH rows ahead (ring must
+// then be set); DEPTH == 0: each thread loads its labels two rows ahead.
+template <class Acc, int CPT, int NT, int PHASE, int DEPTH = 0>
+__device__ inline void scan_band_body(const Job& J, int band, const float* __restrict__ dtex, ScanShared<Acc, NT>& sh,
+                                      LabelRing<DEPTH> ring = {}) {
     using T = typename Acc::T;
     const int n = J.n, H = J.H, nb = J.nb;
     const int j0 = band * H;
@@ -258,8 +290,22 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
     T* RCout = reinterpret_cast<T*>(J.rowcum);
 
     // density source: a given texture, or labels through the region table
-    // (in shared memory when it fits); labels are loaded two rows ahead
+    // (in shared memory when it fits); labels arrive DEPTH rows ahead through
+    // the ring, or two rows ahead in registers
     const bool from_labels = (dtex == nullptr);
+    constexpr bool kRing = DEPTH > 0;
+    const bool use_ring = kRing && from_labels;
+    constexpr unsigned kRowBytes = 2u * CPT * NT;
+    if constexpr (kRing) {
+        if (tid == 0) {
+            for (int q = 0; q < DEPTH; ++q) mbar_init(ring.bars + q, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (use_ring && tid == 0)
+            for (int q = 0; q < DEPTH && q < rows; ++q)
+                tma_load_1d(ring.rows + q * (CPT * NT), J.labels + (size_t)(j0 + q) * n, kRowBytes, ring.bars + q);
+    }
     const float* table = J.dens;
     if (from_labels && J.n_regions + 1 <= kDensSmem) {
         for (int v = tid; v <= J.n_regions; v += NT) sh.dens[v] = J.dens[v];
@@ -269,15 +315,22 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
     LabelWords<CPT> lw0{}, lw1{};
     float dn[CPT];
     if (from_labels) {
-        lw0 = load_labels<CPT>(J, j0, i0);
-        if (rows > 1) lw1 = load_labels<CPT>(J, j0 + 1, i0);
+        if (!use_ring) {
+            lw0 = load_labels<CPT>(J, j0, i0);
+            if (rows > 1) lw1 = load_labels<CPT>(J, j0 + 1, i0);
+        }
     } else {
         load_density<CPT>(J, dtex, j0, i0, dn);
     }
     for (int r = 0; r < rows; ++r) {
         const int j = j0 + r;
         float d[CPT];
-        if (from_labels) {
+        bool row_ok = true;
+        if (use_ring) {
+            const int q = r % DEPTH;
+            row_ok = mbar_wait(ring.bars + q, (unsigned)(r / DEPTH) & 1u);
+            labels_to_density<CPT>(smem_labels<CPT>(ring.rows + q * (CPT * NT), i0), table, d);
+        } else if (from_labels) {
             labels_to_density<CPT>(lw0, table, d);
             lw0 = lw1;
             if (r + 2 < rows) lw1 = load_labels<CPT>(J, j + 2, i0);
@@ -303,7 +356,22 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
         if (lane == 31) sh.wtot[buf][wid] = incl;
         sh.e1first[buf][tid] = E1[0];
         sh.e2last[buf][tid] = E2[CPT - 1];
-        __syncthreads();
+        if (__syncthreads_or(!row_ok)) {
+            // a staged row never arrived: record it, drain the copies still
+            // in flight (bounded), leave the band unfinished
+            if (tid == 0) {
+                atomicExch(&J.st->error, INIM_E_TIMEOUT);
+                for (int rr = r; rr < rows && rr < r + DEPTH; ++rr)
+                    mbar_wait(ring.bars + rr % (DEPTH > 0 ? DEPTH : 1), (unsigned)(rr / (DEPTH > 0 ? DEPTH : 1)) & 1u);
+            }
+            return;
+        }
+        // every thread has read this row's slot: refill it DEPTH rows ahead
+        if (use_ring && tid == 0 && r + DEPTH < rows) {
+            fence_proxy_async_smem();
+            tma_load_1d(ring.rows + (r % DEPTH) * (CPT * NT), J.labels + (size_t)(j + DEPTH) * n, kRowBytes,
+                        ring.bars + r % DEPTH);
+        }
         T off = Acc::sub(incl, run);          // exclusive within the warp
         T rowtot = Acc::zero();
 #pragma unroll
@@ -385,11 +453,14 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
                                                   const int2* __restrict__ bmap,
                                                   const float* __restrict__ dtex) {
     __shared__ ScanShared<Acc, NT> sh;
+    __shared__ uint64_t bars[kLabelDepth];
+    extern __shared__ __align__(128) unsigned char scan_ring[];     // [kLabelDepth][CPT * NT] u16
     const int2 m = bmap[blockIdx.x];
     const Job& J = jobs[m.x];
     pdl_wait_and_release();
     if (!J.st->active) return;
-    scan_band_body<Acc, CPT, NT, PHASE>(J, m.y, dtex, sh);
+    LabelRing<kLabelDepth> ring{reinterpret_cast<uint16_t*>(scan_ring), bars};
+    scan_band_body<Acc, CPT, NT, PHASE, kLabelDepth>(J, m.y, dtex, sh, ring);
 }
 
 // phase 2: carries.  Each carry is an exclusive prefix sum over the bands b'
@@ -550,14 +621,24 @@ cudaError_t launch_scan_tile(const Job* d_jobs, const BlockMap& band, const Bloc
                              const float* dtex, int phase, cudaStream_t s) {
     const int2* bm = band.d_map;
     const int2* cm = carry.d_map;
+    constexpr size_t ring_bytes = (size_t)kLabelDepth * CPT * NT * 2;
+    static bool attr_set = false;                  // per instantiation: allow the ring above 48 KB in total
     cudaError_t e = cudaSuccess;
-    if (phase == 0 || phase == 1) e = launch_pdl(k_scan_band<Acc, CPT, NT, 1>, band.n_blocks, NT, 0, s, d_jobs, bm, dtex);
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_scan_band<Acc, CPT, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_scan_band<Acc, CPT, NT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (phase == 0 || phase == 1)
+        e = launch_pdl(k_scan_band<Acc, CPT, NT, 1>, band.n_blocks, NT, ring_bytes, s, d_jobs, bm, dtex);
     if (e == cudaSuccess && (phase == 0 || phase == 2)) {
         if (carry.q_per_block == 32) e = launch_pdl(k_scan_carry_grouped<Acc>, carry.n_blocks, 32 * kCarryGroups, 0, s, d_jobs, cm);
         else e = launch_pdl(k_scan_carry<Acc>, carry.n_blocks, 256, 0, s, d_jobs, cm);
     }
     if (e == cudaSuccess && (phase == 0 || phase == 3))
-        e = launch_pdl(k_scan_band<Acc, CPT, NT, 3>, band.n_blocks, NT, 0, s, d_jobs, bm, dtex);
+        e = launch_pdl(k_scan_band<Acc, CPT, NT, 3>, band.n_blocks, NT, ring_bytes, s, d_jobs, bm, dtex);
     return e;
 }
 
