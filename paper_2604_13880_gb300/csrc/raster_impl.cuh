@@ -221,6 +221,21 @@ __device__ __forceinline__ void warp_bitonic(unsigned (&k)[KPL], int lane) {
     }
 }
 
+// Paint the span [a, b) of one region into the row copy, only over pixels that
+// are still background; returns the span's length on lane 0 (0 elsewhere).
+__device__ __forceinline__ int paint_span(uint16_t* row, unsigned R, unsigned ka, unsigned kb, int lane) {
+    const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
+    const uint16_t v = (uint16_t)(ka >> 16);
+    int len = 0;
+    if (a < b) {
+        if (lane == 0) len = b - a;
+        for (int i = a + lane; i < b; i += 32)
+            if (row[i] == (uint16_t)R) row[i] = v;
+    }
+    __syncwarp();
+    return len;
+}
+
 // One row: keys sorted by (region, column) give each region's spans as
 // consecutive pairs.  The spans are painted into a shared-memory copy of the
 // row in sorted order, writing only still-background pixels, so a pixel in
@@ -245,21 +260,21 @@ __device__ inline void raster_row_warp(const Job& J, int j, int cnt, uint16_t* r
     __syncwarp();
     // paint spans in sorted order
     int my_len = 0;
-    const int src_lanes = (cnt + KPL - 1) / KPL;
-    for (int src = 0; src < src_lanes; ++src) {
+    if constexpr (KPL == 1) {
+        // pair p is (lane 2p, lane 2p + 1)
+        for (int p = 0; 2 * p + 1 < cnt; ++p)
+            my_len += paint_span(row, R, __shfl_sync(0xffffffffu, key[0], 2 * p),
+                                 __shfl_sync(0xffffffffu, key[0], 2 * p + 1), lane);
+    } else {
+        const int src_lanes = (cnt + KPL - 1) / KPL;
+        for (int src = 0; src < src_lanes; ++src) {
 #pragma unroll
-        for (int t = 0; t < KPL / 2; ++t) {
-            const unsigned ka = __shfl_sync(0xffffffffu, key[2 * t], src);
-            const unsigned kb = __shfl_sync(0xffffffffu, key[2 * t + 1], src);
-            if (src * KPL + 2 * t + 1 >= cnt) continue;          // padding (warp-uniform)
-            const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
-            const uint16_t v = (uint16_t)(ka >> 16);
-            if (a < b) {
-                if (lane == 0) my_len += b - a;
-                for (int i = a + lane; i < b; i += 32)
-                    if (row[i] == (uint16_t)R) row[i] = v;
+            for (int t = 0; t < KPL / 2; ++t) {
+                const unsigned ka = __shfl_sync(0xffffffffu, key[2 * t], src);
+                const unsigned kb = __shfl_sync(0xffffffffu, key[2 * t + 1], src);
+                if (src * KPL + 2 * t + 1 >= cnt) continue;          // padding (warp-uniform)
+                my_len += paint_span(row, R, ka, kb, lane);
             }
-            __syncwarp();
         }
     }
     // painted pixels vs summed span lengths
@@ -275,12 +290,20 @@ __device__ inline void raster_row_warp(const Job& J, int j, int cnt, uint16_t* r
     }
     if (painted == my_len) {
         // no overlap: counts from the spans held by this lane
+        if constexpr (KPL == 1) {
+            const unsigned kb = __shfl_down_sync(0xffffffffu, key[0], 1);
+            if ((lane & 1) == 0 && lane + 1 < cnt) {
+                const int a = (int)(key[0] & 0xffffu), b = (int)(kb & 0xffffu);
+                if (a < b) atomicAdd(&J.counts[key[0] >> 16], b - a);
+            }
+        } else {
 #pragma unroll
-        for (int t = 0; t < KPL / 2; ++t) {
-            const int idx = lane * KPL + 2 * t;
-            if (idx + 1 < cnt) {
-                const int a = (int)(key[2 * t] & 0xffffu), b = (int)(key[2 * t + 1] & 0xffffu);
-                if (a < b) atomicAdd(&J.counts[key[2 * t] >> 16], b - a);
+            for (int t = 0; t < KPL / 2; ++t) {
+                const int idx = lane * KPL + 2 * t;
+                if (idx + 1 < cnt) {
+                    const int a = (int)(key[2 * t] & 0xffffu), b = (int)(key[2 * t + 1] & 0xffffu);
+                    if (a < b) atomicAdd(&J.counts[key[2 * t] >> 16], b - a);
+                }
             }
         }
     } else {
@@ -323,7 +346,9 @@ __device__ __forceinline__ void raster_rows_item(const Job& J, int first_row, ui
         if (lane == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
         return;
     }
-    if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, row, lane);
+    if (cnt <= 32) raster_row_warp<1>(J, j, cnt, row, lane);
+    else if (cnt <= 2 * 32) raster_row_warp<2>(J, j, cnt, row, lane);
+    else if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, row, lane);
     else if (cnt <= 8 * 32) raster_row_warp<8>(J, j, cnt, row, lane);
     else if (lane == 0) {                            // big row: handled by k_raster_big
         const int q = atomicAdd(&J.st->n_big, 1);
