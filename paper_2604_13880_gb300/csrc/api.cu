@@ -200,6 +200,11 @@ struct Batch {
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph = nullptr;
     cudaGraphExec_t graph1 = nullptr;    // one iteration, for the tail of a fixed-length run
+    // overlapped form (fixed-length runs): each iteration's area kernel on a
+    // side branch, next to the next iteration's raster and scan
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_moved = nullptr, ev_areas = nullptr;
+    cudaGraphExec_t graph_ov = nullptr, graph1_ov = nullptr;
     int graph_iters = 0;
     std::vector<PlainWork> plain;   // per job (plain form only)
     // persistent form: all resolution groups' band / carry items, barrier words,
@@ -243,6 +248,11 @@ struct Batch {
         BlockMap* maps[] = {&edge_blocks, &job_blocks, &row_blocks, &vert_blocks, &region_blocks};
         for (BlockMap* m : maps) dfree(m->d_map);
         for (auto& g : groups) { dfree(g.band.d_map); dfree(g.carry.d_map); }
+        if (graph_ov) cudaGraphExecDestroy(graph_ov);
+        if (graph1_ov) cudaGraphExecDestroy(graph1_ov);
+        if (ev_moved) cudaEventDestroy(ev_moved);
+        if (ev_areas) cudaEventDestroy(ev_areas);
+        if (side) cudaStreamDestroy(side);
         if (ev) cudaEventDestroy(ev);
         if (stream) cudaStreamDestroy(stream);
     }
@@ -343,7 +353,7 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
             const Job& J = B.h_jobs[k];
             for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
             const int len = carry_qspace(J.n, J.nb, J.H);
-            const int qpb = carry_q_per_block(J.nb);
+            const int qpb = carry_q_per_block(J.nb, size_class(group_px[l]));
             for (int q = 0; q < (len + qpb - 1) / qpb; ++q) carry.push_back(make_int2(k, q));
         }
         if (band.empty()) continue;
@@ -352,7 +362,7 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
         g.tile = tile_for(l, B.precision, size_class(group_px[l]));
         CUDA_TRY(make_map(g.band, band));
         CUDA_TRY(make_map(g.carry, carry));
-        g.carry.q_per_block = carry_q_per_block(((1 << l) + g.tile.H - 1) / g.tile.H);
+        g.carry.q_per_block = carry_q_per_block(((1 << l) + g.tile.H - 1) / g.tile.H, size_class(group_px[l]));
         B.groups.push_back(g);
     }
     CUDA_TRY(cudaMemcpy(B.d_jobs, B.h_jobs.data(), nj * sizeof(Job), cudaMemcpyHostToDevice));
@@ -386,6 +396,12 @@ void purge_all() {
 }
 
 // retile one resolution group of a batch in place (buffers sized for min_H)
+long long group_pixels(const Batch& B, int log2n) {
+    long long px = 0;
+    for (auto& sp : B.spec) if (sp.log2n == log2n) px += 1LL << (2 * sp.log2n);
+    return px;
+}
+
 int retile_group(Batch& B, Group& g, ScanTile t) {
     std::vector<int2> band, carry;
     for (int k = 0; k < (int)B.spec.size(); ++k) {
@@ -395,14 +411,14 @@ int retile_group(Batch& B, Group& g, ScanTile t) {
         J.nb = (J.n + t.H - 1) / t.H;
         for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
         const int len = carry_qspace(J.n, J.nb, J.H);
-        const int qpb = carry_q_per_block(J.nb);
+        const int qpb = carry_q_per_block(J.nb, size_class(group_pixels(B, g.log2n)));
         for (int q = 0; q < (len + qpb - 1) / qpb; ++q) carry.push_back(make_int2(k, q));
     }
     dfree(g.band.d_map);
     dfree(g.carry.d_map);
     CUDA_TRY(make_map(g.band, band));
     CUDA_TRY(make_map(g.carry, carry));
-    g.carry.q_per_block = carry_q_per_block((1 << g.log2n) / t.H);
+    g.carry.q_per_block = carry_q_per_block((1 << g.log2n) / t.H, size_class(group_pixels(B, g.log2n)));
     g.tile = t;
     CUDA_TRY(cudaMemcpyAsync(B.d_jobs, B.h_jobs.data(), B.h_jobs.size() * sizeof(Job), cudaMemcpyHostToDevice,
                              B.stream));
@@ -427,8 +443,14 @@ cudaError_t enqueue_prologue(Batch& B, cudaStream_t s) {
     return launch_raster_prologue(B.d_jobs, (int)B.spec.size(), B.edge_blocks, s);
 }
 
-// one fused iteration
-cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s) {
+// One fused iteration.  overlap: the area kernel goes to the side stream once
+// the vertices have moved, and the next iteration's move waits for it (the
+// raster of the next iteration only reads the vertices, the move rewrites
+// them); `first` marks the first iteration of a captured sequence (the
+// previous area kernel finished with the previous graph launch).  Only for
+// runs of a fixed length: a stop decision taken by an area kernel would come
+// after the next iteration's raster started.
+cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s, bool overlap = false, bool first = true) {
     cudaError_t e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, s);
     if (e == cudaSuccess) e = launch_density_table(B.d_jobs, (int)B.spec.size(), s);
     for (auto& g : B.groups) {
@@ -437,8 +459,16 @@ cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s) {
         else if (B.precision == INIM_KAHAN) e = launch_scan_kahan(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
         else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
     }
+    if (overlap && !first && e == cudaSuccess) e = cudaStreamWaitEvent(s, B.ev_areas, 0);
     if (e == cudaSuccess) e = launch_gather(B.d_jobs, B.vert_blocks, B.precision, s);
-    if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, B.region_blocks, 1, s);
+    if (!overlap) {
+        if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, B.region_blocks, 1, s);
+        return e;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(B.ev_moved, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B.side, B.ev_moved, 0);
+    if (e == cudaSuccess) e = launch_areas_errors(B.d_jobs, B.region_blocks, 1, B.side);
+    if (e == cudaSuccess) e = cudaEventRecord(B.ev_areas, B.side);
     return e;
 }
 
@@ -468,11 +498,12 @@ int kernels_per_fused_iteration(const Batch& B) {
 }
 constexpr int kKernelsPerPlainIteration = 15;
 
-cudaError_t capture_iterations(Batch& B, int iters, cudaGraphExec_t* out) {
+cudaError_t capture_iterations(Batch& B, int iters, cudaGraphExec_t* out, bool overlap) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int k = 0; k < iters && e == cudaSuccess; ++k) e = enqueue_fused_iteration(B, B.stream);
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) e = enqueue_fused_iteration(B, B.stream, overlap, k == 0);
+    if (overlap && e == cudaSuccess) e = cudaStreamWaitEvent(B.stream, B.ev_areas, 0);     // join the side branch
     const cudaError_t e2 = cudaStreamEndCapture(B.stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
@@ -481,31 +512,56 @@ cudaError_t capture_iterations(Batch& B, int iters, cudaGraphExec_t* out) {
     return e;
 }
 
-int ensure_graph(Batch& B) {
-    if (B.graph && B.graph1) return INIM_OK;
-    cudaError_t e = capture_iterations(B, kGraphIters, &B.graph);
-    if (e == cudaSuccess) e = capture_iterations(B, 1, &B.graph1);
-    if (e != cudaSuccess) return fail(INIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+int ensure_graph(Batch& B, bool overlap = false) {
     B.graph_iters = kGraphIters;
+    if (!overlap) {
+        if (B.graph && B.graph1) return INIM_OK;
+        cudaError_t e = capture_iterations(B, kGraphIters, &B.graph, false);
+        if (e == cudaSuccess) e = capture_iterations(B, 1, &B.graph1, false);
+        if (e != cudaSuccess) return fail(INIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        return INIM_OK;
+    }
+    if (B.graph_ov && B.graph1_ov) return INIM_OK;
+    if (!B.side) {
+        int prio = 0;
+        CUDA_TRY(cudaStreamGetPriority(B.stream, &prio));
+        CUDA_TRY(cudaStreamCreateWithPriority(&B.side, cudaStreamNonBlocking, prio));
+        CUDA_TRY(cudaEventCreateWithFlags(&B.ev_moved, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&B.ev_areas, cudaEventDisableTiming));
+    }
+    cudaError_t e = capture_iterations(B, kGraphIters, &B.graph_ov, true);
+    if (e == cudaSuccess) e = capture_iterations(B, 1, &B.graph1_ov, true);
+    if (e != cudaSuccess) return fail(INIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     return INIM_OK;
 }
 
 // launch the graphs for `iters` more iterations: full replays, then the
 // one-iteration graph for the remainder (no idle iterations at the end)
-cudaError_t launch_iterations(Batch& B, int iters) {
+cudaError_t launch_iterations(Batch& B, int iters, bool overlap = false) {
     const int per = kernels_per_fused_iteration(B);
+    cudaGraphExec_t full = overlap ? B.graph_ov : B.graph, one = overlap ? B.graph1_ov : B.graph1;
     while (iters >= B.graph_iters) {
-        cudaError_t e = cudaGraphLaunch(B.graph, B.stream);
+        cudaError_t e = cudaGraphLaunch(full, B.stream);
         if (e != cudaSuccess) return e;
         g_launches += (long long)B.graph_iters * per;
         iters -= B.graph_iters;
     }
     for (; iters > 0; --iters) {
-        cudaError_t e = cudaGraphLaunch(B.graph1, B.stream);
+        cudaError_t e = cudaGraphLaunch(one, B.stream);
         if (e != cudaSuccess) return e;
         g_launches += per;
     }
     return cudaSuccess;
+}
+
+// every job runs exactly max_iters iterations (no stop rule): the overlapped
+// graphs are safe
+bool fixed_length(const Batch& B, int max_iters) {
+    for (const JobState& st : B.h_states) {
+        const bool rule = st.stop_on_rule && (st.xi_stop > 0.0f || st.eps_stop > 0.0f || st.stall_window > 0);
+        if (rule || st.max_iters != max_iters) return false;
+    }
+    return true;
 }
 
 JobState initial_state(const inim_params& p, int stop_on_rule, int max_iters) {
@@ -565,6 +621,8 @@ int run_persistent(Batch& B, int iters, int rounds, const std::vector<int>& job_
     const int nj = (int)B.spec.size();
     int st = ensure_rounds(B, rounds);
     if (st != INIM_OK) return st;
+    CUDA_TRY(enqueue_prologue(B, B.stream));              // empty buckets, restarted parity counters
+    g_launches += 1;
     CUDA_TRY(cudaMemcpyAsync(B.d_job_rounds, job_rounds.data(), nj * sizeof(int), cudaMemcpyHostToDevice, B.stream));
     CUDA_TRY(cudaMemcpyAsync(B.d_round_init, B.h_states.data(), nj * sizeof(JobState), cudaMemcpyHostToDevice,
                              B.stream));
@@ -584,11 +642,12 @@ int run_persistent(Batch& B, int iters, int rounds, const std::vector<int>& job_
 
 // enqueue a fixed-iteration run of the batch (graph replays) without waiting
 int enqueue_fused_async(Batch& B, int max_iters) {
-    int st = ensure_graph(B);
+    const bool ov = fixed_length(B, max_iters);
+    int st = ensure_graph(B, ov);
     if (st != INIM_OK) return st;
     CUDA_TRY(enqueue_prologue(B, B.stream));
     g_launches += 1;                                       // bucket reset
-    CUDA_TRY(launch_iterations(B, max_iters));
+    CUDA_TRY(launch_iterations(B, max_iters, ov));
     return INIM_OK;
 }
 
@@ -600,14 +659,15 @@ bool needs_poll(const inim_params& p) {
 int run_fused(Batch& B, int max_iters, bool poll) {
     const int nj = (int)B.spec.size();
     if (persistent_ok(B)) return run_persistent(B, max_iters, 1, std::vector<int>(nj, 1));
-    int st = ensure_graph(B);
+    const bool ov = !poll && fixed_length(B, max_iters);
+    int st = ensure_graph(B, ov);
     if (st != INIM_OK) return st;
     CUDA_TRY(enqueue_prologue(B, B.stream));
     g_launches += 1;                                       // bucket reset
     int done = 0;
     while (done < max_iters) {
         const int step = std::min(B.graph_iters, max_iters - done);
-        CUDA_TRY(launch_iterations(B, step));
+        CUDA_TRY(launch_iterations(B, step, ov));
         done += step;
         if (poll && done < max_iters) {
             CUDA_TRY(cudaMemcpyAsync(B.h_states.data(), B.d_states, nj * sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));

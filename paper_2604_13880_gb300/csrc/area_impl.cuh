@@ -24,7 +24,7 @@ __device__ inline void errors_and_stop(const Job& J, int update_state) {
     __shared__ double ssum[kRegionsPerBlock], smax[kRegionsPerBlock];
     __shared__ int sfold[kRegionsPerBlock];
     JobState* st = J.st;
-    const double M = st->mass;
+    const double M = st->mass_it[st->area_it & 1];       // this iteration's raster
     double sum = 0.0, mx = 0.0;
     int fold = 0;
     for (int v = threadIdx.x; v < J.n_regions; v += blockDim.x) {
@@ -54,6 +54,7 @@ __device__ inline void errors_and_stop(const Job& J, int update_state) {
         const double eps = S / (double)J.n_regions;
         st->eps = eps;
         st->xi = X;
+        st->area_it += 1;
         if (F) st->foldover = 1;
         if (update_state) {
             st->iters += 1;

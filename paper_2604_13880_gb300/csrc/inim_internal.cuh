@@ -34,6 +34,10 @@ struct JobState {
     int   fix_bits;      // fraction bits of the fixed-point InIms
     double d0;           // area-weighted mean density of the regions
     double mass;         // total mass in the texture (w(v) = s(v) / mass)
+    double mass_it[2];   // the same by iteration parity: the area kernel of an
+                         // iteration may run next to the next iteration's density
+    int   raster_it;     // density tables built in this run (selects mass_it)
+    int   area_it;       // error reductions done in this run (selects mass_it)
     double bdv_abs;      // background density in value units
     int   stop_on_rule;  // 0: run exactly max_iters (no early stop)
     int   blocks_done;   // area blocks finished in this iteration (last one reduces)

@@ -22,7 +22,6 @@ namespace {
 constexpr int kPersistThreads = 256;
 // the density phase keeps its reduction arrays right after the row scratch,
 // at a 16-byte aligned offset (sizeof(RowShared) is not a multiple of 8)
-constexpr size_t kRowSharedPadded = (sizeof(RowShared) + 15) & ~size_t(15);
 static_assert(kRowSharedPadded % 16 == 0, "aligned reduction arrays");
 constexpr long long kSpinCap = 1LL << 24;   // ~1-2 s of polling with back-off
 
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persistent(PersistPlan P
 }  // namespace
 
 int persistent_smem_bytes(int max_n) {
-    size_t a = kRowSharedPadded + 32 * sizeof(double) + 32 * sizeof(long long);
+    size_t a = kTableSmem;
     size_t b = sizeof(ScanShared<AccF32, kPersistThreads>);
     size_t c = (size_t)kWarpsPerBlock * max_n * 2;
     size_t m = a > b ? a : b;

@@ -25,11 +25,16 @@ namespace inim {
 
 namespace {
 
-// Empty buckets (a block per job) at the start of a run.
+// Empty buckets and restarted iteration-parity counters (a block per job) at
+// the start of a run.
 __global__ void __launch_bounds__(256) k_raster_reset(const Job* __restrict__ jobs) {
     const Job& J = jobs[blockIdx.x];
     pdl_wait_and_release();
     if (!J.st->active) return;
+    if (threadIdx.x == 0) {
+        J.st->raster_it = 0;
+        J.st->area_it = 0;
+    }
     reset_buckets_block(J);
 }
 

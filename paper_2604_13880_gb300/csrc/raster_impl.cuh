@@ -44,6 +44,10 @@ struct RowShared {
     unsigned wx[kRowThreads / 32];
     unsigned wc[kRowThreads / 32];
 };
+// RowShared plus the density table's reduction arrays in one block of shared
+// memory: [RowShared, padded to 16][32 doubles][32 long longs]
+constexpr size_t kRowSharedPadded = (sizeof(RowShared) + 15) & ~size_t(15);
+constexpr size_t kTableSmem = kRowSharedPadded + 32 * sizeof(double) + 32 * sizeof(long long);
 
 template <int CPT>
 __device__ inline void raster_row(const Job& J, int j, RowShared& sh) {
@@ -404,6 +408,8 @@ __device__ inline void density_table_body(const Job& J, RowShared& rsh, double* 
         st->d0 = d0;
         st->bdv_abs = (double)J.bdv_scale * d0;
         st->mass = empty ? 1.0 : sum_s + st->bdv_abs * (double)o_bg;
+        st->mass_it[st->raster_it & 1] = st->mass;
+        st->raster_it += 1;
         // all InIm magnitudes are <= C' = sum_o + bdv * o_bg (relative units)
         const double cbound = empty ? (double)npx : ((double)sum_o + (double)J.bdv_scale * (double)o_bg);
         int e = 0;

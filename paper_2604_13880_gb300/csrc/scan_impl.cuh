@@ -541,9 +541,13 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
 // as the serial walk, associated by group, with 1/8 of its dependent chain.
 constexpr int kCarryGroups = 8;
 
-// q values per carry block: the grouped form pays off once there are many
-// bands (its dependent chain is nb / 8 loads instead of nb)
-__host__ __device__ inline int carry_q_per_block(int nb) { return nb >= 32 ? 32 : 256; }
+// q values per carry block: the grouped form pays off for a small
+// (latency-bound) batch once there are many bands (its dependent chain is
+// nb / 8 loads instead of nb); a large batch has parallelism enough for the
+// serial walk, which moves fewer blocks.
+__host__ __device__ inline int carry_q_per_block(int nb, int size_class) {
+    return (size_class == 0 && nb >= 32) ? 32 : 256;
+}
 
 template <class Acc>
 __device__ __forceinline__ typename Acc::T carry_term(const Job& J, const typename Acc::T* a, int kind, int q,

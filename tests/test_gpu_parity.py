@@ -351,6 +351,25 @@ def test_batch_mixed_resolutions_equals_single_runs():
         assert stats[b]["iters"] == 10 + 3 * b
 
 
+def test_overlapped_graph_equals_sequential_graph():
+    # a fixed-length batch runs its area kernels next to the next iteration's
+    # raster; with a stop rule that cannot fire the same batch runs the
+    # sequential graph: vertices and the reported errors must be identical
+    w = synth.time_varying_workload()
+    mesh, vals = w["mesh"], w["values"].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    res = []
+    for xi_stop in (0.0, 1e-30):
+        jobs = [dict(map=m, values=vals[t], params=P.params(log2_res=10, shape=sh, max_iters=19, xi_stop=xi_stop,
+                                                            stall_window=0))
+                for t, sh in ((0, 0.25), (5, 0.5), (11, 0.75))]
+        res.append(P.inim_run_batch(jobs))
+    for b in range(3):
+        np.testing.assert_array_equal(res[0][0][b], res[1][0][b])
+        for key in ("iters", "eps", "xi", "foldover", "overlap"):
+            assert res[0][1][b][key] == res[1][1][b][key], (b, key)
+
+
 def test_stop_rule_reports_consistent_errors():
     w = synth.single_step_workload()
     mesh = w["mesh"]
