@@ -41,6 +41,62 @@ METRIC = "InIm iterations/s"
 WORKLOAD = "voronoi200_v50k_res1024_T24_it50_shapes3_direct+cumulative"
 
 
+def whole_job_rate(local_ms, iters_per_rank, world, dist=None, device="cpu"):
+    """Replicas: the slowest rank's time (max over ranks) and the whole-job
+    rate, every rank's iterations divided by that time."""
+    import torch
+    t = torch.tensor([float(local_ms)], device=device, dtype=torch.float64)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, iters_per_rank * world / (ms_max / 1e3)
+
+
+def stage_bytes(n_jobs, N, V, R, E, K, nb):
+    """Algorithmic bytes per launch of every stage over a batch of n_jobs
+    (FP32; per job: P = N^2 pixels, V vertices, R regions, E ring edges, K
+    crossing keys, nb bands)."""
+    Ppx = N * N
+    return {
+        "crossings": n_jobs * (8 * E + 8 * V + 4 * K),
+        "raster_rows": n_jobs * (4 * K + 2 * Ppx),
+        "density_table": n_jobs * (12 * R),
+        "scan_phase1": n_jobs * (2 * Ppx + 3 * nb * N * 4),
+        "scan_carry": n_jobs * (2 * 3 * nb * N * 4),
+        "scan_phase3": n_jobs * (2 * Ppx + 8 * Ppx + 3 * nb * N * 4),
+        "gather_move": n_jobs * 48 * V,
+        "areas_errors": n_jobs * (8 * E + 8 * V + 8 * R),
+    }
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# ncu captures of `bench.py --ncu-case <batch>` with the kernels and tiles of
+# this source; keyed by (batch, stage, band rows, columns per thread, threads)
+TRAFFIC = {
+    ("chain3", "crossings", 8, 4, 256): 2.359e6,
+    ("chain3", "raster_rows", 8, 4, 256): 0.614e6,
+    ("chain3", "density_table", 8, 4, 256): 0.083e6,
+    ("chain3", "scan_phase1", 8, 4, 256): 6.310e6,
+    ("chain3", "scan_carry", 8, 4, 256): 4.767e6,
+    ("chain3", "scan_phase3", 8, 4, 256): 11.033e6,
+    ("chain3", "gather_move", 8, 4, 256): 7.250e6,
+    ("chain3", "areas_errors", 8, 4, 256): 1.986e6,
+    ("direct72", "scan_phase3", 16, 4, 256): 754.772e6,
+}
+
+
+def roofline(batches, bn, sn, pk):
+    b = batches[bn]
+    t = b["tile"]
+    achieved = b["algo"][sn] / (b["stages"][sn] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": sn, "batch": bn, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"],
+            "traffic": TRAFFIC.get((bn, sn, t["band_rows"], t["cols_per_thread"], t["threads"])),
+            "algorithmic_bytes_per_launch": b["algo"][sn], "launch_ms": b["stages"][sn],
+            "launches_per_step": b["per_step"],
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "fallback" not in pk else "fallback"}
+
+
 def crossings_count(mesh, N):
     """Crossing keys of one raster of the map at its start positions: for
     every ring edge, the texture rows whose pixel centres it spans."""
@@ -178,9 +234,9 @@ def precision_study(args):
 # ---------------------------------------------------------------------------
 def ncu_case(args):
     """direct72: the sweep's 72-solve direct batch; chain3: the 3-solve batch
-    of its cumulative series.  Scan tiles fixed to the ones the autotuner
-    picks for the sweep (64/4/256 for the 72-solve batch, 8/4/256 for the
-    3-solve batch).  Per iteration the batch launches, in order: k_crossings,
+    of its cumulative series.  Scan tiles fixed to the ones the sweep ends up
+    with (16/4/256 for the 72-solve batch, chosen on the step; 8/4/256 for
+    the 3-solve batch).  Per iteration the batch launches, in order: k_crossings,
     k_raster_rows, k_density_table, k_scan_band<...,1>, k_scan_carry*,
     k_scan_band<...,3>, k_gather_move, k_areas_errors (after k_raster_reset)."""
     import torch
@@ -191,7 +247,7 @@ def ncu_case(args):
     k = w["log2_res"]
     vals = np.ascontiguousarray(w["values"].astype(np.float32))
     m = P.inim_map_create(mesh)
-    P.inim_set_scan_tile(k, P.INIM_FP32, 1, 64, 4, 256)
+    P.inim_set_scan_tile(k, P.INIM_FP32, 1, 16, 4, 256)
     P.inim_set_scan_tile(k, P.INIM_FP32, 0, 8, 4, 256)
     steps = range(T_STEPS) if args.ncu_case == "direct72" else range(1)
     jobs = [(sh, t) for sh in SHAPES for t in steps]
@@ -344,20 +400,17 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
     t_wall = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed_step")       # profilers can capture exactly the timed steps
     for _ in range(args.steps):
         run_step(plan_d)
+    torch.cuda.nvtx.range_pop()
     ev1.record()
     barrier()
     wall = time.perf_counter() - t_wall
     ms = ev0.elapsed_time(ev1)
     launches = P.inim_launch_count() - launches0
     clk = clocks.stop() if clocks else None
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    total_iters = ITERS_PER_STEP * args.steps * world
-    value = total_iters / (ms_max / 1e3)
+    ms_max, value = whole_job_rate(ms, ITERS_PER_STEP * args.steps, world, dist, dev)
 
     # e2e: the same sweep through the public API with pinned host buffers
     vals_h = torch.as_tensor(vals).pin_memory()
@@ -372,10 +425,7 @@ def main():
         run_step(plan_h)
     barrier()
     e2e_s = time.perf_counter() - t
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ITERS_PER_STEP * e_steps * world / float(e2e_t.item())
+    _, e2e_value = whole_job_rate(1e3 * e2e_s, ITERS_PER_STEP * e_steps, world, dist, dev)
     n_sol = 2 * len(SHAPES) * T_STEPS
     h2d = n_sol * R * 4            # the values of every solve
     d2h = n_sol * V * 8            # the vertices after every solve
@@ -395,39 +445,34 @@ def main():
         line["clocks"] = clk
 
     if rank == 0:
-        # roofline of the dominant stage, measured on the 72-solve batch
-        run_step(plan_d)
-        _lib.check(lib.inim_run_batch(plan_d[1], len(plan_d[1]), None), "direct batch")
-        stages = P.inim_profile_stages(reps=10)
+        # stage times of both batch shapes of the step (CUDA events around each
+        # stage on the library's stream); the step's dominant kernel is the one
+        # with the largest time per step (launch time x launches per step)
         N = 1 << k
-        Ppx = N * N
-        nb = -(-N // tiles["large"]["band_rows"])            # bands of the 72-solve batch's tile
-        n_jobs = len(SHAPES) * T_STEPS
         E = int(P.inim_map_info(m)["n_edges"])
         K = crossings_count(mesh, N)
-        algo = {   # algorithmic bytes per launch over the whole batch (design notes)
-            "crossings": n_jobs * (8 * E + 8 * V + 4 * K),
-            "raster_rows": n_jobs * (4 * K + 2 * Ppx),
-            "density_table": n_jobs * (12 * R),
-            "scan_phase1": n_jobs * (2 * Ppx + 3 * nb * N * 4),
-            "scan_carry": n_jobs * (2 * 3 * nb * N * 4),
-            "scan_phase3": n_jobs * (2 * Ppx + 8 * Ppx + 3 * nb * N * 4),
-            "gather_move": n_jobs * 48 * V,
-            "areas_errors": n_jobs * (8 * E + 8 * V + 8 * R),
-        }
-        dom = max(stages, key=stages.get)
-        pk = peaks()
-        achieved = algo[dom] / (stages[dom] / 1e3) / 1e9
-        line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"],
-                            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                            "algorithmic_bytes_per_launch": algo[dom], "launch_ms": stages[dom],
-                            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "fallback" not in pk
-                            else "fallback"}
-        line["stages_ms"] = stages
-        line["stages_gbs"] = {s: algo[s] / (stages[s] / 1e3) / 1e9 for s in stages}
-        # the same stages (per-step kernels) on a 3-solve batch, latency-bound
+        run_step(plan_d)
+        _lib.check(lib.inim_run_batch(plan_d[1], len(plan_d[1]), None), "direct batch")
+        stages_d = P.inim_profile_stages(reps=10)
         _lib.check(lib.inim_run_batch(plan_d[2], len(plan_d[2]), None), "3-solve batch")
-        line["stages_3solve_ms"] = P.inim_profile_stages(reps=20)
+        stages_c = P.inim_profile_stages(reps=20)
+        batches = {
+            "direct72": dict(stages=stages_d, jobs=len(SHAPES) * T_STEPS, tile=tiles["large"], per_step=ITERS),
+            "chain3": dict(stages=stages_c, jobs=len(SHAPES), tile=tiles["small"], per_step=T_STEPS * ITERS),
+        }
+        pk = peaks()
+        for name, b in batches.items():
+            b["algo"] = stage_bytes(b["jobs"], N, V, R, E, K, -(-N // b["tile"]["band_rows"]))
+        dom_b, dom_s = max(((bn, sn) for bn, b in batches.items() for sn in b["stages"]),
+                           key=lambda x: batches[x[0]]["stages"][x[1]] * batches[x[0]]["per_step"])
+        line["roofline"] = roofline(batches, dom_b, dom_s, pk)
+        dd = max(stages_d, key=stages_d.get)
+        line["roofline_direct72"] = roofline(batches, "direct72", dd, pk)
+        line["stages_ms"] = stages_d
+        line["stages_gbs"] = {st: batches["direct72"]["algo"][st] / (stages_d[st] / 1e3) / 1e9 for st in stages_d}
+        line["stages_3solve_ms"] = stages_c
+        line["stage_ms_per_step"] = {f"{bn}:{sn}": round(b["stages"][sn] * b["per_step"], 3)
+                                     for bn, b in batches.items() for sn in b["stages"]}
         # the sweep with the cumulative series in one persistent launch instead
         # (runs after the direct batch), with its phase times per iteration
         P.inim_set_persistent(True)

@@ -155,7 +155,8 @@ ScanTile tile_for(int log2n, int precision, int cls) {
 }
 
 // (columns per thread, threads) pairs with a compiled band-scan kernel
-constexpr int kTilePairs[][2] = {{2, 128}, {4, 128}, {2, 256}, {8, 128}, {4, 256}, {8, 256}, {4, 512}, {8, 512}};
+constexpr int kTilePairs[][2] = {{2, 128}, {4, 128}, {2, 256}, {8, 128}, {4, 256}, {8, 256}, {4, 512}, {8, 512},
+                                 {16, 64}, {32, 32}};
 constexpr int kTileHeights[] = {4, 8, 16, 32, 64};
 
 bool tile_valid(int log2n, ScanTile t) {

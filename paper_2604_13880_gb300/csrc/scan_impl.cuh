@@ -100,9 +100,12 @@ template <int CPT>
 __device__ __forceinline__ LabelWords<CPT> load_labels(const Job& J, int j, int i0) {
     LabelWords<CPT> L;
     const uint16_t* src = J.labels + (size_t)j * J.n + i0;
-    if constexpr (CPT == 8) {
-        const uint4 v = *reinterpret_cast<const uint4*>(src);
-        L.w[0] = v.x; L.w[1] = v.y; L.w[2] = v.z; L.w[3] = v.w;
+    if constexpr (CPT % 8 == 0) {
+#pragma unroll
+        for (int q = 0; q < CPT / 8; ++q) {
+            const uint4 v = reinterpret_cast<const uint4*>(src)[q];
+            L.w[4 * q] = v.x; L.w[4 * q + 1] = v.y; L.w[4 * q + 2] = v.z; L.w[4 * q + 3] = v.w;
+        }
     } else if constexpr (CPT == 4) {
         const uint2 v = *reinterpret_cast<const uint2*>(src);
         L.w[0] = v.x; L.w[1] = v.y;
@@ -226,9 +229,12 @@ template <int CPT>
 __device__ __forceinline__ LabelWords<CPT> smem_labels(const uint16_t* row, int i0) {
     LabelWords<CPT> L;
     const uint16_t* src = row + i0;
-    if constexpr (CPT == 8) {
-        const uint4 v = *reinterpret_cast<const uint4*>(src);
-        L.w[0] = v.x; L.w[1] = v.y; L.w[2] = v.z; L.w[3] = v.w;
+    if constexpr (CPT % 8 == 0) {
+#pragma unroll
+        for (int q = 0; q < CPT / 8; ++q) {
+            const uint4 v = reinterpret_cast<const uint4*>(src)[q];
+            L.w[4 * q] = v.x; L.w[4 * q + 1] = v.y; L.w[4 * q + 2] = v.z; L.w[4 * q + 3] = v.w;
+        }
     } else if constexpr (CPT == 4) {
         const uint2 v = *reinterpret_cast<const uint2*>(src);
         L.w[0] = v.x; L.w[1] = v.y;
@@ -659,6 +665,8 @@ cudaError_t launch_scan_acc(const Job* d_jobs, const BlockMap& band, const Block
         case 8 * 10000 + 256: return launch_scan_tile<Acc, 8, 256>(d_jobs, band, carry, dtex, phase, s);
         case 4 * 10000 + 512: return launch_scan_tile<Acc, 4, 512>(d_jobs, band, carry, dtex, phase, s);
         case 8 * 10000 + 512: return launch_scan_tile<Acc, 8, 512>(d_jobs, band, carry, dtex, phase, s);
+        case 16 * 10000 + 64: return launch_scan_tile<Acc, 16, 64>(d_jobs, band, carry, dtex, phase, s);
+        case 32 * 10000 + 32: return launch_scan_tile<Acc, 32, 32>(d_jobs, band, carry, dtex, phase, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -234,6 +234,46 @@ def test_one_iteration(shape):
     assert np.abs(x.cpu().numpy() - want).max() <= 1e-5 * EXTENT
 
 
+# degenerate cases of the method: a region whose value is zero (density 0,
+# it can only shrink), a single region in a large background, values over
+# twelve decades, the smallest texture, a vertex count that is no multiple of
+# the block size
+def _one_iteration_case(mesh, vals, k, shape, iters=1):
+    m = P.inim_map_create(mesh)
+    xy = mesh.verts_f32()
+    x = dev(xy)
+    P.inim_iterate(m, x, dev(vals.astype(np.float32)), P.params(log2_res=k, shape=shape), iters)
+    want = xy.astype(np.float64)
+    for _ in range(iters):
+        want, _ = O.iterate(want, arrays(mesh), vals.astype(np.float32).astype(np.float64), k, shape)
+    return x.cpu().numpy(), want
+
+
+def test_zero_valued_region():
+    mesh = synth.voronoi_map(30, 1500, seed=61)
+    vals = synth.lognormal_values(30, seed=62)
+    vals[[3, 17]] = 0.0
+    got, want = _one_iteration_case(mesh, vals, 9, 0.0)
+    assert np.abs(got - want).max() <= 1e-5 * EXTENT
+
+
+def test_single_region_in_background():
+    mesh = synth.square_map([(0.3, 0.35, 0.55, 0.7)])
+    got, want = _one_iteration_case(mesh, np.array([5.0]), 8, 0.25, iters=3)
+    assert np.abs(got - want).max() <= 1e-5 * EXTENT
+    # one region of any value fills its share of the mass: with bdv = d0 it
+    # already has the mean density, so nothing moves
+    assert np.abs(got - mesh.verts).max() <= 1e-6
+
+
+def test_values_over_twelve_decades_at_smallest_texture():
+    mesh = synth.voronoi_map(25, 1233, seed=63)          # 1233: no multiple of 256 vertices
+    vals = 10.0 ** np.random.default_rng(64).uniform(-6, 6, 25)
+    got, want = _one_iteration_case(mesh, vals, 8, 0.5)
+    assert mesh.n_verts % 256 != 0
+    assert np.abs(got - want).max() <= 1e-5 * EXTENT
+
+
 def test_one_iteration_config_timevarying():
     w = synth.time_varying_workload()
     mesh = w["mesh"]
@@ -393,7 +433,7 @@ def test_stop_rule_reports_consistent_errors():
 # ---------------------------------------------------------------------------
 # A8: scan tiles and the autotuner
 # ---------------------------------------------------------------------------
-TILES_1024 = [(h, c, t) for h in (4, 8, 16, 32, 64) for (c, t) in ((8, 128), (4, 256))]
+TILES_1024 = [(h, c, t) for h in (4, 8, 16, 32, 64) for (c, t) in ((8, 128), (4, 256), (16, 64), (32, 32))]
 
 
 @pytest.mark.parametrize("tile", TILES_1024)
@@ -411,6 +451,28 @@ def test_every_scan_tile_is_exact_in_fixed_point(tile):
     np.testing.assert_array_equal(T, I["at"])
     np.testing.assert_array_equal(A, I["A"])
     np.testing.assert_array_equal(B, I["B"])
+
+
+def test_every_scan_tile_gives_identical_iterations_in_fixed_point():
+    # the label path (rows staged by bulk copies) in every tile: the 64-bit
+    # tables are exact, so the moved vertices must not depend on the tile
+    w = synth.time_varying_workload()
+    mesh, vals = w["mesh"], w["values"][0].astype(np.float32)
+    m = P.inim_map_create(mesh)
+    ref = None
+    for tile in TILES_1024:
+        for large in (0, 1):
+            P.inim_set_scan_tile(10, P.INIM_FIX64, large, *tile)
+        try:
+            x = dev(mesh.verts_f32())
+            P.inim_iterate(m, x, dev(vals), P.params(log2_res=10, shape=0.5, precision=P.INIM_FIX64), 2)
+            got = x.cpu().numpy()
+        finally:
+            for large in (0, 1):
+                P.inim_set_scan_tile(10, P.INIM_FIX64, large, 0, 0, 0)
+        if ref is None:
+            ref = got
+        np.testing.assert_array_equal(got, ref, err_msg=str(tile))
 
 
 def test_autotuner_picks_a_valid_tile_and_stays_on_the_oracle():
