@@ -226,18 +226,18 @@ __device__ __forceinline__ void warp_bitonic(unsigned (&k)[KPL], int lane) {
 }
 
 // Paint the span [a, b) of one region into the row copy, only over pixels that
-// are still background; returns the span's length on lane 0 (0 elsewhere).
+// are still background; returns how many of this lane's pixels of the span
+// were painted already (a pixel inside two regions).
 __device__ __forceinline__ int paint_span(uint16_t* row, unsigned R, unsigned ka, unsigned kb, int lane) {
     const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
     const uint16_t v = (uint16_t)(ka >> 16);
-    int len = 0;
-    if (a < b) {
-        if (lane == 0) len = b - a;
-        for (int i = a + lane; i < b; i += 32)
-            if (row[i] == (uint16_t)R) row[i] = v;
+    int over = 0;
+    for (int i = a + lane; i < b; i += 32) {
+        if (row[i] == (uint16_t)R) row[i] = v;
+        else ++over;
     }
     __syncwarp();
-    return len;
+    return over;
 }
 
 // One row: keys sorted by (region, column) give each region's spans as
@@ -257,18 +257,18 @@ __device__ inline void raster_row_warp(const Job& J, int j, int cnt, uint16_t* r
         key[e] = idx < cnt ? bucket[idx] : 0xffffffffu;
     }
     // background fill of the row copy
-    unsigned* row32 = reinterpret_cast<unsigned*>(row);
     const unsigned bg2 = R | (R << 16);
-    for (int i = lane; i < (n >> 1); i += 32) row32[i] = bg2;
+    const uint4 bg8 = make_uint4(bg2, bg2, bg2, bg2);
+    for (int i = lane; i < (n >> 3); i += 32) reinterpret_cast<uint4*>(row)[i] = bg8;
     warp_bitonic<KPL>(key, lane);
     __syncwarp();
-    // paint spans in sorted order
-    int my_len = 0;
+    // paint spans in sorted order, noting pixels that were painted already
+    int my_over = 0;
     if constexpr (KPL == 1) {
         // pair p is (lane 2p, lane 2p + 1)
         for (int p = 0; 2 * p + 1 < cnt; ++p)
-            my_len += paint_span(row, R, __shfl_sync(0xffffffffu, key[0], 2 * p),
-                                 __shfl_sync(0xffffffffu, key[0], 2 * p + 1), lane);
+            my_over += paint_span(row, R, __shfl_sync(0xffffffffu, key[0], 2 * p),
+                                  __shfl_sync(0xffffffffu, key[0], 2 * p + 1), lane);
     } else {
         const int src_lanes = (cnt + KPL - 1) / KPL;
         for (int src = 0; src < src_lanes; ++src) {
@@ -277,22 +277,11 @@ __device__ inline void raster_row_warp(const Job& J, int j, int cnt, uint16_t* r
                 const unsigned ka = __shfl_sync(0xffffffffu, key[2 * t], src);
                 const unsigned kb = __shfl_sync(0xffffffffu, key[2 * t + 1], src);
                 if (src * KPL + 2 * t + 1 >= cnt) continue;          // padding (warp-uniform)
-                my_len += paint_span(row, R, ka, kb, lane);
+                my_over += paint_span(row, R, ka, kb, lane);
             }
         }
     }
-    // painted pixels vs summed span lengths
-    int painted = 0;
-    for (int i = lane; i < (n >> 1); i += 32) {
-        const unsigned w = row32[i];
-        painted += ((w & 0xffffu) != R) + ((w >> 16) != R);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        painted += __shfl_xor_sync(0xffffffffu, painted, o);
-        my_len += __shfl_xor_sync(0xffffffffu, my_len, o);
-    }
-    if (painted == my_len) {
+    if (!__any_sync(0xffffffffu, my_over != 0)) {
         // no overlap: counts from the spans held by this lane
         if constexpr (KPL == 1) {
             const unsigned kb = __shfl_down_sync(0xffffffffu, key[0], 1);
