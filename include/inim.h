@@ -330,11 +330,14 @@ int inim_warmstart_load(const void* weights, size_t bytes);
 /*
  * Tile of the integral-image band scan for one (resolution, precision, size
  * class): band_rows rows per band (one block each), cols_per_thread columns
- * per thread, threads per block (cols_per_thread * threads == N).  large = 1
- * for resolution groups of a batch holding >= 2^23 pixels in total, 0 below.
- * band_rows = 0 restores the built-in default.  The tile changes the FP32
- * summation order (not the FIX64 result).  Setting a tile drops the cached
- * batches.  INIM_E_ARG if no compiled kernel has this tile.
+ * per thread, threads per block (cols_per_thread * threads == N).
+ * cols_per_thread = 0 with threads = 256 selects the parallel-rows form (a
+ * warp computes each row's prefix, one barrier per band; N = 512 or 1024,
+ * band_rows = 8 or 16).  large = 1 for resolution groups of a batch holding
+ * >= 2^23 pixels in total, 0 below.  band_rows = 0 restores the built-in
+ * default.  The tile changes the FP32 summation order (not the FIX64
+ * result).  Setting a tile drops the cached batches.  INIM_E_ARG if no
+ * compiled kernel has this tile.
  */
 int inim_set_scan_tile(int32_t log2_res, int32_t precision, int32_t large, int32_t band_rows,
                        int32_t cols_per_thread, int32_t threads);
@@ -344,7 +347,8 @@ int inim_get_scan_tile(int32_t log2_res, int32_t precision, int32_t large, int32
 /*
  * Autotuner (not part of the paper): builds a batch of these jobs, rasterises
  * their start positions, times every compiled tile (band heights 4..64,
- * every (columns, threads) pair with columns * threads == N) on it with CUDA
+ * every (columns, threads) pair with columns * threads == N, and the
+ * parallel-rows form where it is compiled) on it with CUDA
  * events over `reps` runs of the three scan phases, and sets the fastest tile
  * for each resolution group's (resolution, precision, size class).
  */

@@ -151,16 +151,19 @@ ScanTile default_tile(int log2n) {
 ScanTile tile_for(int log2n, int precision, int cls) {
     ScanTile t = g_tiles[precision][cls][log2n];
     if (t.H <= 0) t = default_tile(log2n);
+    t.n = 1 << log2n;
     return t;
 }
 
 // (columns per thread, threads) pairs with a compiled band-scan kernel
 constexpr int kTilePairs[][2] = {{2, 128}, {4, 128}, {2, 256}, {8, 128}, {4, 256}, {8, 256}, {4, 512}, {8, 512},
-                                 {16, 64}, {32, 32}};
+                                 {16, 64}, {32, 32}, {0, 256}};
 constexpr int kTileHeights[] = {4, 8, 16, 32, 64};
 
 bool tile_valid(int log2n, ScanTile t) {
     const int n = 1 << log2n;
+    if (t.cpt == 0)                               // parallel-rows form: its instantiations
+        return t.nt == 256 && (n == 512 || n == 1024) && (t.H == 8 || t.H == 16);
     bool pair = false;
     for (auto& q : kTilePairs) pair |= (q[0] == t.cpt && q[1] == t.nt);
     bool h = false;
@@ -1490,7 +1493,7 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
         ScanTile best_t = g.tile;
         for (auto& q : kTilePairs) {
             for (int H : kTileHeights) {
-                ScanTile t{H, q[0], q[1]};
+                ScanTile t{H, q[0], q[1], 1 << g.log2n};
                 if (!tile_valid(g.log2n, t)) continue;
                 st = retile_group(B, g, t);
                 if (st != INIM_OK) return st;

@@ -220,7 +220,10 @@ struct BlockMap {            // block -> (job, first item) tables for one kernel
     int   q_per_block = 256; // carry maps: q values per block (32 = the grouped carry kernel)
 };
 
-struct ScanTile { int H; int cpt; int nt; };   // band height, columns/thread, threads
+// band height, columns per thread, threads; cpt == 0 selects the
+// parallel-rows band scan (256 threads), which is instantiated per texture
+// side n
+struct ScanTile { int H; int cpt; int nt; int n = 0; };
 
 cudaError_t raster_setup(int max_n);   // once per process
 cudaError_t launch_raster_prologue(const Job* d_jobs, int n_jobs, const BlockMap& edge_blocks, cudaStream_t s);

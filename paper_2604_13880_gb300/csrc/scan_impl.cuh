@@ -652,9 +652,22 @@ cudaError_t launch_scan_tile(const Job* d_jobs, const BlockMap& band, const Bloc
     return e;
 }
 
+template <class Acc, int N, int H>
+cudaError_t launch_scan_pb(const Job* d_jobs, const BlockMap& band, const BlockMap& carry, const float* dtex,
+                           int phase, cudaStream_t s);
+
 template <class Acc>
 cudaError_t launch_scan_acc(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
                             ScanTile tile, const float* dtex, int phase, cudaStream_t s) {
+    if (tile.cpt == 0) {                          // parallel-rows form
+        switch (tile.n * 100 + tile.H) {
+            case 1024 * 100 + 8: return launch_scan_pb<Acc, 1024, 8>(d_jobs, band, carry, dtex, phase, s);
+            case 1024 * 100 + 16: return launch_scan_pb<Acc, 1024, 16>(d_jobs, band, carry, dtex, phase, s);
+            case 512 * 100 + 8: return launch_scan_pb<Acc, 512, 8>(d_jobs, band, carry, dtex, phase, s);
+            case 512 * 100 + 16: return launch_scan_pb<Acc, 512, 16>(d_jobs, band, carry, dtex, phase, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     const int key = tile.cpt * 10000 + tile.nt;
     switch (key) {
         case 2 * 10000 + 128: return launch_scan_tile<Acc, 2, 128>(d_jobs, band, carry, dtex, phase, s);
@@ -672,3 +685,5 @@ cudaError_t launch_scan_acc(const Job* d_jobs, const BlockMap& band, const Block
 }
 
 }  // namespace inim
+
+#include "scan_pb.cuh"

@@ -433,7 +433,8 @@ def test_stop_rule_reports_consistent_errors():
 # ---------------------------------------------------------------------------
 # A8: scan tiles and the autotuner
 # ---------------------------------------------------------------------------
-TILES_1024 = [(h, c, t) for h in (4, 8, 16, 32, 64) for (c, t) in ((8, 128), (4, 256), (16, 64), (32, 32))]
+TILES_1024 = ([(h, c, t) for h in (4, 8, 16, 32, 64) for (c, t) in ((8, 128), (4, 256), (16, 64), (32, 32))]
+              + [(8, 0, 256), (16, 0, 256)])          # cols_per_thread 0: the parallel-rows band scan
 
 
 @pytest.mark.parametrize("tile", TILES_1024)
