@@ -235,8 +235,8 @@ def precision_study(args):
 def ncu_case(args):
     """direct72: the sweep's 72-solve direct batch; chain3: the 3-solve batch
     of its cumulative series.  Scan tiles fixed to the ones the sweep ends up
-    with (16/4/256 for the 72-solve batch, chosen on the step; 8/4/256 for
-    the 3-solve batch).  Per iteration the batch launches, in order: k_crossings,
+    with (16/4/256 for the 72-solve batch, chosen on the step; 8 rows in the
+    parallel-rows form for the 3-solve batch).  Per iteration the batch launches, in order: k_crossings,
     k_raster_rows, k_density_table, k_scan_band<...,1>, k_scan_carry*,
     k_scan_band<...,3>, k_gather_move, k_areas_errors (after k_raster_reset)."""
     import torch
@@ -248,7 +248,7 @@ def ncu_case(args):
     vals = np.ascontiguousarray(w["values"].astype(np.float32))
     m = P.inim_map_create(mesh)
     P.inim_set_scan_tile(k, P.INIM_FP32, 1, 16, 4, 256)
-    P.inim_set_scan_tile(k, P.INIM_FP32, 0, 8, 4, 256)
+    P.inim_set_scan_tile(k, P.INIM_FP32, 0, 8, 0, 256)
     steps = range(T_STEPS) if args.ncu_case == "direct72" else range(1)
     jobs = [(sh, t) for sh in SHAPES for t in steps]
     arr = (P.inim_job * len(jobs))()

@@ -132,7 +132,7 @@ __device__ bool one_iteration(const PersistPlan& P, unsigned char* smem) {
     for (int it = blockIdx.x; it < P.n_row_items; it += gridDim.x) {
         const int2 m = P.row_items[it];
         const Job& J = P.jobs[m.x];
-        if (active(J)) raster_rows_item(J, m.y, reinterpret_cast<uint16_t*>(smem));
+        if (active(J)) raster_rows_item(J, m.y, reinterpret_cast<unsigned*>(smem));
         __syncthreads();
     }
     if (!grid_barrier(P)) return false;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persistent(PersistPlan P
 int persistent_smem_bytes(int max_n) {
     size_t a = kTableSmem;
     size_t b = sizeof(ScanShared<AccF32, kPersistThreads>);
-    size_t c = (size_t)kWarpsPerBlock * max_n * 2;
+    size_t c = kWarpsPerBlock * row_warp_bytes(max_n);
     size_t m = a > b ? a : b;
     return (int)(m > c ? m : c);
 }

@@ -51,14 +51,13 @@ __global__ void __launch_bounds__(256) k_crossings(const Job* __restrict__ jobs,
     if (m.y == 0) reset_raster_block(J);
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_raster_rows(const Job* __restrict__ jobs,
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_raster_rows(const Job* __restrict__ jobs,
                                                                     const int2* __restrict__ bmap) {
-    extern __shared__ __align__(16) uint16_t rows_smem[];
+    extern __shared__ __align__(16) unsigned rows_smem[];
     const int2 m = bmap[blockIdx.x];                 // (job, first row)
-    const Job& J = jobs[m.x];
+    const Job J = jobs[m.x];                         // fixed over a run: read before the wait
     pdl_wait_and_release();
-    if (!J.st->active) return;
-    raster_rows_item(J, m.y, rows_smem);
+    raster_rows_item(J, m.y, rows_smem, true);
 }
 
 __global__ void __launch_bounds__(kRowThreads) k_density_table(const Job* __restrict__ jobs) {
@@ -78,7 +77,7 @@ cudaError_t raster_setup(int max_n) {
     (void)max_n;
     static bool done = false;
     if (done) return cudaSuccess;
-    const int bytes = kWarpsPerBlock * (1 << kMaxLog2) * 2;
+    const int bytes = (int)(kWarpsPerBlock * row_warp_bytes(1 << kMaxLog2));
     cudaError_t e = cudaFuncSetAttribute(k_raster_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) done = true;
     return e;
@@ -94,7 +93,7 @@ cudaError_t launch_raster_crossings(const Job* d_jobs, const BlockMap& edge_bloc
 }
 
 cudaError_t launch_raster_rows(const Job* d_jobs, const BlockMap& row_blocks, int max_n, cudaStream_t s) {
-    return launch_pdl(k_raster_rows, row_blocks.n_blocks, kWarpsPerBlock * 32, (size_t)kWarpsPerBlock * max_n * 2, s,
+    return launch_pdl(k_raster_rows, row_blocks.n_blocks, kWarpsPerBlock * 32, kWarpsPerBlock * row_warp_bytes(max_n), s,
                       d_jobs, (const int2*)row_blocks.d_map);
 }
 

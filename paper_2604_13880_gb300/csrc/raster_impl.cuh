@@ -225,125 +225,230 @@ __device__ __forceinline__ void warp_bitonic(unsigned (&k)[KPL], int lane) {
     }
 }
 
-// Paint the span [a, b) of one region into the row copy, only over pixels that
-// are still background; returns how many of this lane's pixels of the span
-// were painted already (a pixel inside two regions).
-__device__ __forceinline__ int paint_span(uint16_t* row, unsigned R, unsigned ka, unsigned kb, int lane) {
-    const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
-    const uint16_t v = (uint16_t)(ka >> 16);
-    int over = 0;
-    for (int i = a + lane; i < b; i += 32) {
-        if (row[i] == (uint16_t)R) row[i] = v;
-        else ++over;
+// Shared-memory bytes one warp of the row rasteriser uses for a row of n
+// pixels: a u32 difference array of n entries and a bit mask of n bits.
+__host__ __device__ constexpr size_t row_warp_bytes(int n) { return (size_t)n * 4 + (size_t)n / 8; }
+
+// Span [a, b) of region v as two events of a difference array: +w at a,
+// -w at b, w = 2^17 + v - R (mod 2^32).  The prefix sum at pixel i is then
+// P = sum over the spans covering i of w, and with Q = R + P:
+//   no span:   Q = R                  (the background label)
+//   one span:  Q = 2^17 + v           (low half v)
+//   c >= 2:    P >= c (2^17 - R) >= 2^17 (R <= 65534), so Q >= 2^17 + R.
+// So the label is the low half of Q, and a pixel is inside two or more spans
+// exactly when P >= 2^17 (no wrap: c < 2^14).  An end at b = n lies past the
+// last pixel and is dropped.
+__device__ __forceinline__ void mark_span(unsigned* diff, unsigned ka, unsigned kb, unsigned n, unsigned R) {
+    const unsigned a = ka & 0xffffu, b = kb & 0xffffu;
+    if (a < b) {
+        const unsigned w = 0x20000u + (ka >> 16) - R;
+        atomicAdd(&diff[a], w);
+        if (b < n) atomicAdd(&diff[b], 0u - w);
+    }
+}
+
+// One round of the striped prefix over a row: pixels [256r, 256r + 256),
+// lane l holding [256r + 8l, 256r + 8l + 8).  Returns the eight inclusive
+// prefixes (from `carry`, the prefix before the round) and advances carry.
+struct Round8 { unsigned p[8]; };
+
+__device__ __forceinline__ Round8 prefix_round(const unsigned* diff, int r, int lane, unsigned& carry) {
+    const uint4* src = reinterpret_cast<const uint4*>(diff) + 64 * r + 2 * lane;
+    const uint4 a = src[0], b = src[1];
+    Round8 t;
+    t.p[0] = a.x;
+    t.p[1] = t.p[0] + a.y;
+    t.p[2] = t.p[1] + a.z;
+    t.p[3] = t.p[2] + a.w;
+    t.p[4] = t.p[3] + b.x;
+    t.p[5] = t.p[4] + b.y;
+    t.p[6] = t.p[5] + b.z;
+    t.p[7] = t.p[6] + b.w;
+    unsigned incl = t.p[7];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    const unsigned base = carry + incl - t.p[7];
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t.p[k] += base;
+    return t;
+}
+
+// Fold-over in this row: the label pass wrote a meaningless label at each
+// pixel inside c >= 2 spans, and the span lengths counted it c times.  Such a
+// pixel takes the smallest covering region id.  Three steps:
+//  (a) a second striped prefix pass marks those pixels in the row bit mask;
+//      each pixel's word of the difference array is read by its owner lane
+//      only, which resets a marked word at once to ~0: the array now holds a
+//      running minimum per marked pixel;
+//  (b) each lane, for each of its own spans, takes the minimum with its
+//      region over the marked pixels the span covers, and gives back one
+//      count per such pixel;
+//  (c) lanes, one 32-pixel word of the mask each, write the resolved labels
+//      and count them once.
+template <int KPL>
+__device__ __forceinline__ void resolve_overlaps_warp(const Job& J, int j, int cnt, const unsigned (&key)[KPL],
+                                                      unsigned* diff, unsigned* bits, int lane) {
+    const int n = J.n;
+    unsigned carry = 0;
+    for (int r = 0; r < (n >> 8); ++r) {
+        const Round8 t = prefix_round(diff, r, lane, carry);
+        unsigned m8 = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m8 |= (t.p[k] >= 0x20000u ? 1u : 0u) << k;
+        const int i0 = 256 * r + 8 * lane;
+        for (unsigned h = m8; h; h &= h - 1u) diff[i0 + __ffs(h) - 1] = 0xffffffffu;
+        // lanes 4q .. 4q+3 make up mask word 8r + q
+        unsigned m = m8 << (8 * (lane & 3));
+        m |= __shfl_xor_sync(0xffffffffu, m, 1);
+        m |= __shfl_xor_sync(0xffffffffu, m, 2);
+        if ((lane & 3) == 0) bits[8 * r + (lane >> 2)] = m;
     }
     __syncwarp();
-    return over;
+    // (b) this lane's spans
+    auto take = [&](unsigned ka, unsigned kb) {
+        const int a = (int)(ka & 0xffffu), b = (int)(kb & 0xffffu);
+        if (a >= b) return;
+        const unsigned v = ka >> 16;
+        int taken = 0;
+        for (int w = a >> 5; w <= ((b - 1) >> 5); ++w) {
+            const int lo = max(a - (w << 5), 0), hi = min(b - (w << 5), 32);
+            const unsigned range = (hi - lo == 32) ? 0xffffffffu : (((1u << (hi - lo)) - 1u) << lo);
+            const unsigned hit = bits[w] & range;
+            taken += __popc(hit);
+            for (unsigned h = hit; h; h &= h - 1u) atomicMin(&diff[(w << 5) + __ffs(h) - 1], v);
+        }
+        if (taken) atomicAdd(&J.counts[v], -taken);
+    };
+    if constexpr (KPL == 1) {
+        const unsigned kb = __shfl_down_sync(0xffffffffu, key[0], 1);
+        if ((lane & 1) == 0 && lane + 1 < cnt) take(key[0], kb);
+    } else {
+#pragma unroll
+        for (int t = 0; t < KPL / 2; ++t)
+            if (lane * KPL + 2 * t + 1 < cnt) take(key[2 * t], key[2 * t + 1]);
+    }
+    __syncwarp();
+    // (c) the resolved labels, counted as runs of equal labels
+    uint16_t* lab = J.labels + (size_t)j * n;
+    unsigned cur = 0xffffffffu;
+    int run = 0;
+    for (int w = lane; w < (n >> 5); w += 32) {
+        for (unsigned h = bits[w]; h; h &= h - 1u) {
+            const int i = (w << 5) + __ffs(h) - 1;
+            const unsigned v = diff[i];
+            lab[i] = (uint16_t)v;
+            if (v != cur) {
+                if (run) atomicAdd(&J.counts[cur], run);
+                cur = v;
+                run = 0;
+            }
+            ++run;
+        }
+    }
+    if (run) atomicAdd(&J.counts[cur], run);
+    if (lane == 0) atomicExch(&J.st->overlap, 1);
 }
 
 // One row: keys sorted by (region, column) give each region's spans as
-// consecutive pairs.  The spans are painted into a shared-memory copy of the
-// row in sorted order, writing only still-background pixels, so a pixel in
-// several regions keeps the smallest id.  Overlap <=> the summed span lengths
-// exceed the painted pixel count.
+// consecutive pairs.  Each lane enters its own spans into the warp's
+// difference array; a striped prefix pass (rounds of 256 pixels, 8 per lane,
+// a warp scan per round) then yields every label, stored as one contiguous
+// 512-byte write per round, and, from the largest prefix, whether any pixel
+// lies in two spans.  The cost does not grow with the number of spans.  Such
+// pixels are then resolved by resolve_overlaps_warp.  Keys are taken striped
+// (lane l holds bucket slots l, l + 32, ...): the sort's input order is free,
+// and s0, s1 are slots lane and 32 + lane, read with the row's count.
 template <int KPL>
-__device__ inline void raster_row_warp(const Job& J, int j, int cnt, uint16_t* row, int lane) {
+__device__ __forceinline__ void raster_row_warp(const Job& J, int j, int cnt, unsigned s0, unsigned s1,
+                                                unsigned* diff, int lane) {
     const int n = J.n;
     const unsigned R = (unsigned)J.n_regions;
     const uint32_t* bucket = J.keys + (size_t)j * kKeyStride;
     unsigned key[KPL];
 #pragma unroll
     for (int e = 0; e < KPL; ++e) {
-        const int idx = lane * KPL + e;
-        key[e] = idx < cnt ? bucket[idx] : 0xffffffffu;
+        const int idx = e * 32 + lane;
+        const unsigned raw = e == 0 ? s0 : (e == 1 ? s1 : (idx < cnt ? bucket[idx] : 0u));
+        key[e] = idx < cnt ? raw : 0xffffffffu;
     }
-    // background fill of the row copy
-    const unsigned bg2 = R | (R << 16);
-    const uint4 bg8 = make_uint4(bg2, bg2, bg2, bg2);
-    for (int i = lane; i < (n >> 3); i += 32) reinterpret_cast<uint4*>(row)[i] = bg8;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = lane; i < (n >> 2); i += 32) reinterpret_cast<uint4*>(diff)[i] = z;
     warp_bitonic<KPL>(key, lane);
     __syncwarp();
-    // paint spans in sorted order, noting pixels that were painted already
-    int my_over = 0;
     if constexpr (KPL == 1) {
-        // pair p is (lane 2p, lane 2p + 1)
-        for (int p = 0; 2 * p + 1 < cnt; ++p)
-            my_over += paint_span(row, R, __shfl_sync(0xffffffffu, key[0], 2 * p),
-                                  __shfl_sync(0xffffffffu, key[0], 2 * p + 1), lane);
+        const unsigned kb = __shfl_down_sync(0xffffffffu, key[0], 1);
+        if ((lane & 1) == 0 && lane + 1 < cnt) mark_span(diff, key[0], kb, (unsigned)n, R);
     } else {
-        const int src_lanes = (cnt + KPL - 1) / KPL;
-        for (int src = 0; src < src_lanes; ++src) {
 #pragma unroll
-            for (int t = 0; t < KPL / 2; ++t) {
-                const unsigned ka = __shfl_sync(0xffffffffu, key[2 * t], src);
-                const unsigned kb = __shfl_sync(0xffffffffu, key[2 * t + 1], src);
-                if (src * KPL + 2 * t + 1 >= cnt) continue;          // padding (warp-uniform)
-                my_over += paint_span(row, R, ka, kb, lane);
+        for (int t = 0; t < KPL / 2; ++t)
+            if (lane * KPL + 2 * t + 1 < cnt) mark_span(diff, key[2 * t], key[2 * t + 1], (unsigned)n, R);
+    }
+    __syncwarp();
+    // Q = R + P: labels are its low halves (byte-permute packs two), and the
+    // largest Q tells whether a pixel lies in two or more spans
+    unsigned carry = R, qmax = 0;
+    uint4* dst = reinterpret_cast<uint4*>(J.labels + (size_t)j * n) + lane;
+#pragma unroll 2
+    for (int r = 0; r < (n >> 8); ++r) {
+        const Round8 q = prefix_round(diff, r, lane, carry);
+        qmax = max(qmax, max(max(max(q.p[0], q.p[1]), max(q.p[2], q.p[3])),
+                             max(max(q.p[4], q.p[5]), max(q.p[6], q.p[7]))));
+        dst[32 * r] = make_uint4(__byte_perm(q.p[0], q.p[1], 0x5410), __byte_perm(q.p[2], q.p[3], 0x5410),
+                                 __byte_perm(q.p[4], q.p[5], 0x5410), __byte_perm(q.p[6], q.p[7], 0x5410));
+    }
+    const bool over = qmax >= 0x20000u + R;
+    // counts from the spans held by this lane
+    if constexpr (KPL == 1) {
+        const unsigned kb = __shfl_down_sync(0xffffffffu, key[0], 1);
+        if ((lane & 1) == 0 && lane + 1 < cnt) {
+            const int a = (int)(key[0] & 0xffffu), b = (int)(kb & 0xffffu);
+            if (a < b) atomicAdd(&J.counts[key[0] >> 16], b - a);
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < KPL / 2; ++t) {
+            const int idx = lane * KPL + 2 * t;
+            if (idx + 1 < cnt) {
+                const int a = (int)(key[2 * t] & 0xffffu), b = (int)(key[2 * t + 1] & 0xffffu);
+                if (a < b) atomicAdd(&J.counts[key[2 * t] >> 16], b - a);
             }
         }
     }
-    if (!__any_sync(0xffffffffu, my_over != 0)) {
-        // no overlap: counts from the spans held by this lane
-        if constexpr (KPL == 1) {
-            const unsigned kb = __shfl_down_sync(0xffffffffu, key[0], 1);
-            if ((lane & 1) == 0 && lane + 1 < cnt) {
-                const int a = (int)(key[0] & 0xffffu), b = (int)(kb & 0xffffu);
-                if (a < b) atomicAdd(&J.counts[key[0] >> 16], b - a);
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < KPL / 2; ++t) {
-                const int idx = lane * KPL + 2 * t;
-                if (idx + 1 < cnt) {
-                    const int a = (int)(key[2 * t] & 0xffffu), b = (int)(key[2 * t + 1] & 0xffffu);
-                    if (a < b) atomicAdd(&J.counts[key[2 * t] >> 16], b - a);
-                }
-            }
-        }
-    } else {
-        // fold-over in this row: counts from the resolved labels, as run
-        // lengths over each lane's n/32 contiguous pixels (one atomic per run
-        // instead of one per pixel on a few hot counters)
-        const int per = n >> 5;
-        const int p0 = lane * per;
-        unsigned cur = row[p0];
-        int run = 0;
-        for (int i = p0; i < p0 + per; ++i) {
-            const unsigned l = row[i];
-            if (l != cur) {
-                if (cur != R) atomicAdd(&J.counts[cur], run);
-                cur = l;
-                run = 0;
-            }
-            ++run;
-        }
-        if (cur != R) atomicAdd(&J.counts[cur], run);
-        if (lane == 0) atomicExch(&J.st->overlap, 1);
+    if (__any_sync(0xffffffffu, over)) {
+        __syncwarp();
+        resolve_overlaps_warp<KPL>(J, j, cnt, key, diff, diff + n, lane);
     }
-    // write the row
-    uint4* dst = reinterpret_cast<uint4*>(J.labels + (size_t)j * n);
-    const uint4* srcv = reinterpret_cast<const uint4*>(row);
-    for (int i = lane; i < (n >> 3); i += 32) dst[i] = srcv[i];
     if (lane == 0) J.row_cnt[j] = 0;     // ready for the next iteration
 }
 
 // rows [first_row, first_row + 8) of one job, one warp each; rows_smem holds
-// 8 * N u16 (the row copies)
-__device__ __forceinline__ void raster_rows_item(const Job& J, int first_row, uint16_t* rows_smem) {
+// 8 * row_warp_bytes(N) bytes.  With check_active the job's active flag is
+// read together with the row's count and first key slots (one round trip).
+__device__ __forceinline__ void raster_rows_item(const Job& J, int first_row, unsigned* rows_smem,
+                                                 bool check_active = false) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = first_row + warp;
     if (warp >= kWarpsPerBlock || j >= J.n) return;
-    uint16_t* row = rows_smem + (size_t)warp * J.n;
+    unsigned* diff = rows_smem + (size_t)warp * (row_warp_bytes(J.n) / 4);
+    const uint32_t* bucket = J.keys + (size_t)j * kKeyStride;
+    const int act = check_active ? J.st->active : 1;
     const int cnt = J.row_cnt[j];
+    const unsigned s0 = bucket[lane], s1 = bucket[32 + lane];     // slots past cnt are ignored
     __syncwarp();                                    // every lane has the count before lane 0 resets it
+    if (!act) return;
     if (cnt > kKeyStride) {                          // bucket overflow
         if (lane == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
         return;
     }
-    if (cnt <= 32) raster_row_warp<1>(J, j, cnt, row, lane);
-    else if (cnt <= 2 * 32) raster_row_warp<2>(J, j, cnt, row, lane);
-    else if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, row, lane);
-    else if (cnt <= 8 * 32) raster_row_warp<8>(J, j, cnt, row, lane);
-    else if (lane == 0) {                            // big row: handled by k_raster_big
+    if (cnt <= 32) raster_row_warp<1>(J, j, cnt, s0, s1, diff, lane);
+    else if (cnt <= 2 * 32) raster_row_warp<2>(J, j, cnt, s0, s1, diff, lane);
+    else if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, s0, s1, diff, lane);
+    else if (cnt <= 8 * 32) raster_row_warp<8>(J, j, cnt, s0, s1, diff, lane);
+    else if (lane == 0) {                            // big row: finished by the density-table kernel
         const int q = atomicAdd(&J.st->n_big, 1);
         J.big_rows[q] = j;
     }

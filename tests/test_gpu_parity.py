@@ -64,6 +64,27 @@ def _raster_cases():
     inner = [(0.3, 0.3), (0.3, 0.7), (0.7, 0.7), (0.7, 0.3)]
     yield "hole", synth.Mesh(np.array(outer + inner, np.float64), np.array([0, 4, 8], np.int32),
                              np.arange(8, dtype=np.int32), np.array([0, 0], np.int32), 1), 8
+    # fold-overs: vertex noise of about a tenth of a cell makes neighbouring
+    # regions overlap in many rows (pixels inside two or three spans, in every
+    # crossing-count class and, at 2048 and 4096, in several 32-pixel windows
+    # of one lane)
+    for nm, (R, V, seed, k, sd) in {"foldover60_256": (60, 3000, 21, 8, 0.006),
+                                    "foldover200_1024": (200, 20_000, 22, 10, 0.002),
+                                    "foldover200_1024_big": (200, 50_000, 22, 10, 0.004),
+                                    "foldover400_2048": (400, 40_000, 23, 11, 0.0008),
+                                    "foldover300_4096": (300, 20_000, 24, 12, 0.0005)}.items():
+        m = synth.voronoi_map(R, V, seed=seed, jitter=0.3)
+        noise = np.random.default_rng(seed + 100).normal(0.0, sd, m.verts.shape)
+        yield nm, m.with_verts(np.clip(m.verts + noise, 0.0, 1.0)), k
+    # stacked rectangles: up to ~250 crossings per row (the widest warp
+    # class), then more than 256 (the block-per-row path), most pixels inside
+    # several rectangles
+    for nm, (nr, h0, h1, k) in {"stacked_rects_2048": (200, 0.2, 0.5, 11),
+                                "stacked_rects_big_1024": (400, 0.3, 0.6, 10)}.items():
+        rng = np.random.default_rng(25 + k)
+        lo = rng.uniform(0.0, 0.45, (nr, 2))
+        hi = lo + np.stack([rng.uniform(0.02, 0.5, nr), rng.uniform(h0, h1, nr)], 1)
+        yield nm, synth.square_map([(a, b, c, d) for (a, b), (c, d) in zip(lo, hi)]), k
 
 
 @pytest.mark.parametrize("name,mesh,k", list(_raster_cases()), ids=lambda x: x if isinstance(x, str) else "")
