@@ -20,10 +20,11 @@ namespace {
 __global__ void __launch_bounds__(256) k_areas_errors(const Job* __restrict__ jobs, const int2* __restrict__ bmap,
                                                       int update_state) {
     const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
+    const Job J = jobs[m.x];                  // fixed over a run: read before the wait
+    const AreaPre pre = areas_prefetch(J, m.y);
     pdl_wait_and_release();
     if (!J.st->active) return;
-    areas_item(J, m.y, update_state);
+    areas_body(J, m.y, update_state, pre);
 }
 
 }  // namespace

@@ -88,34 +88,62 @@ __device__ __forceinline__ void shoelace_add(float& hi, float& lo, float2 p, flo
     hi = s;
 }
 
-// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only.
+// The mesh part of one warp's work, fixed over a run and so read before the
+// programmatic-launch wait: the region, the lane's first edge, the region's
+// end and the lane's first four edges.
+struct AreaPre {
+    int v, wr, e, e1;
+    int2 ab[4];
+};
+
 // A block (8 warps) holds 8 >> lw regions, 1 << lw warps each; a warp's lanes
-// take every (32 << lw)-th edge of the region, four edges' loads in flight.
-__device__ inline void areas_item(const Job& J, int item, int update_state) {
+// take every (32 << lw)-th edge of the region.
+__device__ __forceinline__ AreaPre areas_prefetch(const Job& J, int item) {
+    AreaPre a;
+    const int lw = area_warps_log2(J.n_edges, J.n_regions);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int stride = 32 << lw;
+    a.v = item * (kRegionsPerBlock >> lw) + (warp >> lw);
+    a.wr = warp & ((1 << lw) - 1);
+    a.e = 0;
+    a.e1 = 0;
+    if (a.v < J.n_regions) {
+        a.e1 = J.reg_edge_off[a.v + 1];
+        a.e = J.reg_edge_off[a.v] + a.wr * 32 + lane;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        a.ab[u] = (a.e + u * stride < a.e1) ? __ldg(J.edges + a.e + u * stride) : make_int2(0, 0);
+    return a;
+}
+
+// update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only.
+// Edges go in groups of four, in order; the next group's edges are loaded
+// while the current group's vertices are in flight.
+__device__ inline void areas_body(const Job& J, int item, int update_state, const AreaPre& pre) {
     __shared__ double wpart[kRegionsPerBlock];
     const int lw = area_warps_log2(J.n_edges, J.n_regions);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int v = item * (kRegionsPerBlock >> lw) + (warp >> lw);
-    const int wr = warp & ((1 << lw) - 1);
+    const int v = pre.v, wr = pre.wr;
     double acc = 0.0;
     if (v < J.n_regions) {
         float hi = 0.0f, lo = 0.0f;
-        const int e1 = J.reg_edge_off[v + 1];
+        const int e1 = pre.e1;
         const int stride = 32 << lw;
-        int e = J.reg_edge_off[v] + wr * 32 + lane;
-        for (; e + 3 * stride < e1; e += 4 * stride) {
-            int2 ab[4];
+        int2 ab[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ab[u] = pre.ab[u];
+        for (int e = pre.e; e < e1; e += 4 * stride) {
             float2 p[4], q[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) ab[u] = __ldg(J.edges + e + u * stride);
+            for (int u = 0; u < 4; ++u)
+                if (e + u * stride < e1) { p[u] = J.xy[ab[u].x]; q[u] = J.xy[ab[u].y]; }
+            const int en = e + 4 * stride;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) { p[u] = J.xy[ab[u].x]; q[u] = J.xy[ab[u].y]; }
+            for (int u = 0; u < 4; ++u) ab[u] = (en + u * stride < e1) ? __ldg(J.edges + en + u * stride) : ab[u];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) shoelace_add(hi, lo, p[u], q[u]);
-        }
-        for (; e < e1; e += stride) {
-            const int2 ab = __ldg(J.edges + e);
-            shoelace_add(hi, lo, J.xy[ab.x], J.xy[ab.y]);
+            for (int u = 0; u < 4; ++u)
+                if (e + u * stride < e1) shoelace_add(hi, lo, p[u], q[u]);
         }
         acc = (double)hi + (double)lo;
 #pragma unroll
@@ -144,6 +172,10 @@ __device__ inline void areas_item(const Job& J, int item, int update_state) {
     if (!last) return;
     __threadfence();
     errors_and_stop(J, update_state);
+}
+
+__device__ __forceinline__ void areas_item(const Job& J, int item, int update_state) {
+    areas_body(J, item, update_state, areas_prefetch(J, item));
 }
 
 }  // namespace inim

@@ -20,10 +20,16 @@ template <class Acc>
 __global__ void __launch_bounds__(256) k_gather_move(const Job* __restrict__ jobs,
                                                      const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
+    const Job J = jobs[m.x];                  // fixed over a run: read before the wait
+    const int v = m.y * blockDim.x + threadIdx.x;
     pdl_wait_and_release();
-    if (!J.st->active) return;
-    gather_vertex<Acc>(J, m.y * blockDim.x + threadIdx.x);
+    if (v >= J.n_verts) return;
+    // the active flag, the vertex and C in one round trip
+    const int act = J.st->active;
+    const float2 p = J.xy[v];
+    const typename Acc::T C = grand_total<Acc>(J);
+    if (!act) return;
+    move_vertex<Acc>(J, v, p, C);
 }
 
 template <class Acc>

@@ -94,12 +94,17 @@ __device__ __forceinline__ float2 delta_at_pixel(const Ratios& r, const Ratios& 
     return make_float2(tx, ty);
 }
 
+// C = the grand total (the last element of S)
 template <class Acc>
-__device__ __forceinline__ float2 displacement_at(const Job& J, float2 p) {
+__device__ __forceinline__ typename Acc::T grand_total(const Job& J) {
     using T = typename Acc::T;
+    const size_t last = (size_t)J.n * J.n - 1;
+    return J.ST ? reinterpret_cast<const T*>(J.ST)[2 * last] : reinterpret_cast<const T*>(J.S)[last];
+}
+
+template <class Acc>
+__device__ __forceinline__ float2 displacement_at_c(const Job& J, float2 p, typename Acc::T C) {
     const int n = J.n;
-    const T C = J.ST ? reinterpret_cast<const T*>(J.ST)[2 * ((size_t)n * n - 1)]
-                     : reinterpret_cast<const T*>(J.S)[(size_t)n * n - 1];
     const double inv_c = Acc::inv(C);
     const float inv_n = 1.0f / (float)n;
     const float inv_c0 = ldexpf(1.0f, -2 * J.log2n);
@@ -122,13 +127,23 @@ __device__ __forceinline__ float2 displacement_at(const Job& J, float2 p) {
 }
 
 template <class Acc>
-__device__ __forceinline__ void gather_vertex(const Job& J, int v) {
-    if (v >= J.n_verts) return;
-    float2 p = J.xy[v];
-    const float2 dlt = displacement_at<Acc>(J, p);
+__device__ __forceinline__ float2 displacement_at(const Job& J, float2 p) {
+    return displacement_at_c<Acc>(J, p, grand_total<Acc>(J));
+}
+
+// the blend of Sec. 4.1 step 6 and the move, from the vertex p and C loaded
+template <class Acc>
+__device__ __forceinline__ void move_vertex(const Job& J, int v, float2 p, typename Acc::T C) {
+    const float2 dlt = displacement_at_c<Acc>(J, p, C);
     p.x += J.lam * dlt.x;
     p.y += J.lam * dlt.y;
     J.xy[v] = p;
+}
+
+template <class Acc>
+__device__ __forceinline__ void gather_vertex(const Job& J, int v) {
+    if (v >= J.n_verts) return;
+    move_vertex<Acc>(J, v, J.xy[v], grand_total<Acc>(J));
 }
 
 }  // namespace inim

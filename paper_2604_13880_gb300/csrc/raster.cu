@@ -43,11 +43,26 @@ __global__ void __launch_bounds__(256) k_raster_reset(const Job* __restrict__ jo
 // its pixel counts and big-row list.
 __global__ void __launch_bounds__(256) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
-    pdl_wait_and_release();
-    if (!J.st->active) return;
+    const Job J = jobs[m.x];
+    // the job's fields and the mesh (edges, regions) are fixed over a run:
+    // read them before the wait; the vertex positions and the active flag after
     const int e = m.y * blockDim.x + threadIdx.x;
-    emit_crossings_warp(J, e, e < J.n_edges);
+    const bool valid = e < J.n_edges;
+    int2 ab = make_int2(0, 0);
+    unsigned reg = 0;
+    if (valid) {
+        ab = J.edges[e];
+        reg = (unsigned)J.edge_region[e];
+    }
+    pdl_wait_and_release();
+    const int act = J.st->active;
+    float2 p = make_float2(0.0f, 0.0f), q = p;
+    if (valid) {
+        p = J.xy[ab.x];
+        q = J.xy[ab.y];
+    }
+    if (!act) return;
+    emit_crossings_pts(J, valid, reg, p, q);
     if (m.y == 0) reset_raster_block(J);
 }
 
@@ -60,11 +75,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_raster_rows(const Jo
     raster_rows_item(J, m.y, rows_smem, true);
 }
 
-__global__ void __launch_bounds__(kRowThreads) k_density_table(const Job* __restrict__ jobs) {
+__global__ void __launch_bounds__(kRowThreads, 1) k_density_table(const Job* __restrict__ jobs) {
     __shared__ RowShared rsh;
     __shared__ double ss[32];
     __shared__ long long so[32];
-    const Job& J = jobs[blockIdx.x];
+    const Job J = jobs[blockIdx.x];           // fixed over a run: read before the wait
     pdl_wait_and_release();
     if (!J.st->active) return;
     density_table_body(J, rsh, ss, so);

@@ -62,17 +62,15 @@ __device__ __forceinline__ int clamped_ceil_div(long long num, long long den, in
 // (found by a binary search over the lanes' prefixes), which supplies the
 // edge through shuffles.  The warp's serial work is total / 32 crossings
 // instead of the longest edge's row count.
-__device__ __forceinline__ void emit_crossings_warp(const Job& J, int e, bool valid) {
+//
+// emit_crossings_pts takes the edge's region and end points already loaded
+// (valid == false: no edge); emit_crossings_warp loads them.
+__device__ __forceinline__ void emit_crossings_pts(const Job& J, bool valid, unsigned reg, float2 p, float2 q) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     EdgeFix f{};
-    unsigned reg = 0;
     int cnt = 0;
-    if (valid) {
-        const int2 ab = J.edges[e];
-        reg = (unsigned)J.edge_region[e];
-        if (edge_rows_pts(J, J.xy[ab.x], J.xy[ab.y], f)) cnt = f.jhi - f.jlo + 1;
-    }
+    if (valid && edge_rows_pts(J, p, q, f)) cnt = f.jhi - f.jlo + 1;
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -103,6 +101,18 @@ __device__ __forceinline__ void emit_crossings_warp(const Job& J, int e, bool va
             if (slot < kKeyStride) J.keys[(size_t)j * kKeyStride + slot] = (r << 16) | (unsigned)c;
         }
     }
+}
+
+__device__ __forceinline__ void emit_crossings_warp(const Job& J, int e, bool valid) {
+    unsigned reg = 0;
+    float2 p = make_float2(0.0f, 0.0f), q = p;
+    if (valid) {
+        const int2 ab = J.edges[e];
+        reg = (unsigned)J.edge_region[e];
+        p = J.xy[ab.x];
+        q = J.xy[ab.y];
+    }
+    emit_crossings_pts(J, valid, reg, p, q);
 }
 
 // Per job, while the keys of an iteration are being emitted (one block):

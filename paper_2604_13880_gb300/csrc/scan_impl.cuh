@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
     __shared__ uint64_t bars[kLabelDepth];
     extern __shared__ __align__(128) unsigned char scan_ring[];     // [kLabelDepth][CPT * NT] u16
     const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
+    const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_wait_and_release();
     if (!J.st->active) return;
     LabelRing<kLabelDepth> ring{reinterpret_cast<uint16_t*>(scan_ring), bars};
@@ -533,7 +533,7 @@ template <class Acc>
 __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs,
                                                     const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
+    const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_wait_and_release();
     if (!J.st->active) return;
     scan_carry_body<Acc>(J, m.y * blockDim.x + threadIdx.x);
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     using T = typename Acc::T;
     __shared__ T tot[kCarryGroups][32];
     const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
+    const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_wait_and_release();
     if (!J.st->active) return;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kPbThreads) k_scan_band_pb(const Job* __restri
     __shared__ uint64_t bars[H];
 
     const int2 m = bmap[blockIdx.x];
-    const Job& J = jobs[m.x];
+    const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_wait_and_release();
     if (!J.st->active) return;
     const int band = m.y, nb = J.nb, j0 = band * H;
