@@ -482,47 +482,69 @@ __host__ __device__ __forceinline__ int carry_qspace(int n, int nb, int H) {
     return n + 2 * (n + (nb - 1) * H);
 }
 
+// One thread's carry chain (kind, q) as a walk over the bands: the term of
+// band b sits at column xp = x0 + b dx of the band's aggregate row, index
+// x0 + b (N + dx) in the kind's block (zero outside [0, N), except for kind
+// 1 past the right edge, where it is the band's row total S(N-1) in the
+// kind-0 block); the carry of band b goes to column q + b dx, index
+// q + b (N + dx) of the kind's carry block.  dx = 0, -H, +H and
+// x0 = q + dx for kinds 0, 1, 2.
+template <class Acc>
+struct CarryChain {
+    using T = typename Acc::T;
+    const T* agg;
+    T* c;
+    int n, kind, q, x0, dx, base;
+    __device__ __forceinline__ CarryChain(const Job& J, int kind_, int q_)
+        : n(J.n), kind(kind_), q(q_) {
+        base = (kind < 0 ? 0 : kind) * J.nb * n;
+        agg = reinterpret_cast<const T*>(J.agg);
+        c = reinterpret_cast<T*>(J.carry) + base;
+        dx = kind == 1 ? -J.H : (kind == 2 ? J.H : 0);
+        x0 = q + dx;
+    }
+    // offset of band b's term in the aggregates, -1 for a zero term
+    __device__ __forceinline__ int term_off(int b) const {
+        const int xp = x0 + b * dx;
+        if ((unsigned)xp < (unsigned)n) return base + x0 + b * (n + dx);
+        if (kind == 1 && xp >= n) return b * n + n - 1;
+        return -1;
+    }
+    __device__ __forceinline__ T term(int b) const {
+        const int o = term_off(b);
+        return o >= 0 ? agg[o] : Acc::zero();
+    }
+    __device__ __forceinline__ void store(int b, T v) const {
+        const int x = q + b * dx;
+        if ((unsigned)x < (unsigned)n) c[q + b * (n + dx)] = v;
+    }
+};
+
+// q in [0, N + 2 span) -> (kind, q within the kind); kind -1 past the end
+__device__ __forceinline__ int carry_kind(int& q, int n, int nb, int H) {
+    const int span = n + (nb - 1) * H;
+    if (q < n) return 0;
+    if ((q -= n) < span) return 1;
+    if ((q -= span) < span) { q -= (nb - 1) * H; return 2; }
+    return -1;
+}
+
 template <class Acc>
 __device__ inline void scan_carry_body(const Job& J, int q) {
     using T = typename Acc::T;
-    const int n = J.n, H = J.H, nb = J.nb;
-    const int span = n + (nb - 1) * H;
-    int kind;
-    if (q < n) kind = 0;
-    else if ((q -= n) < span) kind = 1;
-    else if ((q -= span) < span) { kind = 2; q -= (nb - 1) * H; }
-    else return;
-    const T* agg = reinterpret_cast<const T*>(J.agg);
-    const T* a = agg + (size_t)kind * nb * n;
-    const T* aS = agg;
-    T* c = reinterpret_cast<T*>(J.carry) + (size_t)kind * nb * n;
+    const int nb = J.nb;
+    const int kind = carry_kind(q, J.n, nb, J.H);
+    if (kind < 0) return;
+    const CarryChain<Acc> ch(J, kind, q);
     T acc = Acc::zero();
     for (int b0 = 0; b0 < nb; b0 += kCarryU) {
         T v[kCarryU];
 #pragma unroll
-        for (int u = 0; u < kCarryU; ++u) {
-            const int b = b0 + u;
-            T g = Acc::zero();
-            if (b < nb) {
-                if (kind == 0) {
-                    g = a[(size_t)b * n + q];
-                } else if (kind == 1) {
-                    const int xp = q - (b + 1) * H;
-                    if (xp >= n) g = aS[(size_t)b * n + (n - 1)];
-                    else if (xp >= 0) g = a[(size_t)b * n + xp];
-                } else {
-                    const int xp = q + (b + 1) * H;
-                    if (xp >= 0 && xp < n) g = a[(size_t)b * n + xp];
-                }
-            }
-            v[u] = g;
-        }
+        for (int u = 0; u < kCarryU; ++u) v[u] = (b0 + u < nb) ? ch.term(b0 + u) : Acc::zero();
 #pragma unroll
         for (int u = 0; u < kCarryU; ++u) {
-            const int b = b0 + u;
-            if (b < nb) {
-                const int x = kind == 0 ? q : (kind == 1 ? q - b * H : q + b * H);
-                if (x >= 0 && x < n) c[(size_t)b * n + x] = acc;
+            if (b0 + u < nb) {
+                ch.store(b0 + u, acc);
                 acc = Acc::add(acc, v[u]);
             }
         }
@@ -543,9 +565,11 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
 // 32 consecutive q (the lanes, so loads and stores stay coalesced) times 8
 // groups of consecutive bands (the warps).  Each thread sums the terms of its
 // group's bands, the 8 group totals are scanned in shared memory, and each
-// thread then writes the exclusive prefixes of its own bands.  The same sums
+// thread then reads its terms again and writes the exclusive prefixes of its
+// own bands.  The same sums
 // as the serial walk, associated by group, with 1/8 of its dependent chain.
 constexpr int kCarryGroups = 8;
+constexpr int kCarryUG = 8;               // loads in flight per thread in the grouped form
 
 // q values per carry block: the grouped form pays off for a small
 // (latency-bound) batch once there are many bands (its dependent chain is
@@ -553,20 +577,6 @@ constexpr int kCarryGroups = 8;
 // serial walk, which moves fewer blocks.
 __host__ __device__ inline int carry_q_per_block(int nb, int size_class) {
     return (size_class == 0 && nb >= 32) ? 32 : 256;
-}
-
-template <class Acc>
-__device__ __forceinline__ typename Acc::T carry_term(const Job& J, const typename Acc::T* a, int kind, int q,
-                                                      int b) {
-    const int n = J.n, H = J.H;
-    if (kind == 0) return a[(size_t)b * n + q];
-    if (kind == 1) {
-        const int xp = q - (b + 1) * H;
-        if (xp >= n) return reinterpret_cast<const typename Acc::T*>(J.agg)[(size_t)b * n + (n - 1)];
-        return xp >= 0 ? a[(size_t)b * n + xp] : Acc::zero();
-    }
-    const int xp = q + (b + 1) * H;
-    return (xp >= 0 && xp < n) ? a[(size_t)b * n + xp] : Acc::zero();
 }
 
 template <class Acc>
@@ -579,25 +589,20 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     pdl_wait_and_release();
     if (!J.st->active) return;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int n = J.n, H = J.H, nb = J.nb;
-    const int span = n + (nb - 1) * H;
+    const int nb = J.nb;
     int q = m.y * 32 + lane;
-    int kind = -1;
-    if (q < n) kind = 0;
-    else if ((q -= n) < span) kind = 1;
-    else if ((q -= span) < span) { kind = 2; q -= (nb - 1) * H; }
-    const T* a = reinterpret_cast<const T*>(J.agg) + (size_t)(kind < 0 ? 0 : kind) * nb * n;
-    T* c = reinterpret_cast<T*>(J.carry) + (size_t)(kind < 0 ? 0 : kind) * nb * n;
+    const int kind = carry_kind(q, J.n, nb, J.H);
+    const CarryChain<Acc> ch(J, kind, q);
     const int cb = (nb + kCarryGroups - 1) / kCarryGroups;
     const int b_lo = min(nb, g * cb), b_hi = min(nb, b_lo + cb);
-    T v[kCarryU];
     T s = Acc::zero();
     if (kind >= 0) {
-        for (int b0 = b_lo; b0 < b_hi; b0 += kCarryU) {
+        for (int b0 = b_lo; b0 < b_hi; b0 += kCarryUG) {
+            T v[kCarryUG];
 #pragma unroll
-            for (int u = 0; u < kCarryU; ++u) v[u] = (b0 + u < b_hi) ? carry_term<Acc>(J, a, kind, q, b0 + u) : Acc::zero();
+            for (int u = 0; u < kCarryUG; ++u) v[u] = (b0 + u < b_hi) ? ch.term(b0 + u) : Acc::zero();
 #pragma unroll
-            for (int u = 0; u < kCarryU; ++u) if (b0 + u < b_hi) s = Acc::add(s, v[u]);
+            for (int u = 0; u < kCarryUG; ++u) if (b0 + u < b_hi) s = Acc::add(s, v[u]);
         }
     }
     tot[g][lane] = s;
@@ -605,18 +610,15 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     if (kind < 0) return;
     T acc = Acc::zero();
     for (int k = 0; k < g; ++k) acc = Acc::add(acc, tot[k][lane]);
-    const bool held = (b_hi - b_lo) <= kCarryU;      // the terms are still in v
-    for (int b0 = b_lo; b0 < b_hi; b0 += kCarryU) {
-        if (!held) {
+    // the terms again (this thread's own loads: L1 hits), now with their carries
+    for (int b0 = b_lo; b0 < b_hi; b0 += kCarryUG) {
+        T v[kCarryUG];
 #pragma unroll
-            for (int u = 0; u < kCarryU; ++u) v[u] = (b0 + u < b_hi) ? carry_term<Acc>(J, a, kind, q, b0 + u) : Acc::zero();
-        }
+        for (int u = 0; u < kCarryUG; ++u) v[u] = (b0 + u < b_hi) ? ch.term(b0 + u) : Acc::zero();
 #pragma unroll
-        for (int u = 0; u < kCarryU; ++u) {
-            const int b = b0 + u;
-            if (b < b_hi) {
-                const int x = kind == 0 ? q : (kind == 1 ? q - b * H : q + b * H);
-                if (x >= 0 && x < n) c[(size_t)b * n + x] = acc;
+        for (int u = 0; u < kCarryUG; ++u) {
+            if (b0 + u < b_hi) {
+                ch.store(b0 + u, acc);
                 acc = Acc::add(acc, v[u]);
             }
         }

@@ -40,7 +40,7 @@ struct PbLayout {
 };
 
 template <class Acc, int N, int H, int PHASE>
-__global__ void __launch_bounds__(kPbThreads) k_scan_band_pb(const Job* __restrict__ jobs,
+__global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(const Job* __restrict__ jobs,
                                                              const int2* __restrict__ bmap,
                                                              const float* __restrict__ dtex) {
     using T = typename Acc::T;
