@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_raster_reset(const Job* __restrict__ jo
 // The crossing keys of the current vertex positions, one lane per edge, the
 // crossings spread over each warp; the first edge block of a job also clears
 // its pixel counts and big-row list.
-__global__ void __launch_bounds__(256) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
+__global__ void __launch_bounds__(256, 8) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];
     // the job's fields and the mesh (edges, regions) are fixed over a run:
