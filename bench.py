@@ -469,7 +469,9 @@ def main():
         dd = max(stages_d, key=stages_d.get)
         line["roofline_direct72"] = roofline(batches, "direct72", dd, pk)
         line["stages_ms"] = stages_d
-        line["stages_gbs"] = {st: batches["direct72"]["algo"][st] / (stages_d[st] / 1e3) / 1e9 for st in stages_d}
+        # (a stage timed 0 is not in the iteration: the density table built by scan phase 1)
+        line["stages_gbs"] = {st: batches["direct72"]["algo"][st] / (stages_d[st] / 1e3) / 1e9
+                              for st in stages_d if stages_d[st] > 0}
         line["stages_3solve_ms"] = stages_c
         line["stage_ms_per_step"] = {f"{bn}:{sn}": round(b["stages"][sn] * b["per_step"], 3)
                                      for bn, b in batches.items() for sn in b["stages"]}

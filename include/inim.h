@@ -363,8 +363,11 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps);
  * library's stream (ms[i] = elapsed / reps).  Stages, in iteration order:
  * crossings, raster_rows, density_table, scan_phase1, scan_carry,
  * scan_phase3, gather_move, areas_errors (names from inim_stage_name); the
- * two raster kernels run as pairs, each timed between its own events.  The
- * batch's vertices move while it runs; the next run resets them.  ms must
+ * two raster kernels run as pairs, each timed between its own events.  For
+ * batches whose maps have at most 2047 regions the density table is built by
+ * scan_phase1 (there is no density_table kernel in the iteration) and
+ * ms[2] = 0.  The batch's vertices move while it runs; the next run resets
+ * them.  ms must
  * hold >= 8 floats; *n_stages receives 8.  INIM_E_STATE if no map batch ran
  * yet.
  */

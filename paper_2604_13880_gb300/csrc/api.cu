@@ -200,6 +200,7 @@ struct Batch {
     std::vector<Group> groups;
     int precision = INIM_FP32;
     int max_n = 0;
+    bool fuse_table = false;            // the scan builds the density table (no density kernel)
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -369,6 +370,12 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
         g.carry.q_per_block = carry_q_per_block(((1 << l) + g.tile.H - 1) / g.tile.H, size_class(group_px[l]));
         B.groups.push_back(g);
     }
+    // map jobs with small region tables: the scan's first phase builds the
+    // density table (and the iteration state), the density kernel is left out
+    B.fuse_table = true;
+    for (int k = 0; k < nj; ++k)
+        if (!spec[k].map || B.h_jobs[k].n_regions + 1 > kFusedTableMax) B.fuse_table = false;
+    for (auto& J : B.h_jobs) J.fuse_table = B.fuse_table ? 1 : 0;
     CUDA_TRY(cudaMemcpy(B.d_jobs, B.h_jobs.data(), nj * sizeof(Job), cudaMemcpyHostToDevice));
     return INIM_OK;
 }
@@ -456,7 +463,7 @@ cudaError_t enqueue_prologue(Batch& B, cudaStream_t s) {
 // after the next iteration's raster started.
 cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s, bool overlap = false, bool first = true) {
     cudaError_t e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, s);
-    if (e == cudaSuccess) e = launch_density_table(B.d_jobs, (int)B.spec.size(), s);
+    if (e == cudaSuccess && !B.fuse_table) e = launch_density_table(B.d_jobs, (int)B.spec.size(), s);
     for (auto& g : B.groups) {
         if (e != cudaSuccess) break;
         if (B.precision == INIM_FIX64) e = launch_scan_fix64(B.d_jobs, g.band, g.carry, g.tile, nullptr, s);
@@ -494,7 +501,7 @@ namespace {
 
 int kernels_per_fused_iteration(const Batch& B) {
     int k = 1 + (B.edge_blocks.n_blocks ? 1 : 0);          // crossing keys, rows
-    k += 1;                                                  // density table (+ big rows)
+    k += B.fuse_table ? 0 : 1;                               // density table (else built by the scan)
     k += 3 * (int)B.groups.size();                           // scan phases 1-3
     k += B.vert_blocks.n_blocks ? 1 : 0;                     // gather / move
     k += B.region_blocks.n_blocks ? 1 : 0;                   // areas + errors + stop rule
@@ -1592,6 +1599,7 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
         ms[1] = tr / (float)reps;
     }
     for (int i = 2; i < kNumStages && rc == INIM_OK; ++i) {
+        if (i == 2 && B.fuse_table) { ms[i] = 0.0f; continue; }     // built by the scan's first phase
         cudaError_t e = stage(i);                       // warm
         if (e == cudaSuccess) e = cudaEventRecord(e0, B.stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = stage(i);

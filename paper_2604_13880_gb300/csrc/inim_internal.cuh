@@ -12,6 +12,7 @@ namespace inim {
 
 constexpr int kSubBits = 8;          // sub-pixel bits of the fixed-point raster
 constexpr int kMaxLog2 = 12;         // N <= 4096
+constexpr int kFusedTableMax = 2048; // density table built in the scan when n_regions + 1 <= this
 constexpr int kMinLog2 = 8;          // N >= 256
 constexpr int kKeyStride = 2048;     // crossing keys one texture row can hold (fixed-stride buckets)
 
@@ -65,6 +66,7 @@ struct Job {
     float lam;                 // blend weight = 1 - shape
     float bdv_scale;
     int   precision;           // INIM_FP32 / INIM_FIX64 / INIM_KAHAN
+    int   fuse_table;          // 1: the scan's first phase builds the density table (no density kernel)
     // raster workspace
     uint16_t* labels;          // [n*n]
     int*      row_cnt;         // [n] crossing keys in each row's bucket (reset by the row rasteriser)

@@ -20,9 +20,6 @@ namespace inim {
 namespace {
 
 constexpr int kPersistThreads = 256;
-// the density phase keeps its reduction arrays right after the row scratch,
-// at a 16-byte aligned offset (sizeof(RowShared) is not a multiple of 8)
-static_assert(kRowSharedPadded % 16 == 0, "aligned reduction arrays");
 constexpr long long kSpinCap = 1LL << 24;   // ~1-2 s of polling with back-off
 
 struct PersistPlan {
@@ -142,9 +139,7 @@ __device__ bool one_iteration(const PersistPlan& P, unsigned char* smem) {
         const Job& J = P.jobs[j];
         if (!active(J)) continue;
         RowShared& rsh = *reinterpret_cast<RowShared*>(smem);
-        double* ss = reinterpret_cast<double*>(smem + kRowSharedPadded);       // 16-byte aligned
-        long long* so = reinterpret_cast<long long*>(smem + kRowSharedPadded + 32 * sizeof(double));
-        density_table_body(J, rsh, ss, so);
+        density_table_body(J, rsh);
         __syncthreads();
     }
     if (!grid_barrier(P)) return false;
@@ -222,7 +217,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persistent(PersistPlan P
 }  // namespace
 
 int persistent_smem_bytes(int max_n) {
-    size_t a = kTableSmem;
+    size_t a = kRowSharedPadded;
     size_t b = sizeof(ScanShared<AccF32, kPersistThreads>);
     size_t c = kWarpsPerBlock * row_warp_bytes(max_n);
     size_t m = a > b ? a : b;

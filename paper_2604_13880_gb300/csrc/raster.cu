@@ -69,20 +69,30 @@ __global__ void __launch_bounds__(256, 8) k_crossings(const Job* __restrict__ jo
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_raster_rows(const Job* __restrict__ jobs,
                                                                     const int2* __restrict__ bmap) {
     extern __shared__ __align__(16) unsigned rows_smem[];
+    __shared__ int big[kWarpsPerBlock];
     const int2 m = bmap[blockIdx.x];                 // (job, first row)
     const Job J = jobs[m.x];                         // fixed over a run: read before the wait
     pdl_wait_and_release();
-    raster_rows_item(J, m.y, rows_smem, true);
+    const int jb = raster_rows_item(J, m.y, rows_smem, true, true);
+    if ((threadIdx.x & 31) == 0) big[threadIdx.x >> 5] = jb;
+    __syncthreads();
+    // rows with more crossings than a warp holds: the whole block, one at a
+    // time, in the (now free) row scratch
+    for (int w = 0; w < kWarpsPerBlock; ++w) {
+        const int j = big[w];
+        if (j >= 0) {
+            raster_row_block(J, j, *reinterpret_cast<RowShared*>(rows_smem));
+            __syncthreads();
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kRowThreads, 1) k_density_table(const Job* __restrict__ jobs) {
     __shared__ RowShared rsh;
-    __shared__ double ss[32];
-    __shared__ long long so[32];
     const Job J = jobs[blockIdx.x];           // fixed over a run: read before the wait
     pdl_wait_and_release();
     if (!J.st->active) return;
-    density_table_body(J, rsh, ss, so);
+    density_table_body(J, rsh);
 }
 
 }  // namespace
@@ -92,7 +102,7 @@ cudaError_t raster_setup(int max_n) {
     (void)max_n;
     static bool done = false;
     if (done) return cudaSuccess;
-    const int bytes = (int)(kWarpsPerBlock * row_warp_bytes(1 << kMaxLog2));
+    const int bytes = (int)rows_smem_bytes(1 << kMaxLog2);
     cudaError_t e = cudaFuncSetAttribute(k_raster_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) done = true;
     return e;
@@ -108,7 +118,7 @@ cudaError_t launch_raster_crossings(const Job* d_jobs, const BlockMap& edge_bloc
 }
 
 cudaError_t launch_raster_rows(const Job* d_jobs, const BlockMap& row_blocks, int max_n, cudaStream_t s) {
-    return launch_pdl(k_raster_rows, row_blocks.n_blocks, kWarpsPerBlock * 32, kWarpsPerBlock * row_warp_bytes(max_n), s,
+    return launch_pdl(k_raster_rows, row_blocks.n_blocks, kWarpsPerBlock * 32, rows_smem_bytes(max_n), s,
                       d_jobs, (const int2*)row_blocks.d_map);
 }
 

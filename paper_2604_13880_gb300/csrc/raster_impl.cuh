@@ -4,6 +4,7 @@
 #pragma once
 
 #include "raster_common.cuh"
+#include "table.cuh"
 
 namespace inim {
 
@@ -44,10 +45,8 @@ struct RowShared {
     unsigned wx[kRowThreads / 32];
     unsigned wc[kRowThreads / 32];
 };
-// RowShared plus the density table's reduction arrays in one block of shared
-// memory: [RowShared, padded to 16][32 doubles][32 long longs]
+// RowShared in dynamic shared memory, padded to 16 bytes
 constexpr size_t kRowSharedPadded = (sizeof(RowShared) + 15) & ~size_t(15);
-constexpr size_t kTableSmem = kRowSharedPadded + 32 * sizeof(double) + 32 * sizeof(long long);
 
 template <int CPT>
 __device__ inline void raster_row(const Job& J, int j, RowShared& sh) {
@@ -166,23 +165,6 @@ __device__ inline void raster_row(const Job& J, int j, RowShared& sh) {
     }
     store_labels<CPT>(J.labels + (size_t)j * n + i0, lab);
     if (tid == 0) J.row_cnt[j] = 0;     // ready for the next iteration
-}
-
-// Rows with more crossings than a warp holds in registers, one block per job
-// (usually none): the block-per-row path.
-__device__ inline void raster_big_rows(const Job& J, RowShared& sh) {
-    const int nbig = __ldcg(&J.st->n_big);
-    for (int q = 0; q < nbig; ++q) {
-        const int j = J.big_rows[q];
-        switch (J.n / kRowThreads) {
-            case 1: raster_row<1>(J, j, sh); break;
-            case 2: raster_row<2>(J, j, sh); break;
-            case 4: raster_row<4>(J, j, sh); break;
-            case 8: raster_row<8>(J, j, sh); break;
-            default: raster_row<16>(J, j, sh); break;
-        }
-        __syncthreads();
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -428,89 +410,68 @@ __device__ __forceinline__ void raster_row_warp(const Job& J, int j, int cnt, un
 // rows [first_row, first_row + 8) of one job, one warp each; rows_smem holds
 // 8 * row_warp_bytes(N) bytes.  With check_active the job's active flag is
 // read together with the row's count and first key slots (one round trip).
-__device__ __forceinline__ void raster_rows_item(const Job& J, int first_row, unsigned* rows_smem,
-                                                 bool check_active = false) {
+// A row with more crossings than a warp holds is returned (local_big: the
+// caller's block rasterises it) or appended to the job's big-row list.
+// Returns that row or -1, the same on every lane.
+__device__ __forceinline__ int raster_rows_item(const Job& J, int first_row, unsigned* rows_smem,
+                                                bool check_active = false, bool local_big = false) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = first_row + warp;
-    if (warp >= kWarpsPerBlock || j >= J.n) return;
+    if (warp >= kWarpsPerBlock || j >= J.n) return -1;
     unsigned* diff = rows_smem + (size_t)warp * (row_warp_bytes(J.n) / 4);
     const uint32_t* bucket = J.keys + (size_t)j * kKeyStride;
     const int act = check_active ? J.st->active : 1;
     const int cnt = J.row_cnt[j];
     const unsigned s0 = bucket[lane], s1 = bucket[32 + lane];     // slots past cnt are ignored
     __syncwarp();                                    // every lane has the count before lane 0 resets it
-    if (!act) return;
-    if (cnt > kKeyStride) {                          // bucket overflow
-        if (lane == 0) { atomicExch(&J.st->error, INIM_E_CAPACITY); J.row_cnt[j] = 0; }
-        return;
-    }
+    if (!act) return -1;
     if (cnt <= 32) raster_row_warp<1>(J, j, cnt, s0, s1, diff, lane);
     else if (cnt <= 2 * 32) raster_row_warp<2>(J, j, cnt, s0, s1, diff, lane);
     else if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, s0, s1, diff, lane);
     else if (cnt <= 8 * 32) raster_row_warp<8>(J, j, cnt, s0, s1, diff, lane);
+    else if (local_big) return j;                    // the block path (raster_row), by the caller
     else if (lane == 0) {                            // big row: finished by the density-table kernel
         const int q = atomicAdd(&J.st->n_big, 1);
         J.big_rows[q] = j;
     }
+    return -1;
 }
 
-// per job (a block of 256 threads): the big rows, then d0, density table,
-// background count, total mass, fixed-point scale
-__device__ inline void density_table_body(const Job& J, RowShared& rsh, double* ss, long long* so) {
+// dynamic shared memory of the row kernel: the warps' row scratch, reused by
+// the block path
+__host__ __device__ constexpr size_t rows_smem_bytes(int max_n) {
+    return kWarpsPerBlock * row_warp_bytes(max_n) > kRowSharedPadded ? kWarpsPerBlock * row_warp_bytes(max_n)
+                                                                     : kRowSharedPadded;
+}
+
+// One row by the whole block (256 threads): the block path for rows with
+// more crossings than a warp holds (up to kRowKeyCap; more raise the
+// capacity error in raster_row).
+__device__ __forceinline__ void raster_row_block(const Job& J, int j, RowShared& sh) {
+    switch (J.n / kRowThreads) {
+        case 1: raster_row<1>(J, j, sh); break;
+        case 2: raster_row<2>(J, j, sh); break;
+        case 4: raster_row<4>(J, j, sh); break;
+        case 8: raster_row<8>(J, j, sh); break;
+        default: raster_row<16>(J, j, sh); break;
+    }
+}
+
+// The rows of the job's big-row list (rows with more crossings than a warp
+// holds, left by the persistent kernel's row phase), one block per job.
+__device__ inline void raster_big_rows(const Job& J, RowShared& sh) {
+    const int nbig = __ldcg(&J.st->n_big);
+    for (int q = 0; q < nbig; ++q) {
+        raster_row_block(J, J.big_rows[q], sh);
+        __syncthreads();
+    }
+}
+
+// per job (a block of 256 threads): the big rows left by the row kernel,
+// then the density table and the job's per-iteration state (table.cuh)
+__device__ inline void density_table_body(const Job& J, RowShared& rsh) {
     raster_big_rows(J, rsh);
-    const int R = J.n_regions;
-    double s = 0.0;
-    long long o = 0;
-    int bad = 0;
-    for (int v = threadIdx.x; v < R; v += blockDim.x) {
-        const float sv = J.values[v];
-        if (!(sv >= 0.0f) || isinf(sv)) bad = 1;           // values must be finite, >= 0
-        const int c = __ldcg(J.counts + v);
-        if (c > 0) { s += (double)sv; o += c; }
-    }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&J.st->error, INIM_E_VALUE);
-#pragma unroll
-    for (int k = 16; k > 0; k >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, k);
-        o += __shfl_xor_sync(0xffffffffu, o, k);
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { ss[w] = s; so[w] = o; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double S = 0.0;
-        long long O = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { S += ss[k]; O += so[k]; }
-        ss[0] = S;
-        so[0] = O;
-    }
-    __syncthreads();
-    const double sum_s = ss[0];
-    const long long sum_o = so[0];
-    const long long npx = (long long)J.n * J.n;
-    const long long o_bg = npx - sum_o;
-    const bool empty = (sum_o == 0);
-    const double d0 = empty ? 1.0 : sum_s / (double)sum_o;
-    for (int v = threadIdx.x; v < R; v += blockDim.x) {
-        const int c = __ldcg(J.counts + v);
-        J.dens[v] = (c > 0 && !empty) ? (float)((double)J.values[v] / ((double)c * d0)) : 0.0f;
-    }
-    if (threadIdx.x == 0) {
-        J.dens[R] = empty ? 1.0f : J.bdv_scale;
-        J.counts[R] = (int)o_bg;
-        JobState* st = J.st;
-        st->d0 = d0;
-        st->bdv_abs = (double)J.bdv_scale * d0;
-        st->mass = empty ? 1.0 : sum_s + st->bdv_abs * (double)o_bg;
-        st->mass_it[st->raster_it & 1] = st->mass;
-        st->raster_it += 1;
-        // all InIm magnitudes are <= C' = sum_o + bdv * o_bg (relative units)
-        const double cbound = empty ? (double)npx : ((double)sum_o + (double)J.bdv_scale * (double)o_bg);
-        int e = 0;
-        frexp(cbound * 1.0001 + 1.0, &e);   // cbound < 2^e
-        int fb = 61 - e;
-        st->fix_bits = fb < 0 ? 0 : fb;
-    }
+    region_table(J, J.dens, true);
 }
 
 

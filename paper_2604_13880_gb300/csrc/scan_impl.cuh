@@ -32,6 +32,7 @@
 
 #include "inim_internal.cuh"
 #include "tma.cuh"
+#include "table.cuh"
 
 namespace inim {
 
@@ -250,16 +251,18 @@ __device__ __forceinline__ LabelWords<CPT> smem_labels(const uint16_t* row, int 
 // threads; the caller provides the shared memory.  DEPTH > 0: the label rows
 // arrive through a ring of bulk copies issued DEPTH rows ahead (ring must
 // then be set); DEPTH == 0: each thread loads its labels two rows ahead.
+// fuse_table (phase 1 from labels, R + 1 <= kDensSmem): the block builds this
+// iteration's density table itself (table.cuh); band 0 publishes it with the
+// job state.
 template <class Acc, int CPT, int NT, int PHASE, int DEPTH = 0>
 __device__ inline void scan_band_body(const Job& J, int band, const float* __restrict__ dtex, ScanShared<Acc, NT>& sh,
-                                      LabelRing<DEPTH> ring = {}) {
+                                      LabelRing<DEPTH> ring = {}, bool fuse_table = false) {
     using T = typename Acc::T;
     const int n = J.n, H = J.H, nb = J.nb;
     const int j0 = band * H;
     const int rows = min(H, n - j0);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int i0 = tid * CPT;
-    const float qscale = ldexpf(1.0f, J.st->fix_bits);   // fixed-point unit (FIX64 only)
 
     T Sacc[CPT], E1[CPT], E2[CPT];
     T e1edge = Acc::zero();             // band-local E1 beyond the right edge
@@ -313,11 +316,20 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
                 tma_load_1d(ring.rows + q * (CPT * NT), J.labels + (size_t)(j0 + q) * n, kRowBytes, ring.bars + q);
     }
     const float* table = J.dens;
-    if (from_labels && J.n_regions + 1 <= kDensSmem) {
-        for (int v = tid; v <= J.n_regions; v += NT) sh.dens[v] = J.dens[v];
+    int fix_bits;
+    if (PHASE == 1 && from_labels && fuse_table) {
+        fix_bits = region_table(J, sh.dens, band == 0).fix_bits;
         table = sh.dens;
         __syncthreads();
+    } else {
+        if (from_labels && J.n_regions + 1 <= kDensSmem) {
+            for (int v = tid; v <= J.n_regions; v += NT) sh.dens[v] = J.dens[v];
+            table = sh.dens;
+            __syncthreads();
+        }
+        fix_bits = J.st->fix_bits;
     }
+    const float qscale = ldexpf(1.0f, fix_bits);   // fixed-point unit (FIX64 only)
     LabelWords<CPT> lw0{}, lw1{};
     float dn[CPT];
     if (from_labels) {
@@ -466,7 +478,7 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
     pdl_wait_and_release();
     if (!J.st->active) return;
     LabelRing<kLabelDepth> ring{reinterpret_cast<uint16_t*>(scan_ring), bars};
-    scan_band_body<Acc, CPT, NT, PHASE, kLabelDepth>(J, m.y, dtex, sh, ring);
+    scan_band_body<Acc, CPT, NT, PHASE, kLabelDepth>(J, m.y, dtex, sh, ring, J.fuse_table != 0);
 }
 
 // phase 2: carries.  Each carry is an exclusive prefix sum over the bands b'

@@ -22,6 +22,7 @@ namespace inim {
 
 constexpr int kPbThreads = 256;
 constexpr int kPbDens = 2048;            // region tables up to this size live in shared memory
+static_assert(kFusedTableMax <= kPbDens && kFusedTableMax <= kDensSmem, "fused tables fit in shared memory");
 
 // shared-memory layout (dynamic): R rows padded by one element per 32 (or
 // N/32) columns, so that a lane's contiguous run and a thread's column group
@@ -74,11 +75,20 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
         for (int q = 0; q < H; ++q)
             tma_load_1d(ring + q * N, J.labels + (size_t)(j0 + q) * N, 2u * N, bars + q);
     const float* table = J.dens;
-    if (from_labels && J.n_regions + 1 <= kPbDens) {
-        for (int v = tid; v <= J.n_regions; v += kPbThreads) dens[v] = J.dens[v];
+    int fix_bits;
+    if (PHASE == 1 && from_labels && J.fuse_table) {
+        // this iteration's density table, built here (every band block the
+        // same; band 0 publishes it with the job state)
+        fix_bits = region_table(J, dens, band == 0).fix_bits;
         table = dens;
+    } else {
+        if (from_labels && J.n_regions + 1 <= kPbDens) {
+            for (int v = tid; v <= J.n_regions; v += kPbThreads) dens[v] = J.dens[v];
+            table = dens;
+        }
+        fix_bits = J.st->fix_bits;
     }
-    const float qscale = ldexpf(1.0f, J.st->fix_bits);   // fixed-point unit (FIX64 only)
+    const float qscale = ldexpf(1.0f, fix_bits);   // fixed-point unit (FIX64 only)
 
     // phase-3 carries of this thread's columns and diagonals, loaded early
     const int i0 = tid * CB;
