@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256, 8) k_crossings(const Job* __restrict__ jo
     if (m.y == 0) reset_raster_block(J);
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) k_raster_rows(const Job* __restrict__ jobs,
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 5) k_raster_rows(const Job* __restrict__ jobs,
                                                                     const int2* __restrict__ bmap) {
     extern __shared__ __align__(16) unsigned rows_smem[];
     __shared__ int big[kWarpsPerBlock];
