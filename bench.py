@@ -73,15 +73,14 @@ def stage_bytes(n_jobs, N, V, R, E, K, nb):
 # ncu captures of `bench.py --ncu-case <batch>` with the kernels and tiles of
 # this source; keyed by (batch, stage, band rows, columns per thread, threads)
 TRAFFIC = {
-    ("chain3", "crossings", 8, 4, 256): 2.359e6,
-    ("chain3", "raster_rows", 8, 4, 256): 0.614e6,
-    ("chain3", "density_table", 8, 4, 256): 0.083e6,
-    ("chain3", "scan_phase1", 8, 4, 256): 6.310e6,
-    ("chain3", "scan_carry", 8, 4, 256): 4.767e6,
-    ("chain3", "scan_phase3", 8, 4, 256): 11.033e6,
-    ("chain3", "gather_move", 8, 4, 256): 7.250e6,
-    ("chain3", "areas_errors", 8, 4, 256): 1.986e6,
-    ("direct72", "scan_phase3", 16, 4, 256): 754.772e6,
+    ("chain3", "crossings", 8, 0, 256): 2.358e6,
+    ("chain3", "raster_rows", 8, 0, 256): 0.876e6,
+    ("chain3", "scan_phase1", 8, 0, 256): 6.349e6,
+    ("chain3", "scan_carry", 8, 0, 256): 4.737e6,
+    ("chain3", "scan_phase3", 8, 0, 256): 11.048e6,
+    ("chain3", "gather_move", 8, 0, 256): 7.250e6,
+    ("chain3", "areas_errors", 8, 0, 256): 1.987e6,
+    ("direct72", "scan_phase3", 32, 4, 256): 731.290e6,
 }
 
 
@@ -234,11 +233,12 @@ def precision_study(args):
 # ---------------------------------------------------------------------------
 def ncu_case(args):
     """direct72: the sweep's 72-solve direct batch; chain3: the 3-solve batch
-    of its cumulative series.  Scan tiles fixed to the ones the sweep ends up
-    with (16/4/256 for the 72-solve batch, chosen on the step; 8 rows in the
-    parallel-rows form for the 3-solve batch).  Per iteration the batch launches, in order: k_crossings,
-    k_raster_rows, k_density_table, k_scan_band<...,1>, k_scan_carry*,
-    k_scan_band<...,3>, k_gather_move, k_areas_errors (after k_raster_reset)."""
+    of its cumulative series.  Scan tiles from --tiles, else 16/4/256 for the
+    72-solve batch and 8 rows in the parallel-rows form for the 3-solve
+    batch.  Per iteration the batch launches, in order: k_crossings,
+    k_raster_rows, k_scan_band*<...,1> (which builds the density table),
+    k_scan_carry*, k_scan_band*<...,3>, k_gather_move, k_areas_errors (after
+    k_raster_reset)."""
     import torch
     import paper_2604_13880_gb300 as P
     from paper_2604_13880_gb300 import _lib, synth
@@ -247,8 +247,10 @@ def ncu_case(args):
     k = w["log2_res"]
     vals = np.ascontiguousarray(w["values"].astype(np.float32))
     m = P.inim_map_create(mesh)
-    P.inim_set_scan_tile(k, P.INIM_FP32, 1, 16, 4, 256)
-    P.inim_set_scan_tile(k, P.INIM_FP32, 0, 8, 0, 256)
+    tl = [tuple(int(x) for x in t.split(",")) for t in args.tiles.split(":")] if args.tiles else \
+        [(16, 4, 256), (8, 0, 256)]
+    P.inim_set_scan_tile(k, P.INIM_FP32, 1, *tl[0])
+    P.inim_set_scan_tile(k, P.INIM_FP32, 0, *tl[1])
     steps = range(T_STEPS) if args.ncu_case == "direct72" else range(1)
     jobs = [(sh, t) for sh in SHAPES for t in steps]
     arr = (P.inim_job * len(jobs))()
@@ -276,6 +278,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain form, time-to-eps and CPU baseline")
+    ap.add_argument("--tiles", default=None, metavar="H,C,T:H,C,T",
+                    help="scan tiles (band rows, columns per thread (0 = parallel rows), threads) of the "
+                         "72-solve and the 3-solve batch, instead of the autotuner and the step-level choice")
     ap.add_argument("--precision-study", type=int, default=0, metavar="K",
                     help="instead of the sweep: K iterations of the 4096^2 precision workload in FP32, "
                          "FIX64 and compensated sums; results to --study-out for the FP64 oracle comparison")
@@ -360,15 +365,20 @@ def main():
     plan_d = make_plan(vals_d, out_dir_d, out_cum_d, None)
 
     # scan tiles chosen by the autotuner on the two batch shapes of the step
-    P.inim_autotune_scan(plan_d[1], reps=5)
-    P.inim_autotune_scan(plan_d[2], reps=20)
+    fixed = [tuple(int(x) for x in t.split(",")) for t in args.tiles.split(":")] if args.tiles else None
+    if fixed:
+        P.inim_set_scan_tile(k, P.INIM_FP32, 1, *fixed[0])
+        P.inim_set_scan_tile(k, P.INIM_FP32, 0, *fixed[1])
+    else:
+        P.inim_autotune_scan(plan_d[1], reps=5)
+        P.inim_autotune_scan(plan_d[2], reps=20)
     # The autotuner times each batch's scan alone; in the step the 72-solve
     # batch shares the GPU with the latency-bound cumulative chain, where
-    # shorter bands (blocks that retire sooner) can win.  Time the step with
-    # the tuned large tile and two shorter band heights, keep the fastest.
+    # other band heights can win.  Time the step with the tuned large tile
+    # and two other band heights, keep the fastest.
     tuned = P.inim_get_scan_tile(k, P.INIM_FP32, 1)
     step_times = {}
-    for H in sorted({tuned["band_rows"], 16, 32}):
+    for H in ([] if fixed else sorted({tuned["band_rows"], 16, 32})):
         P.inim_set_scan_tile(k, P.INIM_FP32, 1, H, tuned["cols_per_thread"], tuned["threads"])
         run_step(plan_d)
         torch.cuda.synchronize()
@@ -376,8 +386,9 @@ def main():
         run_step(plan_d)
         torch.cuda.synchronize()
         step_times[H] = time.perf_counter() - t0
-    best_H = min(step_times, key=step_times.get)
-    P.inim_set_scan_tile(k, P.INIM_FP32, 1, best_H, tuned["cols_per_thread"], tuned["threads"])
+    if step_times:
+        best_H = min(step_times, key=step_times.get)
+        P.inim_set_scan_tile(k, P.INIM_FP32, 1, best_H, tuned["cols_per_thread"], tuned["threads"])
     tiles = {cls: P.inim_get_scan_tile(k, P.INIM_FP32, large) for cls, large in (("large", 1), ("small", 0))}
 
     def barrier():
@@ -436,7 +447,8 @@ def main():
             "config": {"workload": WORKLOAD, "texture": "1024x1024", "regions": R, "vertices": V,
                        "iterations_per_step": ITERS_PER_STEP,
                        "l2": "inputs larger than L2 (72 solves x ~13 MB of textures per batched iteration)",
-                       "parallelism": f"replicas{world}", "scan_tiles_autotuned": tiles,
+                       "parallelism": f"replicas{world}",
+                       ("scan_tiles_fixed" if fixed else "scan_tiles_autotuned"): tiles,
                        "large_band_rows_by_step_ms": {str(h): round(1e3 * t, 2) for h, t in step_times.items()}},
             "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "host_buffers": "pinned"},
