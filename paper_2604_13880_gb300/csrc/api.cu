@@ -323,7 +323,7 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
         J.areas = b.areas; J.st = B.d_states + k;
         B.h_jobs[k] = J;
         if (m) {
-            for (int q = 0; q < (m->n_edges + 255) / 256; ++q) eb.push_back(make_int2(k, q));
+            for (int q = 0; q < (m->n_edges + kEdgesPerItem - 1) / kEdgesPerItem; ++q) eb.push_back(make_int2(k, q));
             for (int q = 0; q < (m->n_verts + 255) / 256; ++q) vb.push_back(make_int2(k, q));
             const int rpb = 8 >> area_warps_log2(m->n_edges, m->n_regions);   // regions per area block
             for (int q = 0; q < (m->n_regions + rpb - 1) / rpb; ++q) gb.push_back(make_int2(k, q));

@@ -13,6 +13,8 @@ namespace inim {
 constexpr int kSubBits = 8;          // sub-pixel bits of the fixed-point raster
 constexpr int kMaxLog2 = 12;         // N <= 4096
 constexpr int kFusedTableMax = 2048; // density table built in the scan when n_regions + 1 <= this
+constexpr int kEdgesPerLane = 2;     // edges per lane of the crossing emission
+constexpr int kEdgesPerItem = 256 * kEdgesPerLane;   // edges per crossing block (256 lanes)
 constexpr int kMinLog2 = 8;          // N >= 256
 constexpr int kKeyStride = 2048;     // crossing keys one texture row can hold (fixed-stride buckets)
 

@@ -25,7 +25,7 @@ constexpr long long kSpinCap = 1LL << 24;   // ~1-2 s of polling with back-off
 struct PersistPlan {
     Job* jobs;
     int n_jobs;
-    const int2* edge_items;   int n_edge_items;     // (job, block of 256 edges)
+    const int2* edge_items;   int n_edge_items;     // (job, item of kEdgesPerItem edges)
     const int2* row_items;    int n_row_items;      // (job, first of 8 rows)
     const int2* band_items;   int n_band_items;     // (job, band)
     const int2* carry_items;  int n_carry_items;    // (job, block of 256 q)
@@ -116,8 +116,7 @@ __device__ bool one_iteration(const PersistPlan& P, unsigned char* smem) {
     for (int it = blockIdx.x; it < P.n_edge_items; it += gridDim.x) {
         const int2 m = P.edge_items[it];
         const Job& J = P.jobs[m.x];
-        const int e = m.y * kPersistThreads + tid;
-        if (active(J)) emit_crossings_warp(J, e, e < J.n_edges);
+        if (active(J)) emit_crossings_item(J, m.y);
     }
     for (int j = blockIdx.x; j < P.n_jobs; j += gridDim.x) {
         const Job& J = P.jobs[j];

@@ -41,28 +41,38 @@ __global__ void __launch_bounds__(256) k_raster_reset(const Job* __restrict__ jo
 // The crossing keys of the current vertex positions, one lane per edge, the
 // crossings spread over each warp; the first edge block of a job also clears
 // its pixel counts and big-row list.
-__global__ void __launch_bounds__(256, 8) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
-    const int2 m = bmap[blockIdx.x];
+__global__ void __launch_bounds__(256, 5) k_crossings(const Job* __restrict__ jobs, const int2* __restrict__ bmap) {
+    const int2 m = bmap[blockIdx.x];                 // (job, item of kEdgesPerItem edges)
     const Job J = jobs[m.x];
     // the job's fields and the mesh (edges, regions) are fixed over a run:
     // read them before the wait; the vertex positions and the active flag after
-    const int e = m.y * blockDim.x + threadIdx.x;
-    const bool valid = e < J.n_edges;
-    int2 ab = make_int2(0, 0);
-    unsigned reg = 0;
-    if (valid) {
-        ab = J.edges[e];
-        reg = (unsigned)J.edge_region[e];
+    bool valid[kEdgesPerLane];
+    int2 ab[kEdgesPerLane];
+    unsigned reg[kEdgesPerLane];
+#pragma unroll
+    for (int s = 0; s < kEdgesPerLane; ++s) {
+        const int e = m.y * kEdgesPerItem + s * 256 + (int)threadIdx.x;
+        valid[s] = e < J.n_edges;
+        ab[s] = make_int2(0, 0);
+        reg[s] = 0;
+        if (valid[s]) {
+            ab[s] = J.edges[e];
+            reg[s] = (unsigned)J.edge_region[e];
+        }
     }
     pdl_wait_and_release();
     const int act = J.st->active;
-    float2 p = make_float2(0.0f, 0.0f), q = p;
-    if (valid) {
-        p = J.xy[ab.x];
-        q = J.xy[ab.y];
+    float2 p[kEdgesPerLane], q[kEdgesPerLane];
+#pragma unroll
+    for (int s = 0; s < kEdgesPerLane; ++s) {
+        p[s] = q[s] = make_float2(0.0f, 0.0f);
+        if (valid[s]) {
+            p[s] = J.xy[ab[s].x];
+            q[s] = J.xy[ab[s].y];
+        }
     }
     if (!act) return;
-    emit_crossings_pts(J, valid, reg, p, q);
+    emit_crossings_lane<kEdgesPerLane>(J, valid, reg, p, q);
     if (m.y == 0) reset_raster_block(J);
 }
 

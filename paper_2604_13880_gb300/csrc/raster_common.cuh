@@ -51,26 +51,32 @@ __device__ __forceinline__ int clamped_ceil_div(long long num, long long den, in
     return (int)(c > n ? n : c);
 }
 
-// The crossings of 32 edges with the texture rows they span, one edge per
-// lane of a full warp (lanes with valid == false take part with no
-// crossings): (region << 16 | first counted column) keys appended to the
-// rows' fixed-stride buckets; a bucket that would overflow raises the
-// capacity error when its row is rasterised.  A stretched edge can span
-// hundreds of rows; instead of one lane walking them all, the warp numbers
-// the crossings of its 32 edges with a prefix sum and hands them out 32 at a
-// time: crossing i belongs to the last lane whose exclusive prefix is <= i
-// (found by a binary search over the lanes' prefixes), which supplies the
-// edge through shuffles.  The warp's serial work is total / 32 crossings
-// instead of the longest edge's row count.
-//
-// emit_crossings_pts takes the edge's region and end points already loaded
-// (valid == false: no edge); emit_crossings_warp loads them.
-__device__ __forceinline__ void emit_crossings_pts(const Job& J, bool valid, unsigned reg, float2 p, float2 q) {
+// The crossings of a warp's edges (E per lane; slots with valid == false take
+// part with no crossings) with the texture rows they span: (region << 16 |
+// first counted column) keys appended to the rows' fixed-stride buckets; a
+// bucket that would overflow raises the capacity error when its row is
+// rasterised.  A stretched edge can span hundreds of rows; instead of one lane
+// walking them all, the warp numbers the crossings of its edges with a prefix
+// sum (lane-major, then slot) and hands them out 32 at a time: crossing i
+// belongs to the last lane whose exclusive prefix is <= i (found by a binary
+// search over the lanes' prefixes), which supplies its edges through
+// shuffles, and to the slot whose range holds it.  The warp's serial work is
+// total / 32 crossings instead of the longest edge's row count, with one
+// bucket atomic per lane and round for all of the warp's edges.
+template <int E>
+__device__ __forceinline__ void emit_crossings_lane(const Job& J, const bool (&valid)[E], const unsigned (&reg)[E],
+                                                    const float2 (&p)[E], const float2 (&q)[E]) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    EdgeFix f{};
+    EdgeFix f[E];
+    int c[E];
     int cnt = 0;
-    if (valid && edge_rows_pts(J, p, q, f)) cnt = f.jhi - f.jlo + 1;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        f[e] = EdgeFix{};
+        c[e] = (valid[e] && edge_rows_pts(J, p[e], q[e], f[e])) ? f[e].jhi - f[e].jlo + 1 : 0;
+        cnt += c[e];
+    }
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -87,32 +93,56 @@ __device__ __forceinline__ void emit_crossings_pts(const Job& J, bool valid, uns
             const int cand = owner + step;
             if (__shfl_sync(full, excl, cand) <= i) owner = cand;
         }
-        const long long X0 = __shfl_sync(full, f.X0, owner), Y0 = __shfl_sync(full, f.Y0, owner);
-        const long long X1 = __shfl_sync(full, f.X1, owner), Y1 = __shfl_sync(full, f.Y1, owner);
-        const int jlo = __shfl_sync(full, f.jlo, owner);
-        const int first = __shfl_sync(full, excl, owner);
-        const unsigned r = __shfl_sync(full, reg, owner);
+        const int k = i - __shfl_sync(full, excl, owner);     // index among the owner's crossings
+        long long X0 = 0, Y0 = 0, X1 = 0, Y1 = 0;
+        int j = 0;
+        unsigned r = 0;
+        int acc = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ce = __shfl_sync(full, c[e], owner);
+            const long long x0 = __shfl_sync(full, f[e].X0, owner), y0 = __shfl_sync(full, f[e].Y0, owner);
+            const long long x1 = __shfl_sync(full, f[e].X1, owner), y1 = __shfl_sync(full, f[e].Y1, owner);
+            const int jl = __shfl_sync(full, f[e].jlo, owner);
+            const unsigned re = __shfl_sync(full, reg[e], owner);
+            if (k >= acc && k < acc + ce) {
+                X0 = x0; Y0 = y0; X1 = x1; Y1 = y1;
+                j = jl + (k - acc);
+                r = re;
+            }
+            acc += ce;
+        }
         if (i < total) {
-            const int j = jlo + (i - first);
             const long long dY = Y1 - Y0, dX = X1 - X0;
             const long long Yc = 256LL * j + 128;
-            const int c = clamped_ceil_div(dX * (Yc - Y0) + (X0 - 128) * dY, 256 * dY, J.n);
+            const int col = clamped_ceil_div(dX * (Yc - Y0) + (X0 - 128) * dY, 256 * dY, J.n);
             const int slot = atomicAdd(&J.row_cnt[j], 1);
-            if (slot < kKeyStride) J.keys[(size_t)j * kKeyStride + slot] = (r << 16) | (unsigned)c;
+            if (slot < kKeyStride) J.keys[(size_t)j * kKeyStride + slot] = (r << 16) | (unsigned)col;
         }
     }
 }
 
-__device__ __forceinline__ void emit_crossings_warp(const Job& J, int e, bool valid) {
-    unsigned reg = 0;
-    float2 p = make_float2(0.0f, 0.0f), q = p;
-    if (valid) {
-        const int2 ab = J.edges[e];
-        reg = (unsigned)J.edge_region[e];
-        p = J.xy[ab.x];
-        q = J.xy[ab.y];
+// One item of kEdgesPerItem edges of a job (a block of 256 threads; lane
+// slot s holds edge item * kEdgesPerItem + s * 256 + threadIdx.x), loading
+// the edges and their end points itself.
+__device__ __forceinline__ void emit_crossings_item(const Job& J, int item) {
+    bool valid[kEdgesPerLane];
+    unsigned reg[kEdgesPerLane];
+    float2 p[kEdgesPerLane], q[kEdgesPerLane];
+#pragma unroll
+    for (int s = 0; s < kEdgesPerLane; ++s) {
+        const int e = item * kEdgesPerItem + s * 256 + (int)threadIdx.x;
+        valid[s] = e < J.n_edges;
+        reg[s] = 0;
+        p[s] = q[s] = make_float2(0.0f, 0.0f);
+        if (valid[s]) {
+            const int2 ab = J.edges[e];
+            reg[s] = (unsigned)J.edge_region[e];
+            p[s] = J.xy[ab.x];
+            q[s] = J.xy[ab.y];
+        }
     }
-    emit_crossings_pts(J, valid, reg, p, q);
+    emit_crossings_lane<kEdgesPerLane>(J, valid, reg, p, q);
 }
 
 // Per job, while the keys of an iteration are being emitted (one block):
