@@ -548,7 +548,12 @@ def test_series_persistent_and_graph_paths_agree_with_oracle():
     for got in (graph, pers):
         assert np.abs(got[0] - od).max() <= 1e-4 * EXTENT
         assert np.abs(got[1] - oc).max() <= 1e-4 * EXTENT
-    assert np.abs(graph[1] - pers[1]).max() <= 1e-5
+    # the two paths scan with different tiles (parallel-rows vs row-serial),
+    # so their FP32 InIms round differently: each within the FP32 bound
+    # 2 (N/8 + 64) 2^-24 C of the exact sums (test_inims_fp32), 1.5e-5 C at
+    # N = 512; the cumulative trajectories may differ by the two bounds
+    N = 1 << 9
+    assert np.abs(graph[1] - pers[1]).max() <= 2 * 2 * (N / 8 + 64) * 2.0 ** -24 * EXTENT
     assert [s["iters"] for s in pstats[1]] == [6, 6, 6] and [s["iters"] for s in gstats[1]] == [6, 6, 6]
 
 
