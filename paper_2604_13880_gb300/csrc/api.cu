@@ -316,6 +316,7 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
         J.labels = b.labels; J.row_cnt = b.row_cnt; J.big_rows = b.big_rows;
         J.keys = b.keys;
         J.counts = b.counts; J.dens = b.dens;
+        J.pdl_early = size_class(total_px) == 0 ? 1 : 0;
         J.S = b.S; J.T = b.T; J.A = b.A; J.B = b.B; J.rowcum = b.rowcum;
         // map jobs: one interleaved (S, T) table (S's buffer holds both halves)
         J.ST = m ? b.S : nullptr;

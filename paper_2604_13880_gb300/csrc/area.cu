@@ -22,9 +22,10 @@ __global__ void __launch_bounds__(256) k_areas_errors(const Job* __restrict__ jo
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     const AreaPre pre = areas_prefetch(J, m.y);
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
     areas_body(J, m.y, update_state, pre);
+    pdl_release();
 }
 
 }  // namespace

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) k_gather_move(const Job* __restrict__ job
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     const int v = m.y * blockDim.x + threadIdx.x;
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (v >= J.n_verts) return;
     // the active flag, the vertex and C in one round trip
     const int act = J.st->active;
@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) k_gather_move(const Job* __restrict__ job
     const typename Acc::T C = grand_total<Acc>(J);
     if (!act) return;
     move_vertex<Acc>(J, v, p, C);
+    pdl_release();
 }
 
 template <class Acc>

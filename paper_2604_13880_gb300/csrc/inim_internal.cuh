@@ -69,6 +69,7 @@ struct Job {
     float bdv_scale;
     int   precision;           // INIM_FP32 / INIM_FIX64 / INIM_KAHAN
     int   fuse_table;          // 1: the scan's first phase builds the density table (no density kernel)
+    int   pdl_early;           // 1: let the next kernel launch at this kernel's start (see pdl_start)
     // raster workspace
     uint16_t* labels;          // [n*n]
     int*      row_cnt;         // [n] crossing keys in each row's bucket (reset by the row rasteriser)
@@ -105,11 +106,20 @@ __host__ __device__ inline int area_warps_log2(int n_edges, int n_regions) {
 // programmatic dependent launch: the kernels of one iteration are launched so
 // that the next kernel's grid is set up while the current one runs; every such
 // kernel first waits for its predecessor to complete (and its writes to be
-// visible), then lets its own successor launch.  Without the launch attribute
-// both instructions return at once.
+// visible).  It lets its own successor launch either at once (pdl_start, for
+// jobs with pdl_early: the latency-bound small batches, whose next kernel's
+// blocks then hold their SM slots before a concurrent large batch's blocks
+// take them) or when its own work is issued (pdl_release at the end, for the
+// large batches: waiting blocks would only hold slots the small batches
+// need).  Without the launch attribute all of these return at once.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pdl_wait_and_release() {
-    asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+__device__ __forceinline__ void pdl_release() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_start(bool early) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (early) pdl_release();
 }
 
 bool pdl_enabled();   // INIM_PDL=0 in the environment turns the attribute off

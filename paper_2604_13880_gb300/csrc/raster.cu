@@ -29,7 +29,7 @@ namespace {
 // the start of a run.
 __global__ void __launch_bounds__(256) k_raster_reset(const Job* __restrict__ jobs) {
     const Job& J = jobs[blockIdx.x];
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
     if (threadIdx.x == 0) {
         J.st->raster_it = 0;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, 5) k_crossings(const Job* __restrict__ jo
             reg[s] = (unsigned)J.edge_region[e];
         }
     }
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     const int act = J.st->active;
     float2 p[kEdgesPerLane], q[kEdgesPerLane];
 #pragma unroll
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256, 5) k_crossings(const Job* __restrict__ jo
     if (!act) return;
     emit_crossings_lane<kEdgesPerLane>(J, valid, reg, p, q);
     if (m.y == 0) reset_raster_block(J);
+    pdl_release();
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5) k_raster_rows(const Job* __restrict__ jobs,
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5) k_raster_rows(const Jo
     __shared__ int big[kWarpsPerBlock];
     const int2 m = bmap[blockIdx.x];                 // (job, first row)
     const Job J = jobs[m.x];                         // fixed over a run: read before the wait
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     const int jb = raster_rows_item(J, m.y, rows_smem, true, true);
     if ((threadIdx.x & 31) == 0) big[threadIdx.x >> 5] = jb;
     __syncthreads();
@@ -95,14 +96,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5) k_raster_rows(const Jo
             __syncthreads();
         }
     }
+    pdl_release();
 }
 
 __global__ void __launch_bounds__(kRowThreads, 1) k_density_table(const Job* __restrict__ jobs) {
     __shared__ RowShared rsh;
     const Job J = jobs[blockIdx.x];           // fixed over a run: read before the wait
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
     density_table_body(J, rsh);
+    pdl_release();
 }
 
 }  // namespace

@@ -475,10 +475,11 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
     extern __shared__ __align__(128) unsigned char scan_ring[];     // [kLabelDepth][CPT * NT] u16
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
     LabelRing<kLabelDepth> ring{reinterpret_cast<uint16_t*>(scan_ring), bars};
     scan_band_body<Acc, CPT, NT, PHASE, kLabelDepth>(J, m.y, dtex, sh, ring, J.fuse_table != 0);
+    pdl_release();
 }
 
 // phase 2: carries.  Each carry is an exclusive prefix sum over the bands b'
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
                                                     const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
     scan_carry_body<Acc>(J, m.y * blockDim.x + threadIdx.x);
 }
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     __shared__ T tot[kCarryGroups][32];
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int nb = J.nb;
@@ -635,6 +636,7 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
             }
         }
     }
+    pdl_release();
 }
 
 // ---------------------------------------------------------------------------

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
 
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
-    pdl_wait_and_release();
+    pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
     const int band = m.y, nb = J.nb, j0 = band * H;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
             }
         }
     }
+    pdl_release();
     if constexpr (PHASE == 1) {
         T* agg = reinterpret_cast<T*>(J.agg);
         T a1[CB], a2[CB];
