@@ -189,6 +189,8 @@ struct Group {
     BlockMap band, carry;
 };
 
+constexpr int kGraphSizes = 6;     // CUDA graphs of 1, 2, 4, 8, 16, 32 iterations per batch
+
 struct Batch {
     std::vector<JobSpec> spec;
     std::vector<Job> h_jobs;
@@ -203,14 +205,13 @@ struct Batch {
     bool fuse_table = false;            // the scan builds the density table (no density kernel)
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    cudaGraphExec_t graph1 = nullptr;    // one iteration, for the tail of a fixed-length run
-    // overlapped form (fixed-length runs): each iteration's area kernel on a
-    // side branch, next to the next iteration's raster and scan
+    // CUDA graphs of 1, 2, 4, ... 32 fused iterations (captured on first use),
+    // plain [0] and overlapped [1]: in the overlapped form (fixed-length runs)
+    // each iteration's area kernel runs on a side branch, next to the next
+    // iteration's raster and scan
+    cudaGraphExec_t graphs[2][kGraphSizes] = {};
     cudaStream_t side = nullptr;
     cudaEvent_t ev_moved = nullptr, ev_areas = nullptr;
-    cudaGraphExec_t graph_ov = nullptr, graph1_ov = nullptr;
-    int graph_iters = 0;
     std::vector<PlainWork> plain;   // per job (plain form only)
     // persistent form: all resolution groups' band / carry items, barrier words,
     // per-job round tables (time series), their device pointer arrays
@@ -227,6 +228,12 @@ struct Batch {
     JobState** d_round_stats = nullptr;
     JobState* d_round_init = nullptr;
     long long total_px = 0;
+    // cumulative rounds enqueued at once: per round, the jobs and states to
+    // upload and the final states read back (pinned host memory)
+    int pin_rounds = 0;
+    Job* pin_jobs = nullptr;
+    JobState* pin_states = nullptr;
+    JobState* pin_out_states = nullptr;
     // learned warm start: pooled inputs, predicted fields, per-job field pointers
     float* ws_in = nullptr;
     float* ws_out = nullptr;
@@ -241,20 +248,29 @@ struct Batch {
         round_cap = 0;
     }
 
+    void free_pinned() {
+        if (pin_jobs) cudaFreeHost(pin_jobs);
+        if (pin_states) cudaFreeHost(pin_states);
+        if (pin_out_states) cudaFreeHost(pin_out_states);
+        pin_jobs = nullptr; pin_states = nullptr; pin_out_states = nullptr;
+        pin_rounds = 0;
+    }
+
     ~Batch() {
+        if (stream) cudaStreamSynchronize(stream);     // no copy from the pinned buffers is still queued
+        free_pinned();
         free_rounds();
         dfree(ws_in); dfree(ws_out); dfree(ws_ptrs);
         dfree(d_bar); dfree(d_err); dfree(all_band.d_map); dfree(all_carry.d_map);
-        if (graph) cudaGraphExecDestroy(graph);
-        if (graph1) cudaGraphExecDestroy(graph1);
+        for (auto& row : graphs)
+            for (auto& g : row)
+                if (g) cudaGraphExecDestroy(g);
         for (auto& b : bufs) b.release();
         for (auto& p : plain) plain_free(p);
         dfree(d_jobs); dfree(d_states);
         BlockMap* maps[] = {&edge_blocks, &job_blocks, &row_blocks, &vert_blocks, &region_blocks};
         for (BlockMap* m : maps) dfree(m->d_map);
         for (auto& g : groups) { dfree(g.band.d_map); dfree(g.carry.d_map); }
-        if (graph_ov) cudaGraphExecDestroy(graph_ov);
-        if (graph1_ov) cudaGraphExecDestroy(graph1_ov);
         if (ev_moved) cudaEventDestroy(ev_moved);
         if (ev_areas) cudaEventDestroy(ev_areas);
         if (side) cudaStreamDestroy(side);
@@ -484,7 +500,7 @@ cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s, bool overlap = fal
     return e;
 }
 
-constexpr int kGraphIters = 8;
+constexpr int kPollIters = 8;   // iterations between host polls of the stop rule
 
 std::atomic<long long> g_launches{0};
 
@@ -525,43 +541,32 @@ cudaError_t capture_iterations(Batch& B, int iters, cudaGraphExec_t* out, bool o
 }
 
 int ensure_graph(Batch& B, bool overlap = false) {
-    B.graph_iters = kGraphIters;
-    if (!overlap) {
-        if (B.graph && B.graph1) return INIM_OK;
-        cudaError_t e = capture_iterations(B, kGraphIters, &B.graph, false);
-        if (e == cudaSuccess) e = capture_iterations(B, 1, &B.graph1, false);
-        if (e != cudaSuccess) return fail(INIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-        return INIM_OK;
-    }
-    if (B.graph_ov && B.graph1_ov) return INIM_OK;
-    if (!B.side) {
+    if (overlap && !B.side) {
         int prio = 0;
         CUDA_TRY(cudaStreamGetPriority(B.stream, &prio));
         CUDA_TRY(cudaStreamCreateWithPriority(&B.side, cudaStreamNonBlocking, prio));
         CUDA_TRY(cudaEventCreateWithFlags(&B.ev_moved, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreateWithFlags(&B.ev_areas, cudaEventDisableTiming));
     }
-    cudaError_t e = capture_iterations(B, kGraphIters, &B.graph_ov, true);
-    if (e == cudaSuccess) e = capture_iterations(B, 1, &B.graph1_ov, true);
-    if (e != cudaSuccess) return fail(INIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    for (int q = 0; q < kGraphSizes; ++q) {
+        if (B.graphs[overlap][q]) continue;
+        const cudaError_t e = capture_iterations(B, 1 << q, &B.graphs[overlap][q], overlap);
+        if (e != cudaSuccess) return fail(INIM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
     return INIM_OK;
 }
 
-// launch the graphs for `iters` more iterations: full replays, then the
-// one-iteration graph for the remainder (no idle iterations at the end)
+// launch the graphs for `iters` more iterations, largest first (the binary
+// digits of iters: 50 = 32 + 16 + 2, three graph launches)
 cudaError_t launch_iterations(Batch& B, int iters, bool overlap = false) {
     const int per = kernels_per_fused_iteration(B);
-    cudaGraphExec_t full = overlap ? B.graph_ov : B.graph, one = overlap ? B.graph1_ov : B.graph1;
-    while (iters >= B.graph_iters) {
-        cudaError_t e = cudaGraphLaunch(full, B.stream);
-        if (e != cudaSuccess) return e;
-        g_launches += (long long)B.graph_iters * per;
-        iters -= B.graph_iters;
-    }
-    for (; iters > 0; --iters) {
-        cudaError_t e = cudaGraphLaunch(one, B.stream);
-        if (e != cudaSuccess) return e;
-        g_launches += per;
+    for (int q = kGraphSizes - 1; q >= 0 && iters > 0; --q) {
+        while (iters >= (1 << q)) {
+            cudaError_t e = cudaGraphLaunch(B.graphs[overlap][q], B.stream);
+            if (e != cudaSuccess) return e;
+            g_launches += (long long)per << q;
+            iters -= 1 << q;
+        }
     }
     return cudaSuccess;
 }
@@ -663,6 +668,19 @@ int enqueue_fused_async(Batch& B, int max_iters) {
     return INIM_OK;
 }
 
+// pinned per-round staging for `rounds` rounds of the batch's jobs
+int ensure_pinned_rounds(Batch& B, int rounds) {
+    if (B.pin_rounds >= rounds) return INIM_OK;
+    CUDA_TRY(cudaStreamSynchronize(B.stream));          // the old buffers may still be read by queued copies
+    B.free_pinned();
+    const size_t nj = B.spec.size();
+    CUDA_TRY(cudaMallocHost(&B.pin_jobs, (size_t)rounds * nj * sizeof(Job)));
+    CUDA_TRY(cudaMallocHost(&B.pin_states, (size_t)rounds * nj * sizeof(JobState)));
+    CUDA_TRY(cudaMallocHost(&B.pin_out_states, (size_t)rounds * nj * sizeof(JobState)));
+    B.pin_rounds = rounds;
+    return INIM_OK;
+}
+
 bool needs_poll(const inim_params& p) {
     return p.xi_stop > 0.0f || p.eps_stop > 0.0f || p.stall_window > 0;
 }
@@ -678,7 +696,7 @@ int run_fused(Batch& B, int max_iters, bool poll) {
     g_launches += 1;                                       // bucket reset
     int done = 0;
     while (done < max_iters) {
-        const int step = std::min(B.graph_iters, max_iters - done);
+        const int step = poll ? std::min(kPollIters, max_iters - done) : max_iters - done;
         CUDA_TRY(launch_iterations(B, step, ov));
         done += step;
         if (poll && done < max_iters) {
@@ -929,6 +947,50 @@ int run_series_impl(const inim_series* S, int n) {
                 CUDA_TRY(cudaStreamSynchronize(B->stream));
                 for (int t = 0; t < x.T; ++t) result = worst(result, fill_stats(rs[t], x.stats ? x.stats + t : nullptr));
             }
+        } else if (!poll) {
+            // no stop rule: every round is enqueued at once (its jobs and
+            // states staged through pinned memory, its final states copied
+            // back to pinned memory), with one host wait at the end
+            st = ensure_pinned_rounds(*B, rounds);
+            if (st != INIM_OK) return st;
+            for (int t = 0; t < rounds; ++t) {
+                for (int k = 0; k < nc; ++k) {
+                    const inim_series& x = S[cref[k].series];
+                    if (t > 0 && t < x.T) {
+                        st = setup_job(*B, k, x, t, false);
+                        if (st != INIM_OK) return st;
+                    } else if (t >= x.T) {
+                        B->h_states[k].active = 0;
+                    }
+                }
+                Job* pj = B->pin_jobs + (size_t)t * nc;
+                JobState* ps = B->pin_states + (size_t)t * nc;
+                std::copy(B->h_jobs.begin(), B->h_jobs.end(), pj);
+                std::copy(B->h_states.begin(), B->h_states.end(), ps);
+                CUDA_TRY(cudaMemcpyAsync(B->d_jobs, pj, nc * sizeof(Job), cudaMemcpyHostToDevice, B->stream));
+                CUDA_TRY(cudaMemcpyAsync(B->d_states, ps, nc * sizeof(JobState), cudaMemcpyHostToDevice, B->stream));
+                st = enqueue_fused_async(*B, max_it);
+                if (st != INIM_OK) return st;
+                CUDA_TRY(cudaMemcpyAsync(B->pin_out_states + (size_t)t * nc, B->d_states, nc * sizeof(JobState),
+                                         cudaMemcpyDeviceToHost, B->stream));
+                for (int k = 0; k < nc; ++k) {
+                    const inim_series& x = S[cref[k].series];
+                    if (t >= x.T) continue;
+                    const int V = x.map->n_verts;
+                    CUDA_TRY(cudaMemcpyAsync(x.out_xy + (size_t)t * V * 2, B->bufs[k].xy, (size_t)V * 8,
+                                             cudaMemcpyDefault, B->stream));
+                }
+            }
+            CUDA_TRY(cudaStreamSynchronize(B->stream));
+            for (int t = 0; t < rounds; ++t)
+                for (int k = 0; k < nc; ++k) {
+                    const inim_series& x = S[cref[k].series];
+                    if (t >= x.T) continue;
+                    const JobState& rs = B->pin_out_states[(size_t)t * nc + k];
+                    result = worst(result, fill_stats(rs, x.stats ? x.stats + t : nullptr));
+                }
+            std::copy(B->pin_out_states + (size_t)(rounds - 1) * nc, B->pin_out_states + (size_t)rounds * nc,
+                      B->h_states.begin());
         } else {
             for (int t = 0; t < rounds; ++t) {
                 for (int k = 0; k < nc; ++k) {
