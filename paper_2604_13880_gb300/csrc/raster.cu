@@ -10,15 +10,18 @@
 // A pixel is inside region v iff v's crossing count is odd; inside several
 // regions it takes the smallest id and the overlap flag is raised.
 //
-// Kernels (edge-parallel, then row-parallel; no per-pixel atomics):
-//   k_crossings    per edge: (region << 16 | c) appended to the fixed-stride
-//                  bucket of every row the edge crosses (no histogram or
-//                  prefix pass: each bucket holds up to 2048 keys)
+// Kernels (edge-parallel, then row-parallel; no per-pixel global atomics):
+//   k_crossings    two edges per lane: (region << 16 | c) appended to the
+//                  fixed-stride bucket of every row the edge crosses (no
+//                  histogram or prefix pass: each bucket holds up to 2048 keys)
 //   k_raster_rows  warp per row: sort the row's keys in registers, pair them
-//                  into spans, paint them into a shared-memory copy of the row
-//                  in region order, write the row once; rows with more than
-//                  256 crossings go to the block-per-row path (run by the
-//                  density-table kernel).
+//                  into spans, enter the spans into a shared-memory difference
+//                  array and build every label by one striped prefix pass
+//                  (pixels inside two spans resolved to the smallest region);
+//                  rows with more than 256 crossings are finished by the
+//                  block-per-row path of the same block
+//   k_density_table the density table (table.cuh), only for maps of more than
+//                  2047 regions (otherwise scan phase 1 builds it)
 #include "raster_impl.cuh"
 
 namespace inim {
