@@ -1182,7 +1182,7 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
     int st = check_params(params);
     if (st != INIM_OK) return st;
     const int R = map->n_regions, V = map->n_verts;
-    // host values are checked here, device values by the density kernel
+    // host values are checked here, device values where the density table is built
     const bool val_dev = is_device_ptr(values);
     if (!val_dev) {
         st = check_values(values, (size_t)T * R);
@@ -1281,7 +1281,7 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
         if (st != INIM_OK) return st;
         if (j.params.form != INIM_FORM_FUSED) return fail(INIM_E_ARG, "inim_run_batch needs the fused form");
         if (j.params.precision != jobs[0].params.precision) return fail(INIM_E_ARG, "all jobs need one precision");
-        if (!is_device_ptr(j.values)) {     // device values are checked by the density kernel
+        if (!is_device_ptr(j.values)) {     // device values are checked where the density table is built
             st = check_values(j.values, j.map->n_regions);
             if (st != INIM_OK) return st;
         }

@@ -138,8 +138,8 @@ cudaError_t launch_raster_rows(const Job* d_jobs, const BlockMap& row_blocks, in
                       d_jobs, (const int2*)row_blocks.d_map);
 }
 
-// crossing keys into the row buckets, then the rows; big rows finish in the
-// density kernel
+// crossing keys into the row buckets, then the rows (rows with more than 256
+// crossings are finished by the row kernel's own block)
 cudaError_t launch_raster_main(const Job* d_jobs, const BlockMap& edge_blocks, const BlockMap& row_blocks,
                                int max_n, cudaStream_t s) {
     cudaError_t e = launch_raster_crossings(d_jobs, edge_blocks, s);

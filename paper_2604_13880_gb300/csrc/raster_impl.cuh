@@ -430,7 +430,7 @@ __device__ __forceinline__ int raster_rows_item(const Job& J, int first_row, uns
     else if (cnt <= 4 * 32) raster_row_warp<4>(J, j, cnt, s0, s1, diff, lane);
     else if (cnt <= 8 * 32) raster_row_warp<8>(J, j, cnt, s0, s1, diff, lane);
     else if (local_big) return j;                    // the block path (raster_row), by the caller
-    else if (lane == 0) {                            // big row: finished by the density-table kernel
+    else if (lane == 0) {                            // big row: left to density_table_body (persistent form)
         const int q = atomicAdd(&J.st->n_big, 1);
         J.big_rows[q] = j;
     }
