@@ -13,7 +13,9 @@ shape blend, the desired area w(v)).
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against brute
 force on tiny inputs, closed forms, invariants of Eq. (1)-(3) and hand-derived
-golden values (``tests/golden``).  Parity unpinned by the paper (pinned only
+golden values (``tests/golden``); the dynamic-area background of Eq. (Mb) by
+the fixed point of a map at its target area fraction and the direction in
+which a map away from it moves.  Parity unpinned by the paper (pinned only
 by the shared reading): the shape-blend reading, the desired area w(v) and
 the pixel-sample convention.
 """
@@ -145,8 +147,10 @@ def labels_scanline(xy, ring_off, ring_idx, ring_region, n_regions, log2_res):
 # Step 3: piecewise-constant density texture and background density
 # ----------------------------------------------------------------------------
 
-def density(labels, counts, values, bdv_scale=1.0):
-    """d = s(v)/o(v) inside region v; background = bdv_scale * d0.
+def density(labels, counts, values, bdv_scale=1.0, bdv_abs=None):
+    """d = s(v)/o(v) inside region v; background = bdv_scale * d0, or the
+    given background value bdv_abs (value units per pixel, Eq. (Mb): see
+    background_values).
 
     d0 is the area-weighted mean density of the regions,
     d0 = sum_{v: o(v)>0} s(v) / sum_v o(v), so that with bdv_scale = 1 the
@@ -160,7 +164,7 @@ def density(labels, counts, values, bdv_scale=1.0):
     if tot_o == 0:
         return np.ones(labels.shape), 1.0, 1.0
     d0 = values[has].sum() / tot_o
-    bdv = bdv_scale * d0
+    bdv = bdv_scale * d0 if bdv_abs is None else float(bdv_abs)
     per_region = np.where(has, values / np.maximum(counts, 1), 0.0)
     d = np.where(labels >= 0, per_region[np.maximum(labels, 0)], bdv)
     return d, d0, bdv
@@ -385,6 +389,39 @@ def signed_areas(xy, ring_off, ring_idx, ring_region, n_regions):
     return out
 
 
+def background_values(values, log2_res, a_min, a_max, t0=0, t1=None):
+    """Background value per time step for a map whose area follows its global
+    integral (Sec. 3.5, Eq. (Mb)).
+
+    M_i(t) = sum_v s_v(t) is the global integral; over the selected steps
+    [t0, t1] its extremes M_min, M_max give the weight
+    w(t) = (M_i(t) - M_min) / (M_max - M_min) and the map's area fraction
+    A_i(t) = (1 - w) a_min + w a_max (0 < a_min < a_max < 1), from which the
+    background mass is M_b(t) = M_i(t) (1 - A_i(t)) / A_i(t), i.e.
+    A_i(t) = M_i(t) / (M_i(t) + M_b(t)).  The background value divides M_b(t)
+    by the background pixels the target leaves, (1 - A_i(t)) N^2, which is
+    the equalised density (M_i + M_b) / N^2: at equal density everywhere the
+    map then covers exactly the fraction A_i(t) of the domain.  Readings: w is
+    clipped to [0, 1] for steps outside [t0, t1]; with M_max = M_min, w = 1.
+    Returns (bdv [T], m_b [T], a_i [T]).
+    """
+    vals = np.atleast_2d(np.asarray(values, dtype=np.float64))
+    T = vals.shape[0]
+    t1 = T - 1 if t1 is None else t1
+    if not (0.0 < a_min < a_max < 1.0):
+        raise ValueError("need 0 < a_min < a_max < 1")
+    if not (0 <= t0 <= t1 < T):
+        raise ValueError("need 0 <= t0 <= t1 < T")
+    m_i = vals.sum(axis=1)
+    m_min, m_max = m_i[t0:t1 + 1].min(), m_i[t0:t1 + 1].max()
+    w = np.ones(T) if m_max == m_min else np.clip((m_i - m_min) / (m_max - m_min), 0.0, 1.0)
+    a_i = (1.0 - w) * a_min + w * a_max
+    m_b = m_i * (1.0 - a_i) / a_i
+    N = 1 << log2_res
+    bdv = m_b / ((1.0 - a_i) * N * N)
+    return bdv, m_b, a_i
+
+
 def desired_areas(values, counts, bdv, N):
     """w(v) = s(v) / M with M = sum_{o(v)>0} s(v) + BDV * o_bg the total mass
     in the texture: when the density is equalised, area is proportional to
@@ -410,7 +447,7 @@ def cartographic_errors(areas, desired):
 # ----------------------------------------------------------------------------
 
 def iterate(xy, mesh_arrays, values, log2_res, shape, bdv_scale=1.0, t0=None,
-            raster_xy=None, raster="scanline"):
+            raster_xy=None, raster="scanline", bdv_abs=None):
     """One InIm iteration: raster, density, InIms, Eq. (3) field, bilinear,
     blend, move.  Returns (new_xy, info).
 
@@ -422,7 +459,7 @@ def iterate(xy, mesh_arrays, values, log2_res, shape, bdv_scale=1.0, t0=None,
     rxy = xy if raster_xy is None else raster_xy
     fn = labels_scanline if raster == "scanline" else labels_bruteforce
     labels, counts, overlap = fn(rxy, ring_off, ring_idx, ring_region, R, log2_res)
-    d, d0, bdv = density(labels, counts, values, bdv_scale)
+    d, d0, bdv = density(labels, counts, values, bdv_scale, bdv_abs)
     if t0 is None:
         t0 = transform_uniform(N)
     fx, fy = displacement_field(d, t0)
@@ -466,23 +503,27 @@ class StopRule:
 
 
 def run(mesh, values, log2_res, shape=0.5, bdv_scale=1.0, max_iters=512, xi_stop=0.01,
-        stall_window=32, mode="direct", eps_stop=0.0, init_xy=None):
+        stall_window=32, mode="direct", eps_stop=0.0, init_xy=None, area_fractions=None):
     """Time-varying driver (Sec. 4.2): for each time step, iterate from the
     original map (direct) or from the previous step's result (cumulative)
-    until the stop rule fires.  Returns (xy [T, V, 2], stats list)."""
+    until the stop rule fires.  area_fractions = (a_min, a_max[, t0, t1])
+    sets each step's background value by Eq. (Mb) (background_values)
+    instead of bdv_scale * d0.  Returns (xy [T, V, 2], stats list)."""
     arrays = (mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
     values = np.atleast_2d(np.asarray(values, dtype=np.float64))
     N = 1 << log2_res
     t0 = transform_uniform(N)
     orig = np.asarray(mesh.verts if init_xy is None else init_xy, dtype=np.float64)
     xy = orig.copy()
+    bdv_t = background_values(values, log2_res, *area_fractions)[0] if area_fractions is not None else None
     out, stats = [], []
     for t in range(values.shape[0]):
         if mode == "direct" or t == 0:
             xy = orig.copy()
         rule = StopRule(max_iters, xi_stop, stall_window, eps_stop)
         while True:
-            xy, info = iterate(xy, arrays, values[t], log2_res, shape, bdv_scale, t0)
+            xy, info = iterate(xy, arrays, values[t], log2_res, shape, bdv_scale, t0,
+                               bdv_abs=None if bdv_t is None else bdv_t[t])
             areas = signed_areas(xy, *arrays)
             eps, xi = cartographic_errors(areas, info["desired"])
             if rule.update(eps, xi):
