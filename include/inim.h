@@ -86,7 +86,10 @@ typedef struct {
     int32_t form;         /* INIM_FORM_FUSED or INIM_FORM_PLAIN */
     int32_t warm_start;   /* 1: move vertices by the learned field first (needs
                              inim_warmstart_load); default 0 */
-    int32_t reserved;
+    float   bdv_value;    /* > 0: background density in value units per pixel,
+                             replacing bdv_scale * d0 (dynamic area, Sec. 3.5,
+                             Eq. (Mb): one value per time step from
+                             inim_background_values); default 0 (off) */
 } inim_params;
 
 /* Per time-step statistics. */
@@ -128,6 +131,27 @@ const char* inim_status_string(int status);
 
 /* Message of the last error reported on the calling thread ("" if none). */
 const char* inim_last_error(void);
+
+/*
+ * Background values of a time series whose map area follows its global
+ * integral (dynamic area, Sec. 3.5, Eq. (Mb)); host memory, no GPU work.
+ *   values        [T*n_regions] host s_t(v) >= 0.
+ *   a_min, a_max  area fractions of the map at the smallest and the largest
+ *                 global integral M(t) = sum_v s_t(v) over the selected
+ *                 steps [t0, t1]; 0 < a_min < a_max < 1.
+ *   t0, t1        selected steps; t1 < 0 means T - 1.
+ *   bdv           [T] out: the background value of step t in value units per
+ *                 pixel, M_b(t) / ((1 - A(t)) N^2) with A(t) interpolated
+ *                 linearly in M(t) between a_min and a_max (clipped to them
+ *                 outside [t0, t1]; a_max when M is constant) and
+ *                 M_b(t) = M(t) (1 - A(t)) / A(t).  Pass bdv[t] as
+ *                 inim_params.bdv_value of the solve of step t.
+ *   area_fraction [T] out A(t), or NULL.
+ * Errors: INIM_E_ARG for NULL pointers or sizes, fractions or steps out of
+ * range; INIM_E_VALUE for a negative or non-finite value.
+ */
+int inim_background_values(const float* values, int32_t T, int32_t n_regions, int32_t log2_res, double a_min,
+                           double a_max, int32_t t0, int32_t t1, double* bdv, double* area_fraction);
 
 /*
  * Create a map (Sec. 4.1 step 0: regions described by polygons; the

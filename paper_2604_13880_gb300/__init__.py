@@ -27,7 +27,7 @@ from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_FIX64, INIM_FORM_FUSED, IN
 __all__ = [
     "params", "inim_params_default", "inim_status_string", "inim_map_create", "inim_map_destroy",
     "inim_map_info", "inim_run", "inim_run_batch", "inim_raster", "inim_inims", "inim_displacement",
-    "inim_iterate", "inim_areas", "Map",
+    "inim_iterate", "inim_areas", "inim_background_values", "Map",
 ]
 
 
@@ -148,6 +148,21 @@ def inim_run_batch(jobs, stream=None):
         arr[k].stats = ctypes.pointer(stats[k])
     status = _lib.check(lib.inim_run_batch(arr, n, stream), "inim_run_batch")
     return outs, [s.as_dict() for s in stats], status
+
+
+def inim_background_values(values, log2_res: int, a_min: float, a_max: float, t0: int = 0, t1: int = -1):
+    """Background value and area fraction of every time step of a [T, R]
+    value series with dynamic area (Sec. 3.5, Eq. (Mb)); host arithmetic.
+    Returns (bdv [T], area_fraction [T]) as float64 arrays."""
+    vals = np.ascontiguousarray(values, dtype=np.float32)
+    vals = vals.reshape(1, -1) if vals.ndim == 1 else vals
+    T, R = vals.shape
+    bdv = np.empty(T, np.float64)
+    frac = np.empty(T, np.float64)
+    _lib.check(_lib.load().inim_background_values(_lib.ptr(vals), T, R, log2_res, float(a_min), float(a_max),
+                                                  t0, t1, _lib.ptr(bdv), _lib.ptr(frac)),
+               "inim_background_values")
+    return bdv, frac
 
 
 def inim_raster(m: Map, xy, log2_res: int, labels, counts, stream=None) -> int:

@@ -36,7 +36,7 @@ class inim_params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("form", ctypes.c_int32),
         ("warm_start", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("bdv_value", ctypes.c_float),
     ]
 
 
@@ -82,6 +82,9 @@ _SIGS = {
     "inim_params_default": (None, [ctypes.POINTER(inim_params)]),
     "inim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "inim_last_error": (ctypes.c_char_p, []),
+    "inim_background_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
     "inim_map_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_void_p)]),

@@ -742,6 +742,7 @@ int check_params(const inim_params* p) {
     if (p->log2_res < kMinLog2 || p->log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
     if (!(p->shape >= 0.0f && p->shape < 1.0f)) return fail(INIM_E_ARG, "shape must be in [0, 1)");
     if (!(p->bdv_scale > 0.0f) || !std::isfinite(p->bdv_scale)) return fail(INIM_E_ARG, "bdv_scale must be > 0");
+    if (!(p->bdv_value >= 0.0f) || !std::isfinite(p->bdv_value)) return fail(INIM_E_ARG, "bdv_value must be finite and >= 0");
     if (p->max_iters < 1) return fail(INIM_E_ARG, "max_iters must be >= 1");
     if (p->precision < INIM_FP32 || p->precision > INIM_KAHAN) return fail(INIM_E_ARG, "bad precision");
     if (p->form != INIM_FORM_FUSED && p->form != INIM_FORM_PLAIN) return fail(INIM_E_ARG, "bad form");
@@ -844,6 +845,7 @@ int run_series_impl(const inim_series* S, int n) {
         Job& J = B.h_jobs[k];
         J.lam = 1.0f - x.params.shape;
         J.bdv_scale = x.params.bdv_scale;
+        J.bdv_value = x.params.bdv_value;
         const int R = x.map->n_regions, V = x.map->n_verts;
         CUDA_TRY(cudaMemcpyAsync(B.bufs[k].values, x.values + (size_t)t * R, (size_t)R * 4, cudaMemcpyDefault, B.stream));
         if (reset_xy)
@@ -1066,6 +1068,35 @@ const char* inim_status_string(int s) {
 
 const char* inim_last_error(void) { return g_last_error.c_str(); }
 
+// Eq. (Mb) of Sec. 3.5, host arithmetic in double: the global integral of
+// each step, its extremes over the selected steps, the interpolated area
+// fraction, the background mass and its spread over the background pixels.
+int inim_background_values(const float* values, int32_t T, int32_t n_regions, int32_t log2_res, double a_min,
+                           double a_max, int32_t t0, int32_t t1, double* bdv, double* area_fraction) {
+    if (!values || !bdv || T < 1 || n_regions < 1) return fail(INIM_E_ARG, "bad arguments to inim_background_values");
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
+    if (!(a_min > 0.0 && a_min < a_max && a_max < 1.0)) return fail(INIM_E_ARG, "need 0 < a_min < a_max < 1");
+    if (t1 < 0) t1 = T - 1;
+    if (t0 < 0 || t0 > t1 || t1 >= T) return fail(INIM_E_ARG, "need 0 <= t0 <= t1 < T");
+    if (int st = check_values(values, (size_t)T * n_regions)) return st;
+    std::vector<double> mi((size_t)T, 0.0);
+    for (int t = 0; t < T; ++t)
+        for (int v = 0; v < n_regions; ++v) mi[t] += (double)values[(size_t)t * n_regions + v];
+    double m_min = mi[t0], m_max = mi[t0];
+    for (int t = t0; t <= t1; ++t) { m_min = std::min(m_min, mi[t]); m_max = std::max(m_max, mi[t]); }
+    const double npx = (double)(1 << log2_res) * (double)(1 << log2_res);
+    for (int t = 0; t < T; ++t) {
+        // weight of a_max; steps outside [t0, t1] are clipped to the ends
+        double w = 1.0;
+        if (m_max > m_min) w = std::min(1.0, std::max(0.0, (mi[t] - m_min) / (m_max - m_min)));
+        const double a = (1.0 - w) * a_min + w * a_max;
+        const double m_b = mi[t] * (1.0 - a) / a;           // background mass
+        bdv[t] = m_b / ((1.0 - a) * npx);                   // per background pixel of the target
+        if (area_fraction) area_fraction[t] = a;
+    }
+    return INIM_OK;
+}
+
 int inim_map_create(const float* xy, int32_t n_verts, const int32_t* ring_off, int32_t n_rings,
                     const int32_t* ring_idx, const int32_t* ring_region, int32_t n_regions, int32_t flags,
                     inim_map** out) {
@@ -1212,6 +1243,7 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
             Job& J = B->h_jobs[k];
             J.lam = 1.0f - params->shape;
             J.bdv_scale = params->bdv_scale;
+            J.bdv_value = params->bdv_value;
             CUDA_TRY(cudaMemcpyAsync(B->bufs[k].values, values + (size_t)step * R, R * 4, cudaMemcpyDefault, B->stream));
             const bool reset = direct || t == 0;
             if (reset) CUDA_TRY(cudaMemcpyAsync(B->bufs[k].xy, start, (size_t)V * 8, cudaMemcpyDefault, B->stream));
@@ -1300,6 +1332,7 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
         Job& J = B->h_jobs[k];
         J.lam = 1.0f - j.params.shape;
         J.bdv_scale = j.params.bdv_scale;
+        J.bdv_value = j.params.bdv_value;
         CUDA_TRY(cudaMemcpyAsync(B->bufs[k].values, j.values, (size_t)j.map->n_regions * 4, cudaMemcpyDefault, B->stream));
         CUDA_TRY(cudaMemcpyAsync(B->bufs[k].xy, start_ptr[k], (size_t)j.map->n_verts * 8, cudaMemcpyDefault, B->stream));
         B->h_states[k] = initial_state(j.params, 1, j.params.max_iters);
@@ -1334,6 +1367,7 @@ int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t
     B->h_states[0] = initial_state(p, 0, 1);
     B->h_jobs[0].lam = 1.0f;
     B->h_jobs[0].bdv_scale = 1.0f;
+    B->h_jobs[0].bdv_value = 0.0f;
     const int R = map->n_regions;
     const int n = 1 << log2_res;
     std::vector<float> ones(R, 1.0f);
@@ -1368,6 +1402,7 @@ int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, 
     inim_params_default(&p);
     B->h_states[0] = initial_state(p, 0, 1);
     B->h_jobs[0].bdv_scale = 1.0f;
+    B->h_jobs[0].bdv_value = 0.0f;
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].values, values, (size_t)map->n_regions * 4, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, xy, (size_t)map->n_verts * 8, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->d_jobs, B->h_jobs.data(), sizeof(Job), cudaMemcpyHostToDevice, B->stream));
@@ -1460,6 +1495,7 @@ int inim_iterate(const inim_map* map, float* xy, const float* values, const inim
     Job& J = B->h_jobs[0];
     J.lam = 1.0f - params->shape;
     J.bdv_scale = params->bdv_scale;
+    J.bdv_value = params->bdv_value;
     B->h_states[0] = initial_state(*params, 0, std::max(n_iters, 1));
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].values, hv.data(), hv.size() * 4, cudaMemcpyHostToDevice, B->stream));
     CUDA_TRY(cudaMemcpyAsync(B->bufs[0].xy, hxy.data(), hxy.size() * 4, cudaMemcpyHostToDevice, B->stream));
@@ -1543,6 +1579,7 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
         const inim_job& j = jobs[k];
         B.h_jobs[k].lam = 1.0f - j.params.shape;
         B.h_jobs[k].bdv_scale = j.params.bdv_scale;
+        B.h_jobs[k].bdv_value = j.params.bdv_value;
         CUDA_TRY(cudaMemcpyAsync(B.bufs[k].values, j.values, (size_t)j.map->n_regions * 4, cudaMemcpyDefault, B.stream));
         CUDA_TRY(cudaMemcpyAsync(B.bufs[k].xy, j.init_xy ? j.init_xy : j.map->h_xy0.data(),
                                  (size_t)j.map->n_verts * 8, cudaMemcpyDefault, B.stream));

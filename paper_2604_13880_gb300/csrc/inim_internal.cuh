@@ -67,6 +67,7 @@ struct Job {
     const float* values;       // [n_regions] s(v)
     float lam;                 // blend weight = 1 - shape
     float bdv_scale;
+    float bdv_value;           // > 0: background value in value units (Eq. (Mb)), else bdv_scale * d0
     int   precision;           // INIM_FP32 / INIM_FIX64 / INIM_KAHAN
     int   fuse_table;          // 1: the scan's first phase builds the density table (no density kernel)
     int   pdl_early;           // 1: let the next kernel launch at this kernel's start (see pdl_start)

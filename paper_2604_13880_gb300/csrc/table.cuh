@@ -1,7 +1,9 @@
 // The region density table of Sec. 4.1 step 3, built by one block from the
 // pixel counts o(v) of the raster and the values s(v):
 //   d0 = sum_{o(v) > 0} s(v) / sum_v o(v)          (area-weighted mean density)
-//   dens(v) = s(v) / (o(v) d0) for o(v) > 0, else 0; dens(R) = bdv_scale
+//   dens(v) = s(v) / (o(v) d0) for o(v) > 0, else 0;
+//   dens(R) = bdv_scale, or bdv_value / d0 for a given background value
+//   (value units per pixel: the dynamic-area background of Eq. (Mb))
 // (an empty map, sum o = 0: d0 = 1 and dens(R) = 1).  Used by the density
 // kernel and, fused, by every band block of the scan's first phase, so it
 // keeps its dependent chain short: every region's value and count are loaded
@@ -30,6 +32,7 @@ struct TableSums {
     float hi, lo;    // sum of s(v) over regions with pixels, hi + lo
     int o;           // pixels inside regions
     float d0;        // (hi + lo) / o, 1 for an empty map
+    float dbg;       // background entry dens(R)
     int fix_bits;
     int bad;         // a value is negative, NaN or infinite
 };
@@ -44,11 +47,11 @@ __device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
 }
 
 // Fraction bits of the fixed-point InIms: every InIm magnitude is at most
-// C' = sum o + bdv_scale o_bg (in units of d0), and C' < 2^e leaves 61 - e
+// C' = sum o + dens(R) o_bg (in units of d0), and C' < 2^e leaves 61 - e
 // (the factor 1.0001 covers the FP32 rounding of C').
-__device__ __forceinline__ int table_fix_bits(const Job& J, int o) {
+__device__ __forceinline__ int table_fix_bits(const Job& J, int o, float dbg) {
     const int npx = J.n * J.n;
-    const float cbound = o == 0 ? (float)npx : __fadd_rn((float)o, __fmul_rn(J.bdv_scale, (float)(npx - o)));
+    const float cbound = o == 0 ? (float)npx : __fadd_rn((float)o, __fmul_rn(dbg, (float)(npx - o)));
     int e = 0;
     frexpf(__fadd_rn(__fmul_rn(cbound, 1.0001f), 1.0f), &e);
     const int fb = 61 - e;
@@ -127,7 +130,8 @@ __device__ inline TableSums region_table(const Job& J, float* table, bool lead) 
             const float r = __fadd_rn(__fmaf_rn(-q, of, t.hi), t.lo);
             t.d0 = __fadd_rn(q, __fdiv_rn(r, of));
         }
-        t.fix_bits = table_fix_bits(J, t.o);
+        t.dbg = t.o == 0 ? 1.0f : (J.bdv_value > 0.0f ? __fdiv_rn(J.bdv_value, t.d0) : J.bdv_scale);
+        t.fix_bits = table_fix_bits(J, t.o, t.dbg);
         t.bad = bad;
         tot = t;
     }
@@ -151,9 +155,8 @@ __device__ inline TableSums region_table(const Job& J, float* table, bool lead) 
         for (int v = tid; v < R; v += nt) entry(v, J.values[v], __ldcg(J.counts + v));
     }
     if (tid == 0) {
-        const float dbg = empty ? 1.0f : J.bdv_scale;
-        table[R] = dbg;
-        if (publish) J.dens[R] = dbg;
+        table[R] = t.dbg;
+        if (publish) J.dens[R] = t.dbg;
         if (lead) table_state(J, t);
     }
     return t;
@@ -171,7 +174,7 @@ __device__ inline void table_state(const Job& J, const TableSums& t) {
     const bool empty = (t.o == 0);
     const double s = (double)t.hi + (double)t.lo;
     st->d0 = empty ? 1.0 : s / (double)t.o;
-    st->bdv_abs = (double)J.bdv_scale * st->d0;
+    st->bdv_abs = J.bdv_value > 0.0f ? (double)J.bdv_value : (double)J.bdv_scale * st->d0;
     st->mass = empty ? 1.0 : s + st->bdv_abs * (double)o_bg;
     st->mass_it[st->raster_it & 1] = st->mass;
     st->raster_it += 1;

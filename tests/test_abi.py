@@ -40,13 +40,14 @@ def test_struct_layout_matches_header(tmp_path):
     from paper_2604_13880_gb300 import _lib
     src = tmp_path / "t.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "inim.h"\n'
-                   'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(inim_params), sizeof(inim_step_stats),'
-                   ' sizeof(inim_job), offsetof(inim_job, params), offsetof(inim_params, form));return 0;}\n')
+                   'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(inim_params), sizeof(inim_step_stats),'
+                   ' sizeof(inim_job), offsetof(inim_job, params), offsetof(inim_params, form),'
+                   ' offsetof(inim_params, bdv_value));return 0;}\n')
     exe = tmp_path / "t"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
     want = [ctypes.sizeof(_lib.inim_params), ctypes.sizeof(_lib.inim_step_stats), ctypes.sizeof(_lib.inim_job),
-            _lib.inim_job.params.offset, _lib.inim_params.form.offset]
+            _lib.inim_job.params.offset, _lib.inim_params.form.offset, _lib.inim_params.bdv_value.offset]
     assert got == want
 
 
@@ -78,3 +79,23 @@ def test_map_argument_checks(lib):
     assert lib.inim_map_create(nan.ctypes.data, 3, off.ctypes.data, 1, idx.ctypes.data, reg.ctypes.data,
                                1, 0, ctypes.byref(h)) == -1
     assert b"range" in lib.inim_last_error() or b"coordinates" in lib.inim_last_error()
+
+
+def test_background_values_match_the_oracle(lib):
+    # Eq. (Mb) is host arithmetic in the library: checked against the oracle
+    import paper_2604_13880_gb300 as P
+    from oracle import inim_oracle as O
+    vals = np.random.default_rng(21).lognormal(0.0, 1.0, (11, 17)).astype(np.float32)
+    for a_min, a_max, t0, t1 in [(0.2, 0.9, 0, None), (0.35, 0.6, 3, 7), (0.1, 0.15, 5, 5)]:
+        got, frac = P.inim_background_values(vals, 10, a_min, a_max, t0, -1 if t1 is None else t1)
+        want, _, a_i = O.background_values(vals.astype(np.float64), 10, a_min, a_max, t0, t1)
+        np.testing.assert_allclose(got, want, rtol=1e-12)
+        np.testing.assert_allclose(frac, a_i, rtol=1e-14)
+    with pytest.raises(P.InimError):
+        P.inim_background_values(vals, 10, 0.6, 0.4)
+    with pytest.raises(P.InimError):
+        P.inim_background_values(vals, 10, 0.2, 0.9, 6, 2)
+    bad = vals.copy()
+    bad[2, 3] = -1.0
+    with pytest.raises(P.InimError):
+        P.inim_background_values(bad, 10, 0.2, 0.9)

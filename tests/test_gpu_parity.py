@@ -586,6 +586,60 @@ def test_cumulative_series_with_stop_rule_on_device():
 
 
 # ---------------------------------------------------------------------------
+# A11: dynamic-area background value (Sec. 3.5, Eq. (Mb))
+# ---------------------------------------------------------------------------
+def test_dynamic_area_direct_series_matches_oracle():
+    """Each step's background value from Eq. (Mb) (host), passed per solve as
+    bdv_value: the batch of direct steps follows the oracle's run with the
+    same area fractions (N-iteration bound), and one iteration through the
+    single-step call stays within the one-iteration bound."""
+    mesh = synth.voronoi_map(30, 1500, seed=35)
+    vals = synth.random_walk_values(30, 3, seed=36).astype(np.float32)
+    a_min, a_max, iters = 0.45, 0.65, 4
+    bdv, frac = P.inim_background_values(vals, 8, a_min, a_max)
+    m = P.inim_map_create(mesh)
+    base = mesh.verts_f32().astype(np.float64)
+
+    def prm(t, it):
+        return P.params(log2_res=8, shape=0.25, max_iters=it, xi_stop=0.0, stall_window=0,
+                        bdv_value=float(bdv[t]))
+
+    outs, stats, _ = P.inim_run_batch([dict(map=m, values=vals[t], params=prm(t, iters)) for t in range(3)])
+    ora, ostats = O.run(mesh.with_verts(base), vals.astype(np.float64), 8, shape=0.25, max_iters=iters,
+                        xi_stop=0, stall_window=0, area_fractions=(a_min, a_max))
+    for t in range(3):
+        assert stats[t]["iters"] == iters
+        assert np.abs(outs[t] - ora[t]).max() <= 1e-4 * EXTENT, t
+        assert abs(stats[t]["eps"] - ostats[t]["eps"]) <= 2e-3 and abs(stats[t]["xi"] - ostats[t]["xi"]) <= 2e-3
+    # the background value changes the solution: the default background differs
+    plain, _, _ = P.inim_run_batch([dict(map=m, values=vals[2], params=P.params(
+        log2_res=8, shape=0.25, max_iters=iters, xi_stop=0.0, stall_window=0))])
+    assert np.abs(plain[0] - outs[2]).max() > 1e-3
+    x = dev(mesh.verts_f32())
+    P.inim_iterate(m, x, dev(vals[1]), prm(1, 1), 1)
+    want, _ = O.iterate(base, arrays(mesh), vals[1].astype(np.float64), 8, 0.25,
+                        bdv_abs=float(np.float32(bdv[1])))
+    assert np.abs(x.cpu().numpy() - want).max() <= 1e-5 * EXTENT
+
+
+def test_dynamic_area_map_at_its_target_fraction_does_not_move():
+    """A map covering exactly the target fraction with values proportional to
+    its pixel counts has one density everywhere once the background value is
+    the equalised density: the InIm field is zero and no vertex moves."""
+    lo, side = 64, 128                                  # 128^2 of 256^2 pixels: fraction 1/4
+    a, mid, b = lo / 256, (lo + side // 2) / 256, (lo + side) / 256
+    mesh = synth.square_map([(a, a, mid, b), (mid, a, b, b)])
+    _, cnt, _ = O.labels_scanline(mesh.verts.astype(np.float64), *arrays(mesh), 8)
+    assert cnt.sum() == side * side
+    c = 3.5
+    vals = (c * cnt).astype(np.float32)
+    m = P.inim_map_create(mesh)
+    x = dev(mesh.verts_f32())
+    P.inim_iterate(m, x, dev(vals), P.params(log2_res=8, shape=0.0, bdv_value=c), 3)
+    assert np.abs(x.cpu().numpy() - mesh.verts).max() <= 1e-6
+
+
+# ---------------------------------------------------------------------------
 # A9: precision study at 4096^2 (values over six decades), a few iterations
 # ---------------------------------------------------------------------------
 @pytest.mark.slow
