@@ -209,6 +209,40 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream);
  */
 int inim_run_series(const inim_series* series, int32_t n_series, void* stream);
 
+/* Geographic quality of a cartogram against its original map (Sec. 3.3). */
+typedef struct {
+    double  tau;          /* topology distortion 1 - |E_c & E_m| / |E_c | E_m| (0 if both empty) */
+    double  shape;        /* mean shape distortion over regions with pixels in both rasters */
+    double  rel_pos;      /* relative position error R in [0, 1] */
+    int64_t adj_map;      /* adjacent region pairs |E_m| */
+    int64_t adj_cart;     /* |E_c| */
+    int64_t adj_both;     /* |E_c & E_m| */
+    int32_t n_present;    /* regions with pixels in both rasters */
+    int32_t pad;
+} inim_quality_out;
+
+/*
+ * Quality measures of Sec. 3.3, comparing the map at xy_map (NULL: the map's
+ * own vertices) with the cartogram at xy_cart ([n_verts*2], host or device),
+ * both rasterised at N = 2^log2_res:
+ *   tau       regions are adjacent when two of their pixels are 4-neighbours;
+ *   shape     per region, |P_m sym-diff P_c| / |P_m union P_c| of its pixel
+ *             sets, minimised over whole-pixel translations; a region without
+ *             pixels in either raster scores 1 and is left out of the mean;
+ *   rel_pos   mean over ordered region pairs of the angle between the vectors
+ *             joining their barycentres (polygon area centroids) in the two
+ *             maps, over pi.
+ *   shape_per [n_regions] host out per-region shape distortion, or NULL.
+ * Works in device memory of its own: two R x R bit adjacency tables and the
+ * bounding-box masks of every region.  The shape search visits every
+ * translation of a region's two masks, O(sum over regions of
+ * (w_m + w_c)(h_m + h_c) h w / 32) word operations.  Errors: INIM_E_ARG for
+ * NULL map/xy_cart/out or a resolution out of range; INIM_E_CAPACITY when
+ * the translation work does not fit one launch.
+ */
+int inim_quality(const inim_map* map, const float* xy_map, const float* xy_cart, int32_t log2_res,
+                 inim_quality_out* out, double* shape_per, void* stream);
+
 /* Use (1, default) or skip (0) the persistent launch for small batches. */
 int inim_set_persistent(int32_t enable);
 

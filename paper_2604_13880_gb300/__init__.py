@@ -27,7 +27,7 @@ from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_FIX64, INIM_FORM_FUSED, IN
 __all__ = [
     "params", "inim_params_default", "inim_status_string", "inim_map_create", "inim_map_destroy",
     "inim_map_info", "inim_run", "inim_run_batch", "inim_raster", "inim_inims", "inim_displacement",
-    "inim_iterate", "inim_areas", "inim_background_values", "Map",
+    "inim_iterate", "inim_areas", "inim_background_values", "inim_quality", "Map",
 ]
 
 
@@ -148,6 +148,25 @@ def inim_run_batch(jobs, stream=None):
         arr[k].stats = ctypes.pointer(stats[k])
     status = _lib.check(lib.inim_run_batch(arr, n, stream), "inim_run_batch")
     return outs, [s.as_dict() for s in stats], status
+
+
+def inim_quality(m: Map, xy_cart, log2_res: int, xy_map=None, stream=None):
+    """Quality measures of Sec. 3.3 of the cartogram at xy_cart against the map
+    at xy_map (None: the map's own vertices), rasterised at 2^log2_res.
+    Returns (dict of tau, shape, rel_pos, adj_map, adj_cart, adj_both,
+    n_present; per-region shape distortion [R] float64)."""
+    def prep(a):
+        if a is None or hasattr(a, "data_ptr"):
+            return a
+        return np.ascontiguousarray(a, dtype=np.float32)
+    xc, xm = prep(xy_cart), prep(xy_map)
+    out = _lib.inim_quality_out()
+    per = np.empty(m.n_regions, np.float64)
+    _lib.check(_lib.load().inim_quality(m.handle, _lib.ptr(xm), _lib.ptr(xc), log2_res, ctypes.byref(out),
+                                        _lib.ptr(per), stream if stream is not None else _lib.stream_of(xc, xm)),
+               "inim_quality")
+    res = {k: getattr(out, k) for k in ("tau", "shape", "rel_pos", "adj_map", "adj_cart", "adj_both", "n_present")}
+    return res, per
 
 
 def inim_background_values(values, log2_res: int, a_min: float, a_max: float, t0: int = 0, t1: int = -1):

@@ -40,6 +40,19 @@ class inim_params(ctypes.Structure):
     ]
 
 
+class inim_quality_out(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.c_double),
+        ("shape", ctypes.c_double),
+        ("rel_pos", ctypes.c_double),
+        ("adj_map", ctypes.c_int64),
+        ("adj_cart", ctypes.c_int64),
+        ("adj_both", ctypes.c_int64),
+        ("n_present", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+    ]
+
+
 class inim_step_stats(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int32),
@@ -107,6 +120,8 @@ _SIGS = {
     "inim_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(inim_params),
                                     ctypes.c_int32, ctypes.POINTER(inim_step_stats), ctypes.c_void_p]),
     "inim_areas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "inim_quality": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                    ctypes.POINTER(inim_quality_out), ctypes.c_void_p, ctypes.c_void_p]),
     "inim_inims_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "inim_density_pooled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,

@@ -49,6 +49,25 @@ void dfree(T*& p) {
     p = nullptr;
 }
 
+// device allocations of one call, freed on every return path
+struct DevScratch {
+    std::vector<void*> p;
+    DevScratch() = default;
+    DevScratch(const DevScratch&) = delete;
+    DevScratch& operator=(const DevScratch&) = delete;
+    ~DevScratch() {
+        for (void* q : p) cudaFree(q);
+    }
+    template <class T>
+    cudaError_t get(T** out, size_t bytes) {
+        void* q = nullptr;
+        const cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+        if (e == cudaSuccess) p.push_back(q);
+        *out = (T*)q;
+        return e;
+    }
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1535,6 +1554,127 @@ int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream
     CUDA_TRY(launch_areas_errors(B->d_jobs, B->region_blocks, -1, B->stream));
     CUDA_TRY(cudaMemcpyAsync(areas, B->bufs[0].areas, (size_t)map->n_regions * 8, cudaMemcpyDefault, B->stream));
     CUDA_TRY(cudaStreamSynchronize(B->stream));
+    return INIM_OK;
+}
+
+// Quality measures of Sec. 3.3: both rasters through inim_raster, then the
+// kernels of quality.cu on the caller's stream; the bounding boxes come back
+// to the host once to lay out the shape masks and the translation work.
+int inim_quality(const inim_map* map, const float* xy_map, const float* xy_cart, int32_t log2_res,
+                 inim_quality_out* out, double* shape_per, void* stream) {
+    if (!map || !xy_cart || !out) return fail(INIM_E_ARG, "NULL map, xy_cart or out");
+    if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
+    const int R = map->n_regions, V = map->n_verts, n = 1 << log2_res;
+    const size_t np = (size_t)n * n;
+    const cudaStream_t s = (cudaStream_t)stream;
+    DevScratch w;
+    uint16_t* lab[2];
+    int* cnt[2];
+    const float* xy[2] = {xy_map ? xy_map : (const float*)map->xy0, xy_cart};
+    for (int r = 0; r < 2; ++r) {
+        CUDA_TRY(w.get(&lab[r], np * 2));
+        CUDA_TRY(w.get(&cnt[r], (size_t)(R + 1) * 4));
+        const int st = inim_raster(map, xy[r], log2_res, lab[r], cnt[r], nullptr, stream);
+        if (st < 0) return st;
+    }
+    // topology: one adjacency bitmap per raster, then the four pair counts
+    const long long nw = ((long long)R * R + 31) / 32;
+    uint32_t* bits[2];
+    unsigned long long* pc;
+    for (int r = 0; r < 2; ++r) {
+        CUDA_TRY(w.get(&bits[r], (size_t)nw * 4));
+        CUDA_TRY(cudaMemsetAsync(bits[r], 0, (size_t)nw * 4, s));
+        CUDA_TRY(launch_adjacency(lab[r], log2_res, R, bits[r], s));
+    }
+    CUDA_TRY(w.get(&pc, 4 * sizeof(unsigned long long)));
+    CUDA_TRY(cudaMemsetAsync(pc, 0, 4 * sizeof(unsigned long long), s));
+    CUDA_TRY(launch_pair_counts(bits[0], bits[1], nw, pc, s));
+    // shape: bounding boxes, mask layout and translation chunks
+    int* box[2];
+    std::vector<int> hb[2];
+    for (int r = 0; r < 2; ++r) {
+        CUDA_TRY(w.get(&box[r], (size_t)R * 16));
+        CUDA_TRY(launch_bbox(lab[r], log2_res, R, box[r], s));
+        hb[r].resize((size_t)R * 4);
+        CUDA_TRY(cudaMemcpyAsync(hb[r].data(), box[r], (size_t)R * 16, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<QRegion> reg((size_t)R);
+    std::vector<int2> items;
+    long long words[2] = {0, 0};
+    for (int v = 0; v < R; ++v) {
+        QRegion& g = reg[v];
+        g = QRegion{};
+        if (hb[0][4 * v + 1] < 0 || hb[1][4 * v + 1] < 0) continue;      // missing from a raster
+        for (int r = 0; r < 2; ++r) {
+            g.x0[r] = hb[r][4 * v + 0];
+            g.y0[r] = hb[r][4 * v + 2];
+            g.w[r] = hb[r][4 * v + 1] - g.x0[r] + 1;
+            g.h[r] = hb[r][4 * v + 3] - g.y0[r] + 1;
+            g.W[r] = (g.w[r] + 31) / 32;
+            g.off[r] = words[r];
+            words[r] += (long long)g.W[r] * g.h[r];
+        }
+        const long long ntr = (long long)(g.w[0] + g.w[1] - 1) * (g.h[0] + g.h[1] - 1);
+        const long long chunks = (ntr + kQualityChunk - 1) / kQualityChunk;
+        if ((long long)items.size() + chunks > (long long)INT_MAX)
+            return fail(INIM_E_CAPACITY, "shape distortion: too many translations for one launch");
+        for (long long c = 0; c < chunks; ++c) items.push_back(make_int2(v, (int)c));
+    }
+    QRegion* d_reg;
+    int2* d_items;
+    uint32_t* masks[2];
+    int* omax;
+    double *per, *shp;
+    CUDA_TRY(w.get(&d_reg, (size_t)R * sizeof(QRegion)));
+    CUDA_TRY(cudaMemcpyAsync(d_reg, reg.data(), (size_t)R * sizeof(QRegion), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(w.get(&d_items, items.size() * sizeof(int2)));
+    if (!items.empty())
+        CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    for (int r = 0; r < 2; ++r) {
+        CUDA_TRY(w.get(&masks[r], (size_t)words[r] * 4));
+        CUDA_TRY(cudaMemsetAsync(masks[r], 0, (size_t)words[r] * 4, s));
+        CUDA_TRY(launch_pack(lab[r], log2_res, R, d_reg, r, masks[r], s));
+    }
+    CUDA_TRY(w.get(&omax, (size_t)R * 4));
+    CUDA_TRY(cudaMemsetAsync(omax, 0, (size_t)R * 4, s));
+    CUDA_TRY(launch_correlate(d_items, (int)items.size(), d_reg, masks[0], masks[1], omax, s));
+    CUDA_TRY(w.get(&per, (size_t)R * 8));
+    CUDA_TRY(w.get(&shp, 2 * sizeof(double)));
+    CUDA_TRY(launch_shape_final(cnt[0], cnt[1], omax, R, per, shp, s));
+    // relative positions: barycentres of both vertex sets
+    float2* dxy[2];
+    double2* bary[2];
+    for (int r = 0; r < 2; ++r) {
+        if (r == 0 && !xy_map) {
+            dxy[0] = map->xy0;
+        } else {
+            CUDA_TRY(w.get(&dxy[r], (size_t)V * 8));
+            CUDA_TRY(cudaMemcpyAsync(dxy[r], xy[r], (size_t)V * 8, cudaMemcpyDefault, s));
+        }
+        CUDA_TRY(w.get(&bary[r], (size_t)R * sizeof(double2)));
+        CUDA_TRY(launch_barycentres(map->reg_ring_off, map->reg_rings, map->ring_off, map->ring_idx, dxy[r], R,
+                                    bary[r], s));
+    }
+    double *partial, *rp;
+    CUDA_TRY(w.get(&partial, (size_t)rel_pos_blocks() * 8));
+    CUDA_TRY(w.get(&rp, 8));
+    CUDA_TRY(launch_rel_pos(bary[0], bary[1], R, partial, rp, s));
+    unsigned long long hc[4];
+    double hs[2], hr;
+    CUDA_TRY(cudaMemcpyAsync(hc, pc, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hs, shp, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&hr, rp, sizeof(hr), cudaMemcpyDeviceToHost, s));
+    if (shape_per) CUDA_TRY(cudaMemcpyAsync(shape_per, per, (size_t)R * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    out->adj_map = (int64_t)hc[0];
+    out->adj_cart = (int64_t)hc[1];
+    out->adj_both = (int64_t)hc[2];
+    out->tau = hc[3] == 0 ? 0.0 : 1.0 - (double)hc[2] / (double)hc[3];
+    out->n_present = (int32_t)hs[1];
+    out->shape = hs[1] > 0.0 ? hs[0] / hs[1] : 0.0;
+    out->rel_pos = hr;
+    out->pad = 0;
     return INIM_OK;
 }
 

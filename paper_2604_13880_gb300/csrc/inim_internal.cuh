@@ -280,6 +280,31 @@ cudaError_t launch_apply_field(const Job* d_jobs, const BlockMap& vert_blocks, c
 int warmstart_predict(const float* x, int B, float* y, cudaStream_t s);
 bool warmstart_loaded();
 
+// geographic quality measures (Sec. 3.3).  Bounding-box mask layout of one
+// region in raster 0 (the map) and 1 (the cartogram): origin (x0, y0), size
+// w x h pixels, W words a row at word offset off; W = 0 when the region is
+// missing from either raster.
+struct QRegion {
+    int x0[2], y0[2], w[2], h[2], W[2];
+    long long off[2];
+};
+cudaError_t launch_adjacency(const uint16_t* lab, int log2n, int R, uint32_t* bits, cudaStream_t s);
+cudaError_t launch_pair_counts(const uint32_t* a, const uint32_t* b, long long nw, unsigned long long* out,
+                               cudaStream_t s);
+cudaError_t launch_bbox(const uint16_t* lab, int log2n, int R, int* box, cudaStream_t s);
+cudaError_t launch_pack(const uint16_t* lab, int log2n, int R, const QRegion* reg, int which, uint32_t* masks,
+                        cudaStream_t s);
+cudaError_t launch_correlate(const int2* items, int n_items, const QRegion* reg, const uint32_t* mm,
+                             const uint32_t* mc, int* omax, cudaStream_t s);
+cudaError_t launch_shape_final(const int* cm, const int* cc, const int* omax, int R, double* per, double* out,
+                               cudaStream_t s);
+cudaError_t launch_barycentres(const int* reg_ring_off, const int* reg_rings, const int* ring_off,
+                               const int* ring_idx, const float2* xy, int R, double2* bary, cudaStream_t s);
+int rel_pos_blocks();
+cudaError_t launch_rel_pos(const double2* bm, const double2* bc, int R, double* partial, double* out,
+                           cudaStream_t s);
+constexpr int kQualityChunk = 256;     // translations of one correlation block
+
 // plain (unfused) form: extra full textures of one job
 struct PlainWork {
     float*  d   = nullptr;   // [n*n] density

@@ -76,3 +76,26 @@ def test_relative_position_error_of_a_rotation(theta):
     assert Q.relative_position_error(bm, bc) == pytest.approx(abs(theta) / np.pi, rel=1e-12)
     # translation and uniform scaling keep every direction: R = 0
     assert Q.relative_position_error(bm, 2.0 * bm + 0.3) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_shape_distortion_brute_force_on_tiny_rasters():
+    # the minimum over whole-pixel translations of |P sym-diff C| / |P union C|,
+    # enumerated with explicit pixel sets on random 8 x 8 rasters
+    rng = np.random.default_rng(9)
+    for _ in range(6):
+        lm = rng.integers(-1, 3, (8, 8))
+        lc = rng.integers(-1, 3, (8, 8))
+        per, mean = Q.shape_distortion(lm, lc, 3)
+        vals = []
+        for v in range(3):
+            pm = set(zip(*np.nonzero(lm == v)))
+            pc = set(zip(*np.nonzero(lc == v)))
+            if not pm or not pc:
+                assert per[v] == 1.0
+                continue
+            best = min(len(pm ^ s) / len(pm | s)
+                       for dy in range(-8, 9) for dx in range(-8, 9)
+                       for s in [{(y + dy, x + dx) for y, x in pc}])
+            assert per[v] == pytest.approx(best, rel=1e-15)
+            vals.append(best)
+        assert mean == pytest.approx(np.mean(vals) if vals else 0.0, rel=1e-15)
