@@ -230,6 +230,36 @@ def precision_study(args):
 
 
 # ---------------------------------------------------------------------------
+# quality measures (Sec. 3.3) of the sweep's map against a cartogram of it
+# ---------------------------------------------------------------------------
+def quality_timing(args):
+    """inim_quality on the sweep's map (1024^2, 200 regions) against its
+    cartogram after 20 iterations on the last time step's values: host wall
+    time per call (both rasters, the kernels, the call's own allocations)."""
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import synth
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    m = P.inim_map_create(mesh)
+    x = torch.as_tensor(mesh.verts_f32(), device="cuda")
+    v = torch.as_tensor(w["values"][-1].astype(np.float32), device="cuda")
+    P.inim_iterate(m, x, v, P.params(log2_res=k, shape=0.5), 20)
+    res, _ = P.inim_quality(m, x, k)                       # warm
+    times = []
+    for _ in range(args.quality):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res, _ = P.inim_quality(m, x, k)
+        times.append(time.perf_counter() - t)
+    print(json.dumps({"quality": w["name"], "log2_res": k, "n_regions": mesh.n_regions, "calls": args.quality,
+                      "ms_per_call_median": 1e3 * float(np.median(times)), "ms_per_call_min": 1e3 * min(times),
+                      **res}))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # small fixed cases for profiler captures (ncu): one batch, two iterations
 # ---------------------------------------------------------------------------
 def ncu_case(args):
@@ -286,6 +316,8 @@ def main():
                     help="instead of the sweep: K iterations of the 4096^2 precision workload in FP32, "
                          "FIX64 and compensated sums; results to --study-out for the FP64 oracle comparison")
     ap.add_argument("--study-out", default="precision_study.npz")
+    ap.add_argument("--quality", type=int, default=0, metavar="K",
+                    help="instead of the sweep: time K calls of inim_quality on the sweep's map")
     ap.add_argument("--ncu-case", choices=["direct72", "chain3"], default=None,
                     help="instead of the sweep: one batch for two iterations (small profiler captures)")
     args = ap.parse_args()
@@ -296,6 +328,8 @@ def main():
         return precision_study(args)
     if args.ncu_case:
         return ncu_case(args)
+    if args.quality:
+        return quality_timing(args)
 
     import torch
     import paper_2604_13880_gb300 as P
