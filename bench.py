@@ -487,7 +487,9 @@ def main():
                        "large_band_rows_by_step_ms": {str(h): round(1e3 * t, 2) for h, t in step_times.items()}},
             "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "host_buffers": "pinned"},
-            "gpu_launches": int(launches), "wall_s_timed": wall}
+            "gpu_launches": int(launches), "wall_s_timed": wall,
+            # completed cartograms (time steps of a series, ITERS iterations each) per second
+            "frames": {"value": value / ITERS, "e2e": e2e_value / ITERS, "unit": "cartograms/s"}}
     if clk:
         line["clocks"] = clk
 

@@ -87,7 +87,7 @@ typedef struct {
     int32_t warm_start;   /* 1: move vertices by the learned field first (needs
                              inim_warmstart_load); default 0 */
     float   bdv_value;    /* > 0: background density in value units per pixel,
-                             replacing bdv_scale * d0 (dynamic area, Sec. 3.5,
+                             replacing bdv_scale * d0 (dynamic area, Sec. 4.3,
                              Eq. (Mb): one value per time step from
                              inim_background_values); default 0 (off) */
 } inim_params;
@@ -134,7 +134,7 @@ const char* inim_last_error(void);
 
 /*
  * Background values of a time series whose map area follows its global
- * integral (dynamic area, Sec. 3.5, Eq. (Mb)); host memory, no GPU work.
+ * integral (dynamic area, Sec. 4.3, Eq. (Mb)); host memory, no GPU work.
  *   values        [T*n_regions] host s_t(v) >= 0.
  *   a_min, a_max  area fractions of the map at the smallest and the largest
  *                 global integral M(t) = sum_v s_t(v) over the selected
@@ -152,6 +152,21 @@ const char* inim_last_error(void);
  */
 int inim_background_values(const float* values, int32_t T, int32_t n_regions, int32_t log2_res, double a_min,
                            double a_max, int32_t t0, int32_t t1, double* bdv, double* area_fraction);
+
+/*
+ * Values of an animation with frames_per_step frames per time step (Sec. 5.5:
+ * the in-between frames interpolate the statistical data linearly between
+ * consecutive steps, and every frame gets a cartogram of its own, e.g. one
+ * inim_run over the result); host memory, no GPU work.
+ *   values [T*n_regions] host s_t(v) >= 0.
+ *   out    [((T-1)*frames_per_step + 1)*n_regions] host: frame t f + q
+ *          (0 <= q < f) = (1 - q/f) s_t + (q/f) s_{t+1} in double, rounded to
+ *          float; the last frame is the last step.
+ * Errors: INIM_E_ARG for NULL pointers, T < 1, n_regions < 1 or
+ * frames_per_step < 1; INIM_E_VALUE for a negative or non-finite value.
+ */
+int inim_interpolate_values(const float* values, int32_t T, int32_t n_regions, int32_t frames_per_step,
+                            float* out);
 
 /*
  * Create a map (Sec. 4.1 step 0: regions described by polygons; the

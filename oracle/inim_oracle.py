@@ -391,7 +391,7 @@ def signed_areas(xy, ring_off, ring_idx, ring_region, n_regions):
 
 def background_values(values, log2_res, a_min, a_max, t0=0, t1=None):
     """Background value per time step for a map whose area follows its global
-    integral (Sec. 3.5, Eq. (Mb)).
+    integral (Sec. 4.3, Eq. (Mb)).
 
     M_i(t) = sum_v s_v(t) is the global integral; over the selected steps
     [t0, t1] its extremes M_min, M_max give the weight
@@ -420,6 +420,26 @@ def background_values(values, log2_res, a_min, a_max, t0=0, t1=None):
     N = 1 << log2_res
     bdv = m_b / ((1.0 - a_i) * N * N)
     return bdv, m_b, a_i
+
+
+def interpolate_series(values, frames_per_step):
+    """Value series of an animation with frames_per_step frames per time step
+    (Sec. 5.5: in-between frames interpolate the statistical data linearly
+    between consecutive steps; a cartogram is computed for every frame).
+    Frame t f + q (0 <= q < f) holds (1 - q/f) s_t + (q/f) s_{t+1}; the last
+    frame is the last step.  Returns [(T - 1) f + 1, R] float64."""
+    vals = np.atleast_2d(np.asarray(values, dtype=np.float64))
+    T = vals.shape[0]
+    f = int(frames_per_step)
+    if f < 1:
+        raise ValueError("frames_per_step must be >= 1")
+    out = []
+    for t in range(T - 1):
+        for q in range(f):
+            w = q / f
+            out.append((1.0 - w) * vals[t] + w * vals[t + 1])
+    out.append(vals[T - 1])
+    return np.stack(out)
 
 
 def desired_areas(values, counts, bdv, N):

@@ -27,7 +27,8 @@ from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_FIX64, INIM_FORM_FUSED, IN
 __all__ = [
     "params", "inim_params_default", "inim_status_string", "inim_map_create", "inim_map_destroy",
     "inim_map_info", "inim_run", "inim_run_batch", "inim_raster", "inim_inims", "inim_displacement",
-    "inim_iterate", "inim_areas", "inim_background_values", "inim_quality", "Map",
+    "inim_iterate", "inim_areas", "inim_background_values", "inim_interpolate_values",
+    "inim_quality", "Map",
 ]
 
 
@@ -150,6 +151,18 @@ def inim_run_batch(jobs, stream=None):
     return outs, [s.as_dict() for s in stats], status
 
 
+def inim_interpolate_values(values, frames_per_step: int):
+    """[(T - 1) f + 1, R] float32 values of an animation with f frames per
+    time step of the [T, R] series (Sec. 5.5); host arithmetic."""
+    vals = np.ascontiguousarray(values, dtype=np.float32)
+    vals = vals.reshape(1, -1) if vals.ndim == 1 else vals
+    T, R = vals.shape
+    out = np.empty(((T - 1) * frames_per_step + 1, R), np.float32)
+    _lib.check(_lib.load().inim_interpolate_values(_lib.ptr(vals), T, R, frames_per_step, _lib.ptr(out)),
+               "inim_interpolate_values")
+    return out
+
+
 def inim_quality(m: Map, xy_cart, log2_res: int, xy_map=None, stream=None):
     """Quality measures of Sec. 3.3 of the cartogram at xy_cart against the map
     at xy_map (None: the map's own vertices), rasterised at 2^log2_res.
@@ -171,7 +184,7 @@ def inim_quality(m: Map, xy_cart, log2_res: int, xy_map=None, stream=None):
 
 def inim_background_values(values, log2_res: int, a_min: float, a_max: float, t0: int = 0, t1: int = -1):
     """Background value and area fraction of every time step of a [T, R]
-    value series with dynamic area (Sec. 3.5, Eq. (Mb)); host arithmetic.
+    value series with dynamic area (Sec. 4.3, Eq. (Mb)); host arithmetic.
     Returns (bdv [T], area_fraction [T]) as float64 arrays."""
     vals = np.ascontiguousarray(values, dtype=np.float32)
     vals = vals.reshape(1, -1) if vals.ndim == 1 else vals

@@ -95,6 +95,8 @@ _SIGS = {
     "inim_params_default": (None, [ctypes.POINTER(inim_params)]),
     "inim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "inim_last_error": (ctypes.c_char_p, []),
+    "inim_interpolate_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_void_p]),
     "inim_background_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_void_p, ctypes.c_void_p]),

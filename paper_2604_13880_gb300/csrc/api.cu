@@ -1087,7 +1087,29 @@ const char* inim_status_string(int s) {
 
 const char* inim_last_error(void) { return g_last_error.c_str(); }
 
-// Eq. (Mb) of Sec. 3.5, host arithmetic in double: the global integral of
+// Frames of Sec. 5.5: linear interpolation of the values between consecutive
+// time steps, in double, rounded to float.
+int inim_interpolate_values(const float* values, int32_t T, int32_t n_regions, int32_t frames_per_step,
+                            float* out) {
+    if (!values || !out || T < 1 || n_regions < 1 || frames_per_step < 1)
+        return fail(INIM_E_ARG, "bad arguments to inim_interpolate_values");
+    if (int st = check_values(values, (size_t)T * n_regions)) return st;
+    const int f = frames_per_step;
+    size_t row = 0;
+    for (int t = 0; t + 1 < T; ++t) {
+        const float* a = values + (size_t)t * n_regions;
+        const float* b = a + n_regions;
+        for (int q = 0; q < f; ++q, ++row) {
+            const double w = (double)q / (double)f;
+            for (int v = 0; v < n_regions; ++v)
+                out[row * n_regions + v] = (float)((1.0 - w) * (double)a[v] + w * (double)b[v]);
+        }
+    }
+    std::memcpy(out + row * n_regions, values + (size_t)(T - 1) * n_regions, (size_t)n_regions * 4);
+    return INIM_OK;
+}
+
+// Eq. (Mb) of Sec. 4.3, host arithmetic in double: the global integral of
 // each step, its extremes over the selected steps, the interpolated area
 // fraction, the background mass and its spread over the background pixels.
 int inim_background_values(const float* values, int32_t T, int32_t n_regions, int32_t log2_res, double a_min,

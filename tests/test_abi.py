@@ -101,3 +101,19 @@ def test_background_values_match_the_oracle(lib):
     bad[2, 3] = -1.0
     with pytest.raises(P.InimError):
         P.inim_background_values(bad, 10, 0.2, 0.9)
+
+
+def test_interpolated_frames_match_the_oracle(lib):
+    # the frame values of Sec. 5.5 are host arithmetic in the library
+    import paper_2604_13880_gb300 as P
+    from oracle import inim_oracle as O
+    vals = np.random.default_rng(22).lognormal(0.0, 1.0, (5, 13)).astype(np.float32)
+    for f in (1, 4, 10):
+        got = P.inim_interpolate_values(vals, f)
+        want = O.interpolate_series(vals.astype(np.float64), f).astype(np.float32)
+        assert got.shape == ((5 - 1) * f + 1, 13)
+        np.testing.assert_array_equal(got, want)
+        np.testing.assert_array_equal(got[::f], vals)        # every f-th frame is a time step
+    assert P.inim_interpolate_values(vals[:1], 10).shape == (1, 13)
+    with pytest.raises(P.InimError):
+        P.inim_interpolate_values(vals, 0)

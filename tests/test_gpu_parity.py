@@ -586,7 +586,7 @@ def test_cumulative_series_with_stop_rule_on_device():
 
 
 # ---------------------------------------------------------------------------
-# A11: dynamic-area background value (Sec. 3.5, Eq. (Mb))
+# A11: dynamic-area background value (Sec. 4.3, Eq. (Mb))
 # ---------------------------------------------------------------------------
 def test_dynamic_area_direct_series_matches_oracle():
     """Each step's background value from Eq. (Mb) (host), passed per solve as

@@ -1,4 +1,4 @@
-"""Pins of the oracle's dynamic-area background (Sec. 3.5, Eq. (Mb)).
+"""Pins of the oracle's dynamic-area background (Sec. 4.3, Eq. (Mb)).
 
 The background value of a time step makes the map cover the area fraction
 A_i(t) of the domain once its density is equalised.  Pinned by what that

@@ -129,3 +129,17 @@ def test_pooled_log_density_closed_forms():
     cnt3 = np.array([128, 0])
     out3 = O.pooled_log_density(lab3, cnt3, np.array([5.0, 1.0]), 8, bdv_scale=0.25)
     assert np.allclose(out3[0], 0.0) and np.allclose(out3[1], np.log(0.25))
+
+
+def test_interpolated_frames_closed_forms():
+    # Sec. 5.5 frames: the time steps themselves every f frames, the mean of
+    # two steps half-way, a constant series stays constant
+    a = np.array([[1.0, 4.0, 0.0], [3.0, 2.0, 8.0], [3.0, 2.0, 8.0]])
+    fr = O.interpolate_series(a, 2)
+    assert fr.shape == (5, 3)
+    np.testing.assert_array_equal(fr[[0, 2, 4]], a)
+    np.testing.assert_array_equal(fr[1], [2.0, 3.0, 4.0])
+    np.testing.assert_array_equal(fr[3], a[1])
+    q = O.interpolate_series(a[:2], 4)
+    np.testing.assert_allclose(q[:, 2], [0.0, 2.0, 4.0, 6.0, 8.0], rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(O.interpolate_series(a[:1], 10), a[:1])
