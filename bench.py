@@ -260,6 +260,44 @@ def quality_timing(args):
 
 
 # ---------------------------------------------------------------------------
+# direct vs cumulative (Sec. 5.5) on a random walk with large jumps
+# ---------------------------------------------------------------------------
+def coherence_study(args):
+    """The sweep's map under T steps of a log-normal random walk with step
+    sigma --coherence-sigma, solved in both modes with the stop rule of
+    Sec. 4.1 (xi < 0.01, 32-iteration stall, 512 iterations; shape 0.5): per
+    step the iterations, eps, xi and the quality of the cartogram against the
+    original map (inim_quality: tau, shape distortion, R), and each mode's
+    wall time for the whole series."""
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import synth
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    T = args.coherence_study
+    vals = synth.random_walk_values(mesh.n_regions, T, seed=202, sigma=args.coherence_sigma).astype(np.float32)
+    m = P.inim_map_create(mesh)
+    res = {"coherence_study": w["name"], "steps": T, "sigma": args.coherence_sigma, "modes": {}}
+    for name, mode in (("direct", P.INIM_DIRECT), ("cumulative", P.INIM_CUMULATIVE)):
+        p = P.params(log2_res=k, shape=0.5, mode=mode)
+        P.inim_run(m, vals[:2], p)                         # warm: graphs, scan tiles
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out, stats, _ = P.inim_run(m, vals, p)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        steps = []
+        for s in range(T):
+            q, _ = P.inim_quality(m, out[s], k)
+            steps.append({"iters": stats[s]["iters"], "eps": stats[s]["eps"], "xi": stats[s]["xi"],
+                          "tau": q["tau"], "shape": q["shape"], "rel_pos": q["rel_pos"]})
+        res["modes"][name] = {"wall_s": dt, "iterations": int(sum(x["iters"] for x in steps)), "per_step": steps}
+    print(json.dumps(res))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # small fixed cases for profiler captures (ncu): one batch, two iterations
 # ---------------------------------------------------------------------------
 def ncu_case(args):
@@ -316,6 +354,10 @@ def main():
                     help="instead of the sweep: K iterations of the 4096^2 precision workload in FP32, "
                          "FIX64 and compensated sums; results to --study-out for the FP64 oracle comparison")
     ap.add_argument("--study-out", default="precision_study.npz")
+    ap.add_argument("--coherence-study", type=int, default=0, metavar="T",
+                    help="instead of the sweep: T steps of a random walk with large jumps in direct and "
+                         "cumulative mode with the stop rule, with per-step errors and quality measures")
+    ap.add_argument("--coherence-sigma", type=float, default=0.6)
     ap.add_argument("--quality", type=int, default=0, metavar="K",
                     help="instead of the sweep: time K calls of inim_quality on the sweep's map")
     ap.add_argument("--ncu-case", choices=["direct72", "chain3"], default=None,
@@ -330,6 +372,8 @@ def main():
         return ncu_case(args)
     if args.quality:
         return quality_timing(args)
+    if args.coherence_study:
+        return coherence_study(args)
 
     import torch
     import paper_2604_13880_gb300 as P
