@@ -24,8 +24,10 @@
  *     is queried with cudaPointerGetAttributes); "device" means device memory
  *     of the current CUDA device.  The library copies what it keeps.
  *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
- *     default stream).  Work is enqueued on it; entry points that return
- *     results through host memory synchronise that stream before returning.
+ *     default stream).  A call first waits for the work already enqueued on
+ *     it, runs on streams of the library (inim_quality: on `stream`) and
+ *     returns once its results are complete; inim_inims_noalloc instead
+ *     enqueues its kernels on `stream` and returns at once.
  *   - Return value: INIM_OK (0) on success, a negative INIM_E_* error code,
  *     or a positive INIM_W_* soft status (results are still written).
  *     Errors leave outputs unspecified; the message of the last error on the

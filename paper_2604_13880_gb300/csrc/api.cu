@@ -1260,7 +1260,7 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
         st = check_values(values, (size_t)T * R);
         if (st != INIM_OK) return st;
     }
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     const bool out_dev = is_device_ptr(out_xy);
     const float* start = init_xy ? init_xy : map->h_xy0.data();   // host or device
 
@@ -1320,7 +1320,7 @@ int inim_run_series(const inim_series* S, int32_t n, void* stream) {
             if (st != INIM_OK) return st;
         }
     }
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     return run_series_impl(S, n);
 }
@@ -1362,7 +1362,7 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
         spec[k] = JobSpec{j.map, j.params.log2_res, j.params.precision};
         poll |= needs_poll(j.params);
     }
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;
     Batch* B = get_batch(spec, &st);
@@ -1397,7 +1397,7 @@ int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t
                 int32_t* overlap, void* stream) {
     if (!map || !xy || !labels || !counts) return fail(INIM_E_ARG, "NULL argument");
     if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;
     std::vector<JobSpec> spec{JobSpec{map, log2_res, INIM_FP32}};
@@ -1433,7 +1433,7 @@ int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, 
     if (!map || !xy || !values || !out || pool < 1) return fail(INIM_E_ARG, "NULL argument");
     if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
     if (((1 << log2_res) % pool) != 0) return fail(INIM_E_ARG, "pool must divide N");
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;
     std::vector<JobSpec> spec{JobSpec{map, log2_res, INIM_FP32}};
@@ -1487,7 +1487,7 @@ int inim_inims(const float* density, int32_t log2_res, int32_t precision, int32_
     if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
     if (precision < INIM_FP32 || precision > INIM_KAHAN) return fail(INIM_E_ARG, "bad precision");
     if (precision == INIM_FIX64 && (frac_bits < 0 || frac_bits > 62)) return fail(INIM_E_ARG, "bad frac_bits");
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     Batch* B = nullptr;
     int st = texture_batch(log2_res, precision, frac_bits, density, &B);
@@ -1507,7 +1507,7 @@ int inim_displacement(const float* density, int32_t log2_res, int32_t precision,
     if (!density || !xy || !delta || n < 0) return fail(INIM_E_ARG, "bad arguments");
     if (log2_res < kMinLog2 || log2_res > kMaxLog2) return fail(INIM_E_ARG, "log2_res must be in [8, 12]");
     if (precision < INIM_FP32 || precision > INIM_KAHAN) return fail(INIM_E_ARG, "bad precision");
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     // fixed point: 2^30 units per unit density keeps 4096^2 textures of
     // densities up to 2^6 below 2^62
@@ -1524,7 +1524,7 @@ int inim_iterate(const inim_map* map, float* xy, const float* values, const inim
     if (!map || !xy || !values || n_iters < 0) return fail(INIM_E_ARG, "bad arguments");
     int st = check_params(params);
     if (st != INIM_OK) return st;
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::vector<float> hv = to_host(values, map->n_regions);
     st = check_values(hv.data(), hv.size());
     if (st != INIM_OK) return st;
@@ -1560,7 +1560,7 @@ int inim_iterate(const inim_map* map, float* xy, const float* values, const inim
 
 int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream) {
     if (!map || !xy || !areas) return fail(INIM_E_ARG, "NULL argument");
-    if (stream) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     std::vector<float> hxy = to_host(xy, (size_t)map->n_verts * 2);
     std::lock_guard<std::mutex> lk(g_cache_mu);
     int st = INIM_OK;

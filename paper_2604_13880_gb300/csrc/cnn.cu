@@ -369,7 +369,7 @@ int inim_cnn_set_params(inim_cnn* c, const float* in, long long n) {
 
 int inim_cnn_forward(inim_cnn* c, const float* x, int32_t B, float* y, void* stream) {
     if (!c || !x || !y || B < 1) return cfail(INIM_E_ARG, "bad arguments");
-    if (stream) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     int st = forward(*c, x, B);
     if (st != INIM_OK) return st;
     CK(cudaMemcpyAsync(y, c->out, (size_t)B * kRes * kRes * 2 * 4, cudaMemcpyDefault, c->stream));
@@ -380,7 +380,7 @@ int inim_cnn_forward(inim_cnn* c, const float* x, int32_t B, float* y, void* str
 int inim_cnn_gradients(inim_cnn* c, const float* x, const float* y, int32_t B, float* loss, float* grads,
                        void* stream) {
     if (!c || !x || !y || B < 1) return cfail(INIM_E_ARG, "bad arguments");
-    if (stream) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     int st = forward(*c, x, B);
     if (st == INIM_OK) st = backward(*c, y, B);
     if (st != INIM_OK) return st;
@@ -393,7 +393,7 @@ int inim_cnn_gradients(inim_cnn* c, const float* x, const float* y, int32_t B, f
 int inim_cnn_train_step(inim_cnn* c, const float* x, const float* y, int32_t B, float lr, float* loss,
                         void* stream) {
     if (!c || !x || !y || B < 1 || !(lr > 0.0f)) return cfail(INIM_E_ARG, "bad arguments");
-    if (stream) CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
     int st = forward(*c, x, B);
     if (st == INIM_OK) st = backward(*c, y, B);
     if (st != INIM_OK) return st;
