@@ -117,3 +117,12 @@ def test_interpolated_frames_match_the_oracle(lib):
     assert P.inim_interpolate_values(vals[:1], 10).shape == (1, 13)
     with pytest.raises(P.InimError):
         P.inim_interpolate_values(vals, 0)
+
+
+def test_quality_argument_checks(lib):
+    # rejected before any device work
+    from paper_2604_13880_gb300 import _lib
+    out = _lib.inim_quality_out()
+    xy = np.zeros((3, 2), np.float32)
+    assert lib.inim_quality(None, None, xy.ctypes.data, 8, ctypes.byref(out), None, None) == -1
+    assert b"NULL" in lib.inim_last_error()
