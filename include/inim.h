@@ -218,11 +218,12 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream);
 /*
  * Many time series at once (Sec. 4.2 direct and cumulative modes).  Direct
  * series run as independent solves of one batch; cumulative series run
- * their steps in order, all series together.  Small FP32 batches (N <= 2048,
- * fewer than 2^23 pixels in total) run in one persistent cooperative launch
- * that covers every iteration and, for cumulative series, every time step;
- * larger ones as CUDA graphs of the per-step kernels.  All series need the
- * fused form and one precision.  inim_run is this call with one series.
+ * their steps in order, all series together.  Every batch runs as CUDA
+ * graphs of the per-iteration kernels; with inim_set_persistent(1), small
+ * FP32 batches (N <= 2048, fewer than 2^23 pixels in total) run instead in
+ * one persistent cooperative launch that covers every iteration and, for
+ * cumulative series, every time step.  All series need the fused form and
+ * one precision.  inim_run is this call with one series.
  */
 int inim_run_series(const inim_series* series, int32_t n_series, void* stream);
 
@@ -260,7 +261,7 @@ typedef struct {
 int inim_quality(const inim_map* map, const float* xy_map, const float* xy_cart, int32_t log2_res,
                  inim_quality_out* out, double* shape_per, void* stream);
 
-/* Use (1, default) or skip (0) the persistent launch for small batches. */
+/* Use (1) or skip (0, default) the persistent launch for small batches. */
 int inim_set_persistent(int32_t enable);
 
 /*
