@@ -208,6 +208,21 @@ int inim_run(inim_map* map, const float* values, int32_t T, const inim_params* p
              const float* init_xy, float* out_xy, inim_step_stats* stats, void* stream);
 
 /*
+ * A time series whose map area follows its global integral (dynamic area,
+ * Sec. 4.3, Eq. (Mb)): the background value of every step is computed as by
+ * inim_background_values(values, T, n_regions, params->log2_res, a_min,
+ * a_max, t0, t1) and each step is solved with it as params.bdv_value.
+ * params->mode INIM_DIRECT: one batch of T independent solves;
+ * INIM_CUMULATIVE: the steps in order, each from the previous step's
+ * vertices (one inim_run_batch call per step).  values are host memory;
+ * the other arguments are those of inim_run.  Returns the worst per-step
+ * status; the errors of inim_background_values and inim_run_batch.
+ */
+int inim_run_dynamic(inim_map* map, const float* values, int32_t T, const inim_params* params, double a_min,
+                     double a_max, int32_t t0, int32_t t1, const float* init_xy, float* out_xy,
+                     inim_step_stats* stats, void* stream);
+
+/*
  * Many independent single-step solves of possibly different maps and
  * resolutions in one batched launch sequence captured in a CUDA graph
  * (params.form must be INIM_FORM_FUSED).  Jobs run together until each one's

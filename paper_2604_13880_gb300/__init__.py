@@ -27,7 +27,7 @@ from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_FIX64, INIM_FORM_FUSED, IN
 __all__ = [
     "params", "inim_params_default", "inim_status_string", "inim_map_create", "inim_map_destroy",
     "inim_map_info", "inim_run", "inim_run_batch", "inim_raster", "inim_inims", "inim_displacement",
-    "inim_iterate", "inim_areas", "inim_background_values", "inim_interpolate_values",
+    "inim_iterate", "inim_areas", "inim_background_values", "inim_interpolate_values", "inim_run_dynamic",
     "inim_quality", "Map",
 ]
 
@@ -118,6 +118,25 @@ def inim_run(m: Map, values, p: inim_params, init_xy=None, out_xy=None, stream=N
     s = stream if stream is not None else _lib.stream_of(values, init_xy, out_xy)
     status = _lib.check(lib.inim_run(m.handle, _lib.ptr(values), T, ctypes.byref(p), _lib.ptr(init_xy),
                                      _lib.ptr(out_xy), st, s), "inim_run")
+    return out_xy, [x.as_dict() for x in st], status
+
+
+def inim_run_dynamic(m: Map, values, p: inim_params, a_min: float, a_max: float, t0: int = 0, t1: int = -1,
+                     init_xy=None, out_xy=None, stream=None):
+    """Time-varying run with dynamic area (Eq. (Mb)): host values [T, R];
+    returns (out_xy [T, V, 2], stats list, status) like inim_run."""
+    lib = _lib.load()
+    values = np.ascontiguousarray(np.atleast_2d(values), dtype=np.float32)
+    T = int(values.shape[0])
+    if init_xy is not None and isinstance(init_xy, np.ndarray):
+        init_xy = np.ascontiguousarray(init_xy, dtype=np.float32)
+    if out_xy is None:
+        out_xy = np.empty((T, m.n_verts, 2), np.float32)
+    st = _stats_array(T)
+    s = stream if stream is not None else _lib.stream_of(init_xy, out_xy)
+    status = _lib.check(lib.inim_run_dynamic(m.handle, _lib.ptr(values), T, ctypes.byref(p), float(a_min),
+                                             float(a_max), t0, t1, _lib.ptr(init_xy), _lib.ptr(out_xy), st, s),
+                        "inim_run_dynamic")
     return out_xy, [x.as_dict() for x in st], status
 
 

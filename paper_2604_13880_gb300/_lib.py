@@ -109,6 +109,10 @@ _SIGS = {
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(inim_step_stats),
                                 ctypes.c_void_p]),
     "inim_run_batch": (ctypes.c_int, [ctypes.POINTER(inim_job), ctypes.c_int32, ctypes.c_void_p]),
+    "inim_run_dynamic": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(inim_params),
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(inim_step_stats),
+                                        ctypes.c_void_p]),
     "inim_run_series": (ctypes.c_int, [ctypes.POINTER(inim_series), ctypes.c_int32, ctypes.c_void_p]),
     "inim_set_persistent": (ctypes.c_int, [ctypes.c_int32]),
     "inim_persistent_phase_times": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),

@@ -1393,6 +1393,44 @@ int inim_run_batch(const inim_job* jobs, int32_t n_jobs, void* stream) {
     return result;
 }
 
+// Dynamic area (Eq. (Mb), Sec. 4.3) over a series: the per-step background
+// values on the host, then the steps as single-step jobs carrying them
+// (direct: one batch; cumulative: one call per step, each from the previous
+// step's vertices).
+int inim_run_dynamic(inim_map* map, const float* values, int32_t T, const inim_params* params, double a_min,
+                     double a_max, int32_t t0, int32_t t1, const float* init_xy, float* out_xy,
+                     inim_step_stats* stats, void* stream) {
+    if (!map || !values || !params || !out_xy || T < 1) return fail(INIM_E_ARG, "bad arguments to inim_run_dynamic");
+    if (is_device_ptr(values)) return fail(INIM_E_ARG, "inim_run_dynamic takes host values");
+    if (params->mode != INIM_DIRECT && params->mode != INIM_CUMULATIVE) return fail(INIM_E_ARG, "bad mode");
+    std::vector<double> bdv((size_t)T);
+    int st = inim_background_values(values, T, map->n_regions, params->log2_res, a_min, a_max, t0, t1, bdv.data(),
+                                    nullptr);
+    if (st != INIM_OK) return st;
+    const size_t R = (size_t)map->n_regions, V2 = (size_t)map->n_verts * 2;
+    std::vector<inim_job> jobs((size_t)T);
+    for (int t = 0; t < T; ++t) {
+        inim_job& j = jobs[t];
+        j.map = map;
+        j.values = values + (size_t)t * R;
+        j.init_xy = init_xy;
+        j.out_xy = out_xy + (size_t)t * V2;
+        j.params = *params;
+        j.params.mode = INIM_DIRECT;                  // every job is one time step
+        j.params.bdv_value = (float)bdv[t];
+        j.stats = stats ? stats + t : nullptr;
+    }
+    if (params->mode == INIM_DIRECT) return inim_run_batch(jobs.data(), T, stream);
+    int result = INIM_OK;
+    for (int t = 0; t < T; ++t) {
+        if (t > 0) jobs[t].init_xy = out_xy + (size_t)(t - 1) * V2;
+        st = inim_run_batch(&jobs[t], 1, stream);
+        if (st < 0) return st;
+        result = worst(result, st);
+    }
+    return result;
+}
+
 int inim_raster(const inim_map* map, const float* xy, int32_t log2_res, uint16_t* labels, int32_t* counts,
                 int32_t* overlap, void* stream) {
     if (!map || !xy || !labels || !counts) return fail(INIM_E_ARG, "NULL argument");

@@ -126,3 +126,13 @@ def test_quality_argument_checks(lib):
     xy = np.zeros((3, 2), np.float32)
     assert lib.inim_quality(None, None, xy.ctypes.data, 8, ctypes.byref(out), None, None) == -1
     assert b"NULL" in lib.inim_last_error()
+
+
+def test_run_dynamic_argument_checks(lib):
+    import paper_2604_13880_gb300 as P
+    p = P.params(log2_res=8)
+    vals = np.ones((2, 3), np.float32)
+    out = np.empty((2, 4, 2), np.float32)
+    assert lib.inim_run_dynamic(None, vals.ctypes.data, 2, ctypes.byref(p), 0.2, 0.8, 0, -1, None,
+                                out.ctypes.data, None, None) == -1
+    assert b"inim_run_dynamic" in lib.inim_last_error()
