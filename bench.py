@@ -14,8 +14,8 @@ from CUDA events on the library's stream, SM clocks sampled during the timed
 region, the CPU oracle on a bounded sample (cpu_baseline), the plain
 unfused GPU form on a bounded sample, and time-to-epsilon plain vs fused.
 
---impl reference times the CPU oracle (the reference arm of this build) on
-the same workload and metric.
+--impl reference times the CPU oracle on the same workload and metric (the
+reference arm: the paper's own implementation is not available).
 """
 from __future__ import annotations
 
