@@ -264,7 +264,8 @@ typedef struct {
  *             pixels in either raster scores 1 and is left out of the mean;
  *   rel_pos   mean over ordered region pairs of the angle between the vectors
  *             joining their barycentres (polygon area centroids) in the two
- *             maps, over pi.
+ *             maps, over pi; NaN when a region's polygon has zero area in
+ *             either map (its barycentre is undefined).
  *   shape_per [n_regions] host out per-region shape distortion, or NULL.
  * Works in device memory of its own: two R x R bit adjacency tables and the
  * bounding-box masks of every region.  The shape search visits every
