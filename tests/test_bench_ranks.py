@@ -53,3 +53,21 @@ def test_whole_job_rate_single_rank():
     import bench
     ms, value = bench.whole_job_rate(200.0, 7200, 1)
     assert ms == 200.0 and value == pytest.approx(36000.0)
+
+
+def test_roofline_entry_arithmetic():
+    # achieved = algorithmic bytes per launch / launch time; frac against the
+    # peak; traffic only where a capture of the same kernel and tile exists
+    sys.path.insert(0, ROOT)
+    import bench
+    algo = bench.stage_bytes(3, 1024, 50_000, 200, 90_000, 27_000, 128)
+    assert algo["scan_phase3"] == 3 * (10 * 1024 * 1024 + 12 * 128 * 1024)
+    assert algo["gather_move"] == 3 * 48 * 50_000
+    batches = {"chain3": dict(algo=algo, stages={"scan_phase3": 0.02, "scan_phase1": 0.01},
+                              tile=dict(band_rows=8, cols_per_thread=0, threads=256), per_step=1200)}
+    pk = {"hbm_gbs": 6788.3}
+    r = bench.roofline(batches, "chain3", "scan_phase3", pk)
+    assert r["achieved"] == pytest.approx(algo["scan_phase3"] / 0.02e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] == bench.TRAFFIC[("chain3", "scan_phase3", 8, 0, 256)]
+    assert bench.roofline(batches, "chain3", "scan_phase1", pk)["traffic"] is None
