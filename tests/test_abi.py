@@ -43,13 +43,15 @@ def test_struct_layout_matches_header(tmp_path):
                    'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(inim_params), sizeof(inim_step_stats),'
                    ' sizeof(inim_job), offsetof(inim_job, params), offsetof(inim_params, form),'
                    ' offsetof(inim_params, bdv_value));'
-                   'printf("%zu %zu\\n", sizeof(inim_quality_out), offsetof(inim_quality_out, n_present));return 0;}\n')
+                   'printf("%zu %zu %zu %zu\\n", sizeof(inim_quality_out), offsetof(inim_quality_out, n_present),'
+                   ' sizeof(inim_series), offsetof(inim_series, stats));return 0;}\n')
     exe = tmp_path / "t"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
     want = [ctypes.sizeof(_lib.inim_params), ctypes.sizeof(_lib.inim_step_stats), ctypes.sizeof(_lib.inim_job),
             _lib.inim_job.params.offset, _lib.inim_params.form.offset, _lib.inim_params.bdv_value.offset,
-            ctypes.sizeof(_lib.inim_quality_out), _lib.inim_quality_out.n_present.offset]
+            ctypes.sizeof(_lib.inim_quality_out), _lib.inim_quality_out.n_present.offset,
+            ctypes.sizeof(_lib.inim_series), _lib.inim_series.stats.offset]
     assert got == want
 
 
