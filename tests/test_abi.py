@@ -95,6 +95,12 @@ def test_background_values_match_the_oracle(lib):
         want, _, a_i = O.background_values(vals.astype(np.float64), 10, a_min, a_max, t0, t1)
         np.testing.assert_allclose(got, want, rtol=1e-12)
         np.testing.assert_allclose(frac, a_i, rtol=1e-14)
+    # a constant global integral puts every step at a_max (library and oracle)
+    const = np.ones((4, 5), np.float32)
+    got, frac = P.inim_background_values(const, 9, 0.3, 0.8)
+    want, _, a_i = O.background_values(const.astype(np.float64), 9, 0.3, 0.8)
+    np.testing.assert_allclose(frac, [0.8] * 4, rtol=1e-15)
+    np.testing.assert_allclose(got, want, rtol=1e-12)
     with pytest.raises(P.InimError):
         P.inim_background_values(vals, 10, 0.6, 0.4)
     with pytest.raises(P.InimError):
