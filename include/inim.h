@@ -369,8 +369,10 @@ int inim_areas(const inim_map* map, const float* xy, double* areas, void* stream
  * same array, so calls whose kernels overlap on the GPU (e.g. on two
  * unordered streams) race.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current): make that
- * first call before any stream capture.  No cudaMalloc, cudaFree or other
- * allocating routine is called.
+ * first call before any stream capture.  The address is kept for the life of
+ * the process, so a cudaDeviceReset between calls is not supported.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.  Errors set the
+ * message of inim_last_error() like every other entry point.
  */
 int inim_inims_noalloc(const float* density, int32_t log2_res, float* S, float* T,
                        float* A, float* B, void* stream);

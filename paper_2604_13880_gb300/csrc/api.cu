@@ -26,6 +26,12 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+}  // namespace
+
+int inim::set_last_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                   \
     do {                                                                                 \
         cudaError_t e_ = (expr);                                                         \

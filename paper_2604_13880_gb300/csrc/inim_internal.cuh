@@ -125,6 +125,10 @@ __device__ __forceinline__ void pdl_start(bool early) {
 
 bool pdl_enabled();   // INIM_PDL=0 in the environment turns the attribute off
 
+// records msg as the calling thread's last error (inim_last_error) and
+// returns code
+int set_last_error(int code, const char* msg);
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
                               cudaStream_t s, Args... args) {

@@ -16,7 +16,12 @@
 //     whose kernels overlap on the GPU (different streams, no ordering) race.
 //   - The first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (with that device current); make that first call
-//     before any stream capture.
+//     before any stream capture.  The address is kept for the life of the
+//     process: a cudaDeviceReset between calls is not supported.
+//   - A small set-up kernel writes the job descriptor and block tables into
+//     the array; the first scan kernel after it is launched in plain stream
+//     order (not as a programmatic dependent launch), because the scan
+//     kernels read those tables before they wait on their predecessor.
 #include <mutex>
 
 #include "scan_impl.cuh"
@@ -70,17 +75,21 @@ __global__ void k_noalloc_setup(Job job, int nb, int carry_blocks, unsigned char
 extern "C" int inim_inims_noalloc(const float* density, int32_t log2_res, float* S, float* T, float* A, float* B,
                                   void* stream) {
     using namespace inim;
-    if (!density || !S || !T || !A || !B) return INIM_E_ARG;
-    if (log2_res < kMinLog2) return INIM_E_ARG;
-    if (log2_res > kNaMaxLog2) return INIM_E_CAPACITY;     // beyond the fixed scratch array
+    if (!density || !S || !T || !A || !B) return set_last_error(INIM_E_ARG, "inim_inims_noalloc: null pointer");
+    if (log2_res < kMinLog2) return set_last_error(INIM_E_ARG, "inim_inims_noalloc: log2_res below 8");
+    if (log2_res > kNaMaxLog2)                             // beyond the fixed scratch array
+        return set_last_error(INIM_E_CAPACITY, "inim_inims_noalloc: log2_res above 10 (N <= 1024)");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return INIM_E_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128)
+        return set_last_error(INIM_E_CUDA, "inim_inims_noalloc: no current device");
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_addr[dev]) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return INIM_E_CUDA;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+            if (e != cudaSuccess || !p)
+                return set_last_error(INIM_E_CUDA, "inim_inims_noalloc: cudaGetSymbolAddress failed");
             g_addr[dev] = p;
         }
         base = g_addr[dev];
@@ -89,7 +98,8 @@ extern "C" int inim_inims_noalloc(const float* density, int32_t log2_res, float*
     const int n = 1 << log2_res;
     const int nb = n / kNaH;
     const int carry_blocks = (carry_qspace(n, nb, kNaH) + 255) / 256;
-    ScanTile tile{kNaH, log2_res == 8 ? 2 : (log2_res == 9 ? 4 : 8), 128};
+    constexpr int NT = 128;
+    ScanTile tile{kNaH, log2_res == 8 ? 2 : (log2_res == 9 ? 4 : 8), NT};
 
     Job J{};
     J.n = n;
@@ -107,14 +117,26 @@ extern "C" int inim_inims_noalloc(const float* density, int32_t log2_res, float*
     J.st = reinterpret_cast<JobState*>(b + kOffState);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_noalloc_setup<<<1, 128, 0, s>>>(J, nb, carry_blocks, b);
-    if (cudaGetLastError() != cudaSuccess) return INIM_E_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return set_last_error(INIM_E_CUDA, "inim_inims_noalloc: set-up launch");
     const Job* dj = reinterpret_cast<const Job*>(b + kOffJob);
     BlockMap band, carry;
     band.d_map = reinterpret_cast<int2*>(b + kOffBandMap);
     band.n_blocks = nb;
     carry.d_map = reinterpret_cast<int2*>(b + kOffCarryMap);
     carry.n_blocks = carry_blocks;
-    if (launch_scan_fp32(dj, band, carry, tile, density, s) != cudaSuccess) return INIM_E_CUDA;
-    if (launch_finalize_B(dj, INIM_FP32, s) != cudaSuccess) return INIM_E_CUDA;
+    // phase 1 in plain stream order: it starts only once the set-up kernel
+    // has finished and its writes are visible
+    const size_t ring = (size_t)kLabelDepth * n * 2;    // CPT * NT = n
+    switch (tile.cpt) {
+        case 2: k_scan_band<AccF32, 2, NT, 1><<<nb, NT, ring, s>>>(dj, band.d_map, density); break;
+        case 4: k_scan_band<AccF32, 4, NT, 1><<<nb, NT, ring, s>>>(dj, band.d_map, density); break;
+        default: k_scan_band<AccF32, 8, NT, 1><<<nb, NT, ring, s>>>(dj, band.d_map, density); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return set_last_error(INIM_E_CUDA, "inim_inims_noalloc: scan launch");
+    if (launch_scan_fp32(dj, band, carry, tile, density, s, 2) != cudaSuccess ||
+        launch_scan_fp32(dj, band, carry, tile, density, s, 3) != cudaSuccess)
+        return set_last_error(INIM_E_CUDA, "inim_inims_noalloc: scan launch");
+    if (launch_finalize_B(dj, INIM_FP32, s) != cudaSuccess)
+        return set_last_error(INIM_E_CUDA, "inim_inims_noalloc: finalize launch");
     return INIM_OK;
 }
