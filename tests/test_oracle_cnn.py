@@ -75,3 +75,44 @@ def test_network_gradient_finite_differences():
             checked += 1
         off += co * 9 * ci + co
     assert checked == 28 and loss > 0
+
+
+def test_bf16_round_definition():
+    # BF16 keeps 7 fraction bits: the spacing at 1 is 2^-7
+    u = 2.0 ** -7
+    cases = {1.0: 1.0, 1 + u / 2: 1.0,                     # tie -> even fraction (0)
+             1 + 1.5 * u: 1 + 2 * u,                       # tie -> even fraction (2)
+             1 + u / 2 + 2.0 ** -20: 1 + u,                # just above the tie
+             -(1 + 1.5 * u): -(1 + 2 * u), 3.0: 3.0, 0.0: 0.0}
+    for x, want in cases.items():
+        assert C.bf16_round(np.array([x]))[0] == want, x
+    # nearest of the two BF16 neighbours, by brute force in float64
+    rng = np.random.default_rng(9)
+    x = (rng.normal(size=4000) * 10.0 ** rng.integers(-6, 6, 4000)).astype(np.float32).astype(np.float64)
+    got = C.bf16_round(x)
+    bits = x.astype(np.float32).view(np.uint32)
+    lo = (bits & 0xFFFF0000).view(np.float32).astype(np.float64)             # toward zero
+    hi = ((bits & 0xFFFF0000) + 0x10000).astype(np.uint32).view(np.float32).astype(np.float64)
+    d_lo, d_hi = np.abs(x - lo), np.abs(hi - x)
+    assert np.all((got == lo) | (got == hi))
+    assert np.all(np.where(d_lo < d_hi, got == lo, True)) and np.all(np.where(d_hi < d_lo, got == hi, True))
+
+
+def test_bf16_mode_rounds_only_what_is_stored():
+    params = C.he_init(6)
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(1, 16, 16))
+    out64, s64 = C.forward(params, x)
+    out16, s16 = C.forward(params, x, bf16=True)
+    for name in ("x0", "a0", "e1", "p1", "d3", "d1b"):
+        assert np.array_equal(C.bf16_round(s16[name]), s16[name]), name      # stored values are BF16
+    assert not np.array_equal(C.bf16_round(out16), out16)                      # the head is not rounded
+    rel = np.linalg.norm(out16 - out64) / np.linalg.norm(out64)
+    assert 1e-4 < rel < 3e-2                                                   # roundings only: ~sqrt(40) 2^-9
+    t = rng.normal(size=(1, 16, 16, 2)) * 0.1
+    l64, g64 = C.loss_and_grads(params, x, t)
+    saved = {}
+    l16, g16 = C.loss_and_grads(params, x, t, bf16=True, saved=saved)
+    assert np.array_equal(C.bf16_round(saved["ge1"]), saved["ge1"])
+    assert abs(l16 - l64) < 3e-2 * l64
+    assert np.dot(g16, g64) / (np.linalg.norm(g16) * np.linalg.norm(g64)) > 0.99
