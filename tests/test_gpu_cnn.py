@@ -14,6 +14,8 @@ the bound used is 3e-2 (2.5 sigma).  The backward path doubles the count and
 adds ReLU mask flips where a pre-activation is within rounding of 0: 6e-2
 per layer gradient, cosine similarity >= 0.998 over the whole blob.
 Accumulation is FP32 throughout (its error, ~1e-6 relative, is negligible).
+Those norm checks against the FP64 oracle stand beside element-wise checks
+against the oracle's BF16 mode (below).
 """
 import numpy as np
 import pytest
@@ -112,6 +114,71 @@ def test_gradients_match_oracle(net):
         ew = _rel(g[off:off + nw], want[off:off + nw])
         eb = _rel(g[off + nw:off + nw + co], want[off + nw:off + nw + co])
         assert ew < 6e-2 and eb < 6e-2, (k, ew, eb)
+        off += nw + co
+
+
+# Element-wise parity against the oracle in its BF16 mode (the same values
+# rounded at the same places).  What remains is the order and precision of
+# the sums (FP32 on the GPU, FP64 in the oracle), which moves stored values
+# across BF16 rounding boundaries now and then and, backwards, flips a ReLU
+# mask where a pre-activation is within rounding of zero.  The bounds below
+# hold for an FP32-accumulating emulation of the same network with margins of
+# 3-5x (forward: max |diff| <= 0.044 rms, worst 8x8 tile 0.042 relative;
+# weight gradients: whole layer <= 0.0092 relative, at most 0.11% of the
+# elements off by more than 0.1 rms, max 0.6 rms, per output channel at most
+# 0.65 of the channel bound); a wrong tile, channel or layer breaks them.
+def test_forward_elementwise_vs_bf16_oracle(net):
+    P = _P()
+    for B, seed in ((1, 11), (3, 12)):
+        blob = C.he_init(seed).astype(np.float32)
+        P.inim_cnn_set_params(net, blob)
+        x = _fields(B, seed).astype(np.float32)
+        xd = torch.as_tensor(x, device="cuda").contiguous()
+        yd = torch.empty((B, 64, 64, 2), dtype=torch.float32, device="cuda")
+        P.inim_cnn_forward(net, xd, yd)
+        got = yd.cpu().numpy().astype(np.float64)
+        want, _ = C.forward(blob.astype(np.float64), x.astype(np.float64), bf16=True)
+        rms = float(np.sqrt((want ** 2).mean()))
+        d = np.abs(got - want)
+        assert d.max() <= 0.15 * rms, (B, d.max() / rms)
+        dt = (got - want).reshape(B, 8, 8, 8, 8, 2)
+        wt = want.reshape(B, 8, 8, 8, 8, 2)
+        tile = np.sqrt((dt ** 2).sum(axis=(2, 4))) / np.sqrt((wt ** 2).sum(axis=(2, 4)))
+        assert tile.max() <= 0.15, (B, tile.max())
+
+
+def test_gradients_elementwise_vs_bf16_oracle(net):
+    P = _P()
+    blob = C.he_init(21).astype(np.float32)
+    P.inim_cnn_set_params(net, blob)
+    B = 2
+    x = _fields(B, 21).astype(np.float32)
+    rng = np.random.default_rng(22)
+    target = (0.3 * _fields(2 * B, 23).reshape(B, 2, 64, 64).transpose(0, 2, 3, 1)
+              + 0.01 * rng.normal(size=(B, 64, 64, 2))).astype(np.float32)
+    xd = torch.as_tensor(x, device="cuda").contiguous()
+    td = torch.as_tensor(target, device="cuda").contiguous()
+    gd = torch.empty(C.n_params(), dtype=torch.float32, device="cuda")
+    P.inim_cnn_gradients(net, xd, td, gd)
+    g = gd.cpu().numpy().astype(np.float64)
+    _, want = C.loss_and_grads(blob.astype(np.float64), x.astype(np.float64), target.astype(np.float64), bf16=True)
+    off = 0
+    for k, (ci, co, _) in enumerate(C.LAYERS):
+        nw = co * 9 * ci
+        gw, ww = g[off:off + nw].reshape(co, 9 * ci), want[off:off + nw].reshape(co, 9 * ci)
+        rms = float(np.sqrt((ww ** 2).mean()))
+        d = np.abs(gw - ww)
+        assert np.linalg.norm(gw - ww) <= 0.05 * np.linalg.norm(ww), (k, "layer")
+        assert (d > 0.1 * rms).mean() <= 0.01, (k, "fraction", (d > 0.1 * rms).mean())
+        assert d.max() <= 2.0 * rms, (k, "max", d.max() / rms)
+        # per output channel: a wrong channel (relative error ~1 or more) fails
+        # unless its gradient is tiny; the emulation's worst channel (the
+        # 8x8 bottleneck, where ReLU mask flips weigh most) reaches 0.65 of this
+        ch_err = np.linalg.norm(gw - ww, axis=1)
+        ch_ref = np.linalg.norm(ww, axis=1)
+        assert np.all(ch_err <= 0.6 * ch_ref + 0.05 * rms * np.sqrt(9 * ci)), (k, "channel")
+        gb, wb = g[off + nw:off + nw + co], want[off + nw:off + nw + co]
+        assert np.linalg.norm(gb - wb) <= 0.05 * np.linalg.norm(wb), (k, "bias")
         off += nw + co
 
 
