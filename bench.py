@@ -66,6 +66,9 @@ def stage_bytes(n_jobs, N, V, R, E, K, nb):
         "scan_phase3": n_jobs * (2 * Ppx + 8 * Ppx + 3 * nb * N * 4),
         "gather_move": n_jobs * 48 * V,
         "areas_errors": n_jobs * (8 * E + 8 * V + 8 * R),
+        # single pass: labels read once, S and T written, band aggregates and
+        # carries written (the look-back's reads of earlier bands stay in L2)
+        "scan_fused": n_jobs * (2 * Ppx + 8 * Ppx + 2 * 3 * nb * N * 4),
     }
 
 

@@ -281,6 +281,30 @@ int inim_quality(const inim_map* map, const float* xy_map, const float* xy_cart,
 int inim_set_persistent(int32_t enable);
 
 /*
+ * Single-pass scan (default 0): with 1, batches of at least 2^23 pixels per
+ * texture size build their integral images (Sec. 3.1) with one kernel per
+ * iteration, whose bands take their carries from the earlier bands by
+ * look-back, instead of three kernels (band aggregates, carries, bands with
+ * carries).  The carries are summed in 64-bit fixed point, so the result does
+ * not depend on the order in which bands finish.  Off by default: the three
+ * kernels measured faster on the benchmark's large batch.  Drops the cached
+ * batches.
+ */
+int inim_set_single_pass_scan(int32_t enable);
+
+/*
+ * Failure detection of device-side waits (no counterpart in the paper).
+ * The grid barrier of the persistent launch polls at most `spins` times
+ * (each poll sleeps up to 256 ns); a wait that runs out records
+ * INIM_E_TIMEOUT, the kernel's blocks return without waiting further, and the
+ * call returns INIM_E_TIMEOUT with the CUDA context still usable.  spins <= 0
+ * restores the default of 2^24 polls (a second or two).  Process-wide; takes
+ * effect at the next launch.  (The single-pass scan's look-back waits have a
+ * fixed cap of 2^22 polls and end the same way.)
+ */
+int inim_set_wait_cap(int64_t spins);
+
+/*
  * Phase timing of persistent launches: while enabled, block 0 of the
  * persistent kernel adds the time from one grid barrier to the next (its own
  * work plus the wait for the slowest block) to 8 counters, one per phase of
@@ -456,13 +480,15 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps);
  * stage is launched `reps` times back to back between two CUDA events on the
  * library's stream (ms[i] = elapsed / reps).  Stages, in iteration order:
  * crossings, raster_rows, density_table, scan_phase1, scan_carry,
- * scan_phase3, gather_move, areas_errors (names from inim_stage_name); the
- * two raster kernels run as pairs, each timed between its own events.  For
- * batches whose maps have at most 2047 regions the density table is built by
- * scan_phase1 (there is no density_table kernel in the iteration) and
- * ms[2] = 0.  The batch's vertices move while it runs; the next run resets
- * them.  ms must
- * hold >= 8 floats; *n_stages receives 8.  INIM_E_STATE if no map batch ran
+ * scan_phase3, gather_move, areas_errors, scan_fused (names from
+ * inim_stage_name); the two raster kernels run as pairs, each timed between
+ * its own events.  For batches whose maps have at most 2047 regions the
+ * density table is built by scan_phase1 (there is no density_table kernel in
+ * the iteration) and ms[2] = 0.  Large batches (at least 2^23 pixels per
+ * resolution) scan in one pass: scan_fused holds that kernel and the three
+ * scan phases read 0 (and the other way round for small batches).  The
+ * batch's vertices move while it runs; the next run resets them.  ms must
+ * hold >= 9 floats; *n_stages receives 9.  INIM_E_STATE if no map batch ran
  * yet.
  */
 int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_stages);

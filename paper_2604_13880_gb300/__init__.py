@@ -21,7 +21,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_FIX64, INIM_FORM_FUSED, INIM_FORM_PLAIN,  # noqa: F401
+from ._lib import (INIM_CUMULATIVE, INIM_DIRECT, INIM_E_ARG, INIM_E_CAPACITY, INIM_E_CUDA,  # noqa: F401
+                   INIM_E_STATE, INIM_E_TIMEOUT, INIM_E_VALUE, INIM_FIX64, INIM_FORM_FUSED, INIM_FORM_PLAIN,
                    INIM_FP32, INIM_KAHAN, InimError, inim_job, inim_params, inim_series, inim_step_stats)
 
 __all__ = [
@@ -334,6 +335,16 @@ def inim_set_persistent(enable: bool) -> None:
 
 PERSISTENT_PHASES = ("crossings", "rows", "density", "scan_phase1", "scan_carry", "scan_phase3", "gather_move",
                      "areas_errors")
+
+
+def inim_set_single_pass_scan(enable: bool) -> None:
+    """Large batches scan in one pass, or with three kernels (the default)."""
+    _lib.check(_lib.load().inim_set_single_pass_scan(1 if enable else 0), "inim_set_single_pass_scan")
+
+
+def inim_set_wait_cap(spins: int) -> None:
+    """Polls of a device-side barrier wait before it gives up (INIM_E_TIMEOUT); <= 0: the default."""
+    _lib.check(_lib.load().inim_set_wait_cap(int(spins)), "inim_set_wait_cap")
 
 
 def inim_persistent_phase_times(enable: bool):

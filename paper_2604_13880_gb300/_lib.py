@@ -152,6 +152,8 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int32)]),
     "inim_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "inim_launch_count": (ctypes.c_longlong, []),
+    "inim_set_wait_cap": (ctypes.c_int, [ctypes.c_int64]),
+    "inim_set_single_pass_scan": (ctypes.c_int, [ctypes.c_int32]),
 }
 
 _lib = None

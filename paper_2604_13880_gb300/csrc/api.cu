@@ -121,6 +121,8 @@ struct Buffers {
     void* carry = nullptr;
     double* areas = nullptr;
     float2* xy = nullptr;
+    unsigned* flags = nullptr;          // single-pass scan: band flags
+    long long* binc = nullptr;          // single-pass scan: band inclusive prefixes (fixed point)
 
     cudaError_t alloc(int n_, int prec, int R_, int V_, int nb_, bool interleaved) {
         n = n_; precision = prec; R = R_; V = V_; nb = nb_;
@@ -144,13 +146,17 @@ struct Buffers {
         A_(&carry, (size_t)3 * nb * n * es);
         A_((void**)&areas, (size_t)R * 8);
         A_((void**)&xy, (size_t)V * 8);
+        // map jobs may run the single-pass scan (large batches)
+        A_((void**)&flags, interleaved ? (size_t)nb * 4 : 16);
+        A_((void**)&binc, interleaved ? (size_t)3 * nb * n * 8 : 16);
         if (e == cudaSuccess) e = cudaMemset(row_cnt, 0, (size_t)n * 4);
+        if (e == cudaSuccess) e = cudaMemset(flags, 0, interleaved ? (size_t)nb * 4 : 16);
         return e;
     }
     void release() {
         dfree(labels); dfree(row_cnt); dfree(big_rows); dfree(keys); dfree(counts); dfree(dens);
         dfree(values); dfree(S); dfree(T); dfree(A); dfree(B); dfree(rowcum); dfree(agg);
-        dfree(carry); dfree(areas); dfree(xy);
+        dfree(carry); dfree(areas); dfree(xy); dfree(flags); dfree(binc);
     }
 };
 
@@ -211,8 +217,36 @@ struct JobSpec {
 struct Group {
     int log2n;
     ScanTile tile;
-    BlockMap band, carry;
+    BlockMap band, carry;     // band.ticket: the single-pass scan's ticket counter
 };
+
+// With inim_set_single_pass_scan(1), large groups of map jobs scan in one
+// pass (scan_fused.cuh) with the row-serial tiles; by default every group
+// uses the three kernels (phase 1, carries, phase 3), which measured faster
+// on the 72-solve batch of the time-varying sweep (334 against 484 us per
+// iteration with 16-row bands, 305 against 377 us with 32-row bands): the
+// single-pass blocks hold their SM slots during the look-back (median 9 us)
+// and their phases run slower next to blocks in other phases.
+int g_single_pass = 0;
+
+int fused_for(const ScanTile& t, int size_cls, bool maps) {
+    return (g_single_pass && maps && t.cpt > 0 && size_cls == 1) ? 1 : 0;
+}
+
+// Block order of a single-pass scan: band 0 of every job, then band 1 of
+// every job, ...  A band's look-back then finds its predecessor (dispatched a
+// whole round of jobs earlier) already finished, instead of adding up the
+// aggregates of many bands that started at the same time.
+std::vector<int2> interleave_bands(const std::vector<int2>& band) {
+    std::vector<int2> out;
+    out.reserve(band.size());
+    int max_b = 0;
+    for (const int2& x : band) max_b = std::max(max_b, x.y);
+    for (int b = 0; b <= max_b; ++b)
+        for (const int2& x : band)
+            if (x.y == b) out.push_back(x);
+    return out;
+}
 
 constexpr int kGraphSizes = 6;     // CUDA graphs of 1, 2, 4, 8, 16, 32 iterations per batch
 
@@ -295,7 +329,7 @@ struct Batch {
         dfree(d_jobs); dfree(d_states);
         BlockMap* maps[] = {&edge_blocks, &job_blocks, &row_blocks, &vert_blocks, &region_blocks};
         for (BlockMap* m : maps) dfree(m->d_map);
-        for (auto& g : groups) { dfree(g.band.d_map); dfree(g.carry.d_map); }
+        for (auto& g : groups) { dfree(g.band.d_map); dfree(g.carry.d_map); dfree(g.band.ticket); }
         if (ev_moved) cudaEventDestroy(ev_moved);
         if (ev_areas) cudaEventDestroy(ev_areas);
         if (side) cudaStreamDestroy(side);
@@ -362,6 +396,7 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
         // map jobs: one interleaved (S, T) table (S's buffer holds both halves)
         J.ST = m ? b.S : nullptr;
         J.H = tile.H; J.nb = nb; J.agg = b.agg; J.carry = b.carry;
+        J.bflags = b.flags; J.binc = b.binc;
         J.areas = b.areas; J.st = B.d_states + k;
         B.h_jobs[k] = J;
         if (m) {
@@ -404,11 +439,17 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
             for (int q = 0; q < (len + qpb - 1) / qpb; ++q) carry.push_back(make_int2(k, q));
         }
         if (band.empty()) continue;
+        bool maps = true;
+        for (int k = 0; k < nj; ++k) if (spec[k].log2n == l && !spec[k].map) maps = false;
         Group g;
         g.log2n = l;
         g.tile = tile_for(l, B.precision, size_class(group_px[l]));
+        g.tile.fused = fused_for(g.tile, size_class(group_px[l]), maps);
+        if (g.tile.fused) band = interleave_bands(band);
         CUDA_TRY(make_map(g.band, band));
         CUDA_TRY(make_map(g.carry, carry));
+        CUDA_TRY(cudaMalloc(&g.band.ticket, sizeof(unsigned long long)));
+        CUDA_TRY(cudaMemset(g.band.ticket, 0, sizeof(unsigned long long)));
         g.carry.q_per_block = carry_q_per_block(((1 << l) + g.tile.H - 1) / g.tile.H, size_class(group_px[l]));
         B.groups.push_back(g);
     }
@@ -457,22 +498,34 @@ long long group_pixels(const Batch& B, int log2n) {
 
 int retile_group(Batch& B, Group& g, ScanTile t) {
     std::vector<int2> band, carry;
+    bool maps = true;
     for (int k = 0; k < (int)B.spec.size(); ++k) {
         if (B.spec[k].log2n != g.log2n) continue;
+        maps = maps && B.spec[k].map != nullptr;
         Job& J = B.h_jobs[k];
         J.H = t.H;
         J.nb = (J.n + t.H - 1) / t.H;
+        // a new grid: the single-pass scan's flags start over (with its tickets)
+        CUDA_TRY(cudaMemsetAsync(B.bufs[k].flags, 0, B.spec[k].map ? (size_t)B.bufs[k].nb * 4 : 16, B.stream));
         for (int b = 0; b < J.nb; ++b) band.push_back(make_int2(k, b));
         const int len = carry_qspace(J.n, J.nb, J.H);
         const int qpb = carry_q_per_block(J.nb, size_class(group_pixels(B, g.log2n)));
         for (int q = 0; q < (len + qpb - 1) / qpb; ++q) carry.push_back(make_int2(k, q));
     }
+    const int fused = fused_for(t, size_class(group_pixels(B, g.log2n)), maps);
+    if (fused) band = interleave_bands(band);
     dfree(g.band.d_map);
     dfree(g.carry.d_map);
+    unsigned long long* ticket = g.band.ticket;
+    g.band = BlockMap{};
+    g.carry = BlockMap{};
+    g.band.ticket = ticket;
     CUDA_TRY(make_map(g.band, band));
     CUDA_TRY(make_map(g.carry, carry));
+    CUDA_TRY(cudaMemsetAsync(g.band.ticket, 0, sizeof(unsigned long long), B.stream));
     g.carry.q_per_block = carry_q_per_block((1 << g.log2n) / t.H, size_class(group_pixels(B, g.log2n)));
     g.tile = t;
+    g.tile.fused = fused;
     CUDA_TRY(cudaMemcpyAsync(B.d_jobs, B.h_jobs.data(), B.h_jobs.size() * sizeof(Job), cudaMemcpyHostToDevice,
                              B.stream));
     return INIM_OK;
@@ -544,7 +597,7 @@ namespace {
 int kernels_per_fused_iteration(const Batch& B) {
     int k = 1 + (B.edge_blocks.n_blocks ? 1 : 0);          // crossing keys, rows
     k += B.fuse_table ? 0 : 1;                               // density table (else built by the scan)
-    k += 3 * (int)B.groups.size();                           // scan phases 1-3
+    for (auto& g : B.groups) k += g.tile.fused ? 1 : 3;      // single-pass scan, or phases 1-3
     k += B.vert_blocks.n_blocks ? 1 : 0;                     // gather / move
     k += B.region_blocks.n_blocks ? 1 : 0;                   // areas + errors + stop rule
     return k;
@@ -1336,6 +1389,18 @@ int inim_set_persistent(int32_t enable) {
     return INIM_OK;
 }
 
+int inim_set_single_pass_scan(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_single_pass = enable ? 1 : 0;
+    g_cache.clear();                  // cached batches keep the form they were built with
+    return INIM_OK;
+}
+
+int inim_set_wait_cap(int64_t spins) {
+    set_wait_cap((long long)spins);
+    return INIM_OK;
+}
+
 int inim_persistent_phase_times(int32_t enable, double* ms, int32_t n) {
     if (enable && !g_phase_ns) CUDA_TRY(cudaMalloc(&g_phase_ns, 8 * sizeof(unsigned long long)));
     if (g_phase_ns && ms && n > 0) {
@@ -1838,8 +1903,8 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps) {
 }
 
 static const char* kStageNames[] = {"crossings", "raster_rows", "density_table", "scan_phase1", "scan_carry",
-                                     "scan_phase3", "gather_move", "areas_errors"};
-constexpr int kNumStages = 8;
+                                     "scan_phase3", "gather_move", "areas_errors", "scan_fused"};
+constexpr int kNumStages = 9;
 
 const char* inim_stage_name(int32_t i) {
     return (i >= 0 && i < kNumStages) ? kStageNames[i] : "";
@@ -1864,12 +1929,14 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
     auto stage = [&](int i) -> cudaError_t {
         switch (i) {
             case 2: return launch_density_table(B.d_jobs, nj, B.stream);
-            case 3: case 4: case 5: {
+            case 3: case 4: case 5: case 8: {
+                // phases 1-3 of three-kernel groups; 8: the single-pass groups
+                const int phase = i == 8 ? 4 : i - 2;
                 cudaError_t e = cudaSuccess;
                 for (auto& g : B.groups) {
-                    if (B.precision == INIM_FIX64) e = launch_scan_fix64(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 2);
-                    else if (B.precision == INIM_KAHAN) e = launch_scan_kahan(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 2);
-                    else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, i - 2);
+                    if (B.precision == INIM_FIX64) e = launch_scan_fix64(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, phase);
+                    else if (B.precision == INIM_KAHAN) e = launch_scan_kahan(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, phase);
+                    else e = launch_scan_fp32(B.d_jobs, g.band, g.carry, g.tile, nullptr, B.stream, phase);
                     if (e != cudaSuccess) break;
                 }
                 return e;
@@ -1906,6 +1973,9 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
     }
     for (int i = 2; i < kNumStages && rc == INIM_OK; ++i) {
         if (i == 2 && B.fuse_table) { ms[i] = 0.0f; continue; }     // built by the scan's first phase
+        bool any_fused = false, any_split = false;
+        for (auto& g : B.groups) (g.tile.fused ? any_fused : any_split) = true;
+        if ((i >= 3 && i <= 5 && !any_split) || (i == 8 && !any_fused)) { ms[i] = 0.0f; continue; }
         cudaError_t e = stage(i);                       // warm
         if (e == cudaSuccess) e = cudaEventRecord(e0, B.stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r) e = stage(i);

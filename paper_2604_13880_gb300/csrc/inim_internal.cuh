@@ -89,6 +89,11 @@ struct Job {
     int    H, nb;              // band height, number of bands
     void*  agg;                // [3][nb][n] band aggregates
     void*  carry;              // [3][nb][n] band carries
+    // single-pass scan (large batches): per band a flag (launch epoch << 2 |
+    // status) and the inclusive prefix, i.e. the carries into the next band,
+    // in 64-bit fixed point
+    unsigned*  bflags;         // [nb]
+    long long* binc;           // [3][nb][n]
     // areas and errors
     double*   areas;           // [n_regions] signed shoelace areas
     JobState* st;
@@ -237,12 +242,14 @@ struct BlockMap {            // block -> (job, first item) tables for one kernel
     int2* d_map = nullptr;   // device [n_blocks]
     int   n_blocks = 0;
     int   q_per_block = 256; // carry maps: q values per block (32 = the grouped carry kernel)
+    unsigned long long* ticket = nullptr;   // band maps of single-pass scans: block tickets (device)
 };
 
 // band height, columns per thread, threads; cpt == 0 selects the
 // parallel-rows band scan (256 threads), which is instantiated per texture
-// side n
-struct ScanTile { int H; int cpt; int nt; int n = 0; };
+// side n; fused: the single-pass kernel instead of phases 1-3 (row-serial
+// form, map jobs)
+struct ScanTile { int H; int cpt; int nt; int n = 0; int fused = 0; };
 
 cudaError_t raster_setup(int max_n);   // once per process
 cudaError_t launch_raster_prologue(const Job* d_jobs, int n_jobs, const BlockMap& edge_blocks, cudaStream_t s);
@@ -268,6 +275,7 @@ cudaError_t launch_finalize_B(const Job* d_job, int precision, cudaStream_t s);
 
 // persistent form (small FP32 batches, N <= 2048)
 int persistent_smem_bytes(int max_n);
+void set_wait_cap(long long spins);    // polls of a device-side barrier wait; <= 0: the default
 cudaError_t launch_persistent(Job* d_jobs, int n_jobs, const BlockMap& edge, const BlockMap& row,
                               const BlockMap& band, const BlockMap& carry, const BlockMap& vert,
                               const BlockMap& region, int iters, int rounds, const int* job_rounds,

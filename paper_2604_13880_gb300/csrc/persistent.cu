@@ -20,7 +20,8 @@ namespace inim {
 namespace {
 
 constexpr int kPersistThreads = 256;
-constexpr long long kSpinCap = 1LL << 24;   // ~1-2 s of polling with back-off
+constexpr long long kSpinCap = 1LL << 24;   // default: ~1-2 s of polling with back-off
+long long g_spin_cap = kSpinCap;            // set by inim_set_wait_cap
 
 struct PersistPlan {
     Job* jobs;
@@ -40,6 +41,7 @@ struct PersistPlan {
     JobState* const* round_stats;       // [n_jobs] -> [rounds] final state of every round
     unsigned* bar;            // [2] arrivals, generation
     int* err;
+    long long spin_cap;       // polls of a barrier wait before it gives up
     unsigned long long* phase_ns;       // NULL, or [kPhases] time spent up to each barrier (block 0)
 };
 
@@ -78,7 +80,7 @@ __device__ __forceinline__ bool grid_barrier(const PersistPlan& P) {
             while (*gen == g) {
                 __nanosleep(ns);
                 if (ns < 256) ns <<= 1;
-                if (++spins > kSpinCap) {
+                if (++spins > P.spin_cap) {
                     atomicExch(P.err, INIM_E_TIMEOUT);
                     break;
                 }
@@ -215,6 +217,8 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persistent(PersistPlan P
 
 }  // namespace
 
+void set_wait_cap(long long spins) { g_spin_cap = spins > 0 ? spins : kSpinCap; }
+
 int persistent_smem_bytes(int max_n) {
     size_t a = kRowSharedPadded;
     size_t b = sizeof(ScanShared<AccF32, kPersistThreads>);
@@ -264,6 +268,7 @@ cudaError_t launch_persistent(Job* d_jobs, int n_jobs, const BlockMap& edge, con
     P.round_stats = round_stats;
     P.bar = bar;
     P.err = err;
+    P.spin_cap = g_spin_cap;
     P.phase_ns = phase_ns;
     void* args[] = {&P};
     e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);

@@ -253,10 +253,14 @@ __device__ __forceinline__ LabelWords<CPT> smem_labels(const uint16_t* row, int 
 // then be set); DEPTH == 0: each thread loads its labels two rows ahead.
 // fuse_table (phase 1 from labels, R + 1 <= kDensSmem): the block builds this
 // iteration's density table itself (table.cuh); band 0 publishes it with the
-// job state.
+// job state.  keep_fix_bits >= 0: the table is still in sh.dens from this
+// block's phase 1 (or in J.dens for more than kDensSmem - 1 regions) and the
+// fixed-point bits are given.  fix_bits_out receives the bits used.  Returns
+// false (in every thread) when a staged row never arrived.
 template <class Acc, int CPT, int NT, int PHASE, int DEPTH = 0>
-__device__ inline void scan_band_body(const Job& J, int band, const float* __restrict__ dtex, ScanShared<Acc, NT>& sh,
-                                      LabelRing<DEPTH> ring = {}, bool fuse_table = false) {
+__device__ inline bool scan_band_body(const Job& J, int band, const float* __restrict__ dtex, ScanShared<Acc, NT>& sh,
+                                      LabelRing<DEPTH> ring = {}, bool fuse_table = false, int keep_fix_bits = -1,
+                                      int* fix_bits_out = nullptr) {
     using T = typename Acc::T;
     const int n = J.n, H = J.H, nb = J.nb;
     const int j0 = band * H;
@@ -317,7 +321,10 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
     }
     const float* table = J.dens;
     int fix_bits;
-    if (PHASE == 1 && from_labels && fuse_table) {
+    if (keep_fix_bits >= 0) {
+        fix_bits = keep_fix_bits;
+        if (from_labels && J.n_regions + 1 <= kDensSmem) table = sh.dens;
+    } else if (PHASE == 1 && from_labels && fuse_table) {
         fix_bits = region_table(J, sh.dens, band == 0).fix_bits;
         table = sh.dens;
         __syncthreads();
@@ -329,6 +336,7 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
         }
         fix_bits = J.st->fix_bits;
     }
+    if (fix_bits_out) *fix_bits_out = fix_bits;
     const float qscale = ldexpf(1.0f, fix_bits);   // fixed-point unit (FIX64 only)
     LabelWords<CPT> lw0{}, lw1{};
     float dn[CPT];
@@ -382,7 +390,7 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
                 for (int rr = r; rr < rows && rr < r + DEPTH; ++rr)
                     mbar_wait(ring.bars + rr % (DEPTH > 0 ? DEPTH : 1), (unsigned)(rr / (DEPTH > 0 ? DEPTH : 1)) & 1u);
             }
-            return;
+            return false;
         }
         // every thread has read this row's slot: refill it DEPTH rows ahead
         if (use_ring && tid == 0 && r + DEPTH < rows) {
@@ -464,6 +472,7 @@ __device__ inline void scan_band_body(const Job& J, int band, const float* __res
         store_row<Acc, CPT>(agg + (size_t)(nb + band) * n + i0, E1);
         store_row<Acc, CPT>(agg + (size_t)(2 * nb + band) * n + i0, E2);
     }
+    return true;
 }
 
 template <class Acc, int CPT, int NT, int PHASE>
@@ -672,9 +681,33 @@ template <class Acc, int N, int H>
 cudaError_t launch_scan_pb(const Job* d_jobs, const BlockMap& band, const BlockMap& carry, const float* dtex,
                            int phase, cudaStream_t s);
 
+template <class Acc, int CPT, int NT>
+cudaError_t launch_scan_fused_tile(const Job* d_jobs, const BlockMap& band, cudaStream_t s);
+
+// phase 0: the whole scan (the single-pass kernel for a fused tile); 1, 2, 3:
+// one phase of the three-kernel form (nothing for a fused tile); 4: only the
+// single-pass kernel of a fused tile (for stage timing)
 template <class Acc>
 cudaError_t launch_scan_acc(const Job* d_jobs, const BlockMap& band, const BlockMap& carry,
                             ScanTile tile, const float* dtex, int phase, cudaStream_t s) {
+    const bool fused = tile.fused && tile.cpt > 0 && dtex == nullptr;
+    if (phase == 4 && !fused) return cudaSuccess;
+    if (fused) {
+        if (phase != 0 && phase != 4) return cudaSuccess;
+        switch (tile.cpt * 10000 + tile.nt) {
+            case 2 * 10000 + 128: return launch_scan_fused_tile<Acc, 2, 128>(d_jobs, band, s);
+            case 4 * 10000 + 128: return launch_scan_fused_tile<Acc, 4, 128>(d_jobs, band, s);
+            case 2 * 10000 + 256: return launch_scan_fused_tile<Acc, 2, 256>(d_jobs, band, s);
+            case 8 * 10000 + 128: return launch_scan_fused_tile<Acc, 8, 128>(d_jobs, band, s);
+            case 4 * 10000 + 256: return launch_scan_fused_tile<Acc, 4, 256>(d_jobs, band, s);
+            case 8 * 10000 + 256: return launch_scan_fused_tile<Acc, 8, 256>(d_jobs, band, s);
+            case 4 * 10000 + 512: return launch_scan_fused_tile<Acc, 4, 512>(d_jobs, band, s);
+            case 8 * 10000 + 512: return launch_scan_fused_tile<Acc, 8, 512>(d_jobs, band, s);
+            case 16 * 10000 + 64: return launch_scan_fused_tile<Acc, 16, 64>(d_jobs, band, s);
+            case 32 * 10000 + 32: return launch_scan_fused_tile<Acc, 32, 32>(d_jobs, band, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (tile.cpt == 0) {                          // parallel-rows form
         switch (tile.n * 100 + tile.H) {
             case 1024 * 100 + 8: return launch_scan_pb<Acc, 1024, 8>(d_jobs, band, carry, dtex, phase, s);
@@ -703,3 +736,4 @@ cudaError_t launch_scan_acc(const Job* d_jobs, const BlockMap& band, const Block
 }  // namespace inim
 
 #include "scan_pb.cuh"
+#include "scan_fused.cuh"
