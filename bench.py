@@ -114,6 +114,63 @@ def crossings_count(mesh, N):
     return K
 
 
+def _oracle_worker(task):
+    """One CPU worker of the all-core baseline: `iters` oracle iterations of
+    one solve (its own shape and time step), single-threaded numpy."""
+    arrays, verts, values, k, shape, iters = task
+    from oracle import inim_oracle as O
+    t0 = O.transform_uniform(1 << k)
+    xy = verts.astype(np.float64)
+    t = time.perf_counter()
+    for _ in range(iters):
+        xy, _ = O.iterate(xy, arrays, values, k, shape, t0=t0)
+    return iters, time.perf_counter() - t
+
+
+def cpu_all_cores(mesh, values, k, iters_per_worker=3):
+    """The oracle on every host core the process may use: one independent solve
+    per core (shapes and time steps of the sweep), iterations / wall time."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    arrays = (mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
+    tasks = [(arrays, mesh.verts_f32(), values[c % len(values)], k, SHAPES[c % len(SHAPES)], iters_per_worker)
+             for c in range(cores)]
+    env = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in env:
+        os.environ[v] = "1"                        # one thread per worker process
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_worker, [tasks[0][:5] + (1,)] * cores)      # start-up and imports, untimed
+            t = time.perf_counter()
+            res = pool.map(_oracle_worker, tasks)
+            wall = time.perf_counter() - t
+    finally:
+        for v, x in env.items():
+            if x is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = x
+    n = sum(r[0] for r in res)
+    return {"value": n / wall, "unit": "iterations/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent solves of the 1024^2 map (one per core, the sweep's shapes and "
+                      f"time steps), {iters_per_worker} oracle iterations each, {wall:.1f} s wall"}
+
+
+def quick_warm_start_network(n_maps=1536, epochs=10):
+    """A warm-start network trained on the spot (fields the method generates on
+    the training maps of the learned part, as in warmstart.py, fewer maps);
+    returns (parameter blob, seconds)."""
+    from paper_2604_13880_gb300 import warmstart as W
+    import paper_2604_13880_gb300 as P
+    t = time.perf_counter()
+    maps = W.generate_maps(range(50000, 50000 + n_maps), workers=min(16, os.cpu_count() or 1))
+    X, Y, _ = W.build_dataset(maps, eps_target=0.05, max_iters=512)
+    net, _ = W.train(X, Y, epochs=epochs)
+    blob = P.inim_cnn_get_params(net)
+    net.close()
+    return blob, time.perf_counter() - t
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -302,6 +359,146 @@ def coherence_study(args):
 
 
 # ---------------------------------------------------------------------------
+# the batched workload: 64 independent maps of uneven texture sizes
+# ---------------------------------------------------------------------------
+def batched_config(args):
+    """64 maps (N from {256, 512, 1024, 2048}, 20-500 regions, log-normal
+    values, FP32, shape 0.5) solved together in one batch: iterations/s of 50
+    fixed iterations per map (inputs resident in HBM; and through pinned host
+    buffers), the dominant kernel's roofline from stage timings, and the same
+    batch with the stop rule of Sec. 4.1 (time until every map stops)."""
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import _lib, synth
+    lib = _lib.load()
+    t_gen = time.perf_counter()
+    w = synth.batched_workload()
+    t_gen = time.perf_counter() - t_gen
+    maps = [P.inim_map_create(x["mesh"]) for x in w]
+    B = len(w)
+    vals_h = [torch.as_tensor(np.ascontiguousarray(x["values"][0], dtype=np.float32)).pin_memory() for x in w]
+    vals_d = [v.cuda() for v in vals_h]
+    out_h = [torch.empty((x["mesh"].n_verts, 2)).pin_memory() for x in w]
+    out_d = [torch.empty((x["mesh"].n_verts, 2), device="cuda") for x in w]
+    iters = ITERS
+
+    def jobs(vals, outs, max_iters=iters, rule=False):
+        arr = (P.inim_job * B)()
+        for q, x in enumerate(w):
+            arr[q].map = maps[q].handle
+            arr[q].values = vals[q].data_ptr()
+            arr[q].init_xy = None
+            arr[q].out_xy = outs[q].data_ptr()
+            arr[q].params = P.params(log2_res=x["log2_res"], shape=0.5, max_iters=max_iters,
+                                     xi_stop=0.01 if rule else 0.0, stall_window=32 if rule else 0)
+            arr[q].stats = None
+        return arr
+
+    jd = jobs(vals_d, out_d)
+    P.inim_autotune_scan(jd, reps=5)                         # tiles of every size group of the batch
+    tiles = {f"{1 << kk}": {"small": P.inim_get_scan_tile(kk, P.INIM_FP32, 0),
+                            "large": P.inim_get_scan_tile(kk, P.INIM_FP32, 1)} for kk in (8, 9, 10, 11)}
+
+    def run(a):
+        _lib.check(lib.inim_run_batch(a, B, None), "batched")
+
+    for _ in range(args.warmup):
+        run(jd)
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    launches0 = P.inim_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        run(jd)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = P.inim_launch_count() - launches0
+    clk = clocks.stop()
+    value = B * iters * args.steps / (ms / 1e3)
+    # through the public API with pinned host buffers (values in, vertices out)
+    jh = jobs(vals_h, out_h)
+    run(jh)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        run(jh)
+    torch.cuda.synchronize()
+    e2e = B * iters * args.steps / (time.perf_counter() - t)
+    # stop rule: until every map stops (xi < 0.01, 32 iterations without a new best xi, or 512)
+    stats = (P.inim_step_stats * B)()
+    jr = jobs(vals_d, out_d, 512, True)
+    for q in range(B):
+        jr[q].stats = ctypes.pointer(stats[q])
+    run(jr)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    run(jr)
+    torch.cuda.synchronize()
+    rule_s = time.perf_counter() - t
+    its = [stats[q].iters for q in range(B)]
+    # stage timings of the batch and the dominant kernel against the copy bandwidth
+    run(jd)
+    stages = P.inim_profile_stages(reps=5)
+    pk = peaks()
+    algo = {}
+    for q, x in enumerate(w):
+        mesh = x["mesh"]
+        N = 1 << x["log2_res"]
+        E = int(P.inim_map_info(maps[q])["n_edges"])
+        K = crossings_count(mesh, N)
+        large = sum(1 << (2 * y["log2_res"]) for y in w if y["log2_res"] == x["log2_res"]) >= (1 << 23)
+        H = tiles[str(N)]["large" if large else "small"]["band_rows"]
+        for st_name, b in stage_bytes(1, N, mesh.n_verts, mesh.n_regions, E, K, -(-N // H)).items():
+            algo[st_name] = algo.get(st_name, 0) + b
+    dom = max((sn for sn in stages if stages[sn] > 0), key=lambda sn: stages[sn])
+    achieved = algo[dom] / (stages[dom] / 1e3) / 1e9
+    px = sum(1 << (2 * x["log2_res"]) for x in w)
+    V = sum(x["mesh"].n_verts for x in w)
+    line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched64_res256-2048_regions20-500_it50", "maps": B,
+                       "textures": {str(1 << kk): sum(1 for x in w if x["log2_res"] == kk) for kk in (8, 9, 10, 11)},
+                       "pixels": px, "vertices": V, "iterations_per_map": iters,
+                       "l2": f"inputs larger than L2 ({px * 12 / 1e9:.2f} GB of texture traffic per iteration)",
+                       "scan_tiles_autotuned": tiles, "map_generation_s": t_gen},
+            "e2e": {"value": e2e, "unit": "iterations/s", "h2d_bytes_per_step": sum(4 * x["mesh"].n_regions for x in w),
+                    "d2h_bytes_per_step": 8 * V, "host_buffers": "pinned"},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                         "algorithmic_bytes_per_launch": algo[dom], "launch_ms": stages[dom],
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "fallback" not in pk else "fallback"},
+            "stages_ms": stages,
+            "stages_gbs": {sn: algo[sn] / (stages[sn] / 1e3) / 1e9 for sn in stages if stages[sn] > 0 and sn in algo},
+            "iteration_bytes": px * 12 + V * 48,
+            "iteration_gbs": (px * 12 + V * 48) / (ms / 1e3 / (iters * args.steps)) / 1e9,
+            "stop_rule": {"wall_ms": 1e3 * rule_s, "iters_mean": float(np.mean(its)), "iters_max": int(max(its)),
+                          "iterations_per_s": float(sum(its)) / rule_s,
+                          "converged_xi_below_0.01": int(sum(stats[q].xi < 0.01 for q in range(B)))}}
+    if clk:
+        line["clocks"] = clk
+    if not args.no_extras:
+        # CPU oracle: one iteration of each of a few maps on one core
+        from oracle import inim_oracle as O
+        t = time.perf_counter()
+        n = 0
+        for x in sorted(w, key=lambda y: y["log2_res"])[::8]:
+            mesh = x["mesh"]
+            O.iterate(mesh.verts_f32().astype(np.float64), (mesh.ring_off, mesh.ring_idx, mesh.ring_region,
+                      mesh.n_regions), x["values"][0], x["log2_res"], 0.5)
+            n += 1
+        cpu_s = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": n / cpu_s, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one iteration of each of {n} maps of the batch (every 8th by size), "
+                                          f"{cpu_s:.1f} s"}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # small fixed cases for profiler captures (ncu): one batch, two iterations
 # ---------------------------------------------------------------------------
 def ncu_case(args):
@@ -364,6 +561,8 @@ def main():
     ap.add_argument("--coherence-sigma", type=float, default=0.6)
     ap.add_argument("--quality", type=int, default=0, metavar="K",
                     help="instead of the sweep: time K calls of inim_quality on the sweep's map")
+    ap.add_argument("--config", choices=["sweep", "batched"], default="sweep",
+                    help="batched: the 64-map batched workload instead of the time-varying sweep")
     ap.add_argument("--ncu-case", choices=["direct72", "chain3"], default=None,
                     help="instead of the sweep: one batch for two iterations (small profiler captures)")
     args = ap.parse_args()
@@ -378,6 +577,8 @@ def main():
         return quality_timing(args)
     if args.coherence_study:
         return coherence_study(args)
+    if args.config == "batched":
+        return batched_config(args)
 
     import torch
     import paper_2604_13880_gb300 as P
@@ -513,7 +714,7 @@ def main():
     plan_h = make_plan(vals_h, out_dir_h, out_cum_h, None)
     run_step(plan_h)
     barrier()
-    e_steps = max(1, min(args.steps, 3))
+    e_steps = args.steps                           # the same step count as the device-resident value
     t = time.perf_counter()
     for _ in range(e_steps):
         run_step(plan_h)
@@ -537,7 +738,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "host_buffers": "pinned"},
             "gpu_launches": int(launches), "wall_s_timed": wall,
             # completed cartograms (time steps of a series, ITERS iterations each) per second
-            "frames": {"value": value / ITERS, "e2e": e2e_value / ITERS, "unit": "cartograms/s"}}
+            "cartograms_per_s": {"value": value / ITERS, "e2e": e2e_value / ITERS, "unit": "cartograms/s"}}
     if clk:
         line["clocks"] = clk
 
@@ -599,29 +800,55 @@ def main():
         line["plain_form"] = {"value": plain_value, "unit": "iterations/s",
                               "sample": "3 shapes x 2 time steps x 50 iterations, one solve at a time",
                               "fused_over_plain": value / world / plain_value}
-        # time to cartographic error eps (one solve, shape 0.5, time step 0)
-        eps_target = 0.02
-        tte = {"eps_target": eps_target}
-        for form, name in ((P.INIM_FORM_PLAIN, "plain"), (P.INIM_FORM_FUSED, "fused")):
+        # time to cartographic error eps, the same target for every form:
+        # one solve (time step 0, shape 0.5) in the plain and the fused form,
+        # with and without the learned warm start, and all 24 time steps as
+        # one batch (direct), cold and warm
+        eps_target = 0.1
+        tte = {"eps_target": eps_target, "max_iters": 512, "shape": 0.5}
+
+        def to_eps(vv, form=P.INIM_FORM_FUSED, warm=0):
             p = P.params(log2_res=k, shape=0.5, max_iters=512, xi_stop=0.0, stall_window=0, eps_stop=eps_target,
-                         form=form)
-            P.inim_run(m, vals[:1], p)
+                         form=form, warm_start=warm)
+            P.inim_run(m, vv, p)                                          # warm-up: graphs, buffers
             torch.cuda.synchronize()
             t = time.perf_counter()
-            _, st, _ = P.inim_run(m, vals[:1], p)
+            _, st, _ = P.inim_run(m, vv, p)
             torch.cuda.synchronize()
-            tte[f"{name}_ms"] = 1e3 * (time.perf_counter() - t)
-            tte[f"{name}_iters"] = st[0]["iters"]
-            tte[f"{name}_eps"] = st[0]["eps"]
-        # all 24 time steps of shape 0.5 to eps, batched (direct) vs one at a time (plain)
-        p = P.params(log2_res=k, shape=0.5, max_iters=512, xi_stop=0.0, stall_window=0, eps_stop=eps_target)
-        P.inim_run(m, vals, p)
-        t = time.perf_counter()
-        _, st, _ = P.inim_run(m, vals, p)
-        tte["fused_batched_24_steps_ms"] = 1e3 * (time.perf_counter() - t)
-        tte["fused_batched_24_steps_iters"] = int(sum(s["iters"] for s in st))
+            its = [x["iters"] for x in st]
+            return {"ms": 1e3 * (time.perf_counter() - t), "iters": int(sum(its)),
+                    "reached": int(sum(x["eps"] < eps_target for x in st)), "solves": len(st),
+                    "eps_max": float(max(x["eps"] for x in st))}
+
+        tte["plain"] = to_eps(vals[:1], P.INIM_FORM_PLAIN)
+        tte["fused"] = to_eps(vals[:1])
+        tte["fused_batched_24_steps"] = to_eps(vals)
+        blob, train_s = quick_warm_start_network()
+        P.inim_warmstart_load(blob)
+        tte["warm_start_network"] = {"training_maps": 1536, "epochs": 10, "seconds": train_s,
+                                     "note": "trained in this run on fields the method generates (512^2 maps)"}
+        tte["fused_warm"] = to_eps(vals[:1], warm=1)
+        tte["fused_batched_24_steps_warm"] = to_eps(vals, warm=1)
         line["time_to_eps"] = tte
-        # CPU oracle on a bounded sample (this host's cores)
+        # animation frames (Sec. 5.5): 10 frames per time step, the values
+        # interpolated linearly between steps (231 frames of the 24 steps), a
+        # cartogram of 50 iterations (shape 0.5) for every frame; direct (every
+        # frame from the map, one batch) and cumulative (frame after frame)
+        fv = torch.as_tensor(P.inim_interpolate_values(vals, 10), device=dev).contiguous()
+        nf = int(fv.shape[0])
+        fout = torch.empty((nf, V, 2), device=dev)
+        fr = {"frames_per_step": 10, "frames": nf, "iterations_per_frame": ITERS, "shape": 0.5}
+        for name, mode in (("direct", P.INIM_DIRECT), ("cumulative", P.INIM_CUMULATIVE)):
+            ser = [dict(map=m, values=fv, params=prm(0.5, mode=mode), out_xy=fout)]
+            P.inim_run_series(ser)                                         # warm-up: buffers, graphs
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            P.inim_run_series(ser)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            fr[name] = {"frames_per_s": nf / dt, "seconds": dt, "iterations_per_s": nf * ITERS / dt}
+        line["frames"] = fr
+        # CPU oracle on a bounded sample (this host's cores): one core, then all
         from oracle import inim_oracle as O
         arrays = (mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
         t0 = O.transform_uniform(1 << k)
@@ -635,6 +862,7 @@ def main():
         line["cpu_baseline"] = {"value": n_cpu / cpu_s, "unit": "iterations/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n_cpu} oracle iterations of the 1024^2 map (shape 0.5, t=0), "
                                           f"{cpu_s:.1f} s"}
+        line["cpu_baseline_all_cores"] = cpu_all_cores(mesh, w["values"], k)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
