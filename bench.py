@@ -275,6 +275,15 @@ def precision_study(args):
         p = P.params(log2_res=12, shape=0.5, precision=prec)
         x = torch.as_tensor(xy0, device="cuda")
         v = torch.as_tensor(vals, device="cuda")
+        # scan tiles of this precision chosen by the autotuner on the job itself
+        ja = (P.inim_job * 1)()
+        ja[0].map = m.handle
+        ja[0].values = v.data_ptr()
+        ja[0].init_xy = None
+        ja[0].out_xy = x.data_ptr()
+        ja[0].params = p
+        ja[0].stats = None
+        P.inim_autotune_scan(ja, reps=3)
         P.inim_iterate(m, x.clone(), v, p, 2)             # warm
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -283,6 +292,20 @@ def precision_study(args):
         dt = time.perf_counter() - t
         outs[name] = x.cpu().numpy()
         res["precisions"][name] = {"ms_per_iteration": 1e3 * dt / K, "eps": st["eps"], "xi": st["xi"]}
+        # stage times of this 4096^2 job and its dominant kernel against the copy bandwidth
+        stages = P.inim_profile_stages(reps=5)
+        N = 1 << 12
+        tile = P.inim_get_scan_tile(12, prec, 1)
+        E = int(P.inim_map_info(m)["n_edges"])
+        algo = stage_bytes(1, N, mesh.n_verts, mesh.n_regions, E, crossings_count(mesh, N), -(-N // tile["band_rows"]))
+        if prec != P.INIM_FP32:                     # 64-bit sums: 8 more bytes per pixel in S and T
+            for sn in ("scan_phase3", "scan_fused"):
+                algo[sn] += 8 * N * N
+        dom = max((sn for sn in stages if stages[sn] > 0), key=lambda sn: stages[sn])
+        pk = peaks()
+        gbs = algo[dom] / (stages[dom] / 1e3) / 1e9
+        res["precisions"][name].update(stages_ms=stages, dominant=dom, dominant_gbs=gbs,
+                                       dominant_frac=gbs / pk["hbm_gbs"], scan_tile=tile)
     np.savez_compressed(args.study_out, verts=xy0, ring_off=mesh.ring_off, ring_idx=mesh.ring_idx,
                         ring_region=mesh.ring_region, n_regions=mesh.n_regions, values=vals, iterations=K,
                         **{f"gpu_{k}": v for k, v in outs.items()})

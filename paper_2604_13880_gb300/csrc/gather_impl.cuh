@@ -102,6 +102,130 @@ __device__ __forceinline__ typename Acc::T grand_total(const Job& J) {
     return J.ST ? reinterpret_cast<const T*>(J.ST)[2 * last] : reinterpret_cast<const T*>(J.S)[last];
 }
 
+// The sums that Eq. (1) turns into the eight InIms at one pixel: S and T at
+// the pixel, S at the bottom of its column, S at the end of its row, A(i+j)
+// and the stored B entry of w = i - j.
+template <class Acc>
+struct CornerSums {
+    typename Acc::T a, at, colcum, rc, A, Braw;
+};
+
+// corner_ratios from sums already loaded (the same arithmetic)
+template <class Acc>
+__device__ __forceinline__ Ratios ratios_from(const CornerSums<Acc>& q, int w, typename Acc::T C, double inv_c) {
+    using T = typename Acc::T;
+    const T b = Acc::sub(q.colcum, q.a);
+    const T d = Acc::sub(q.rc, q.a);
+    const T g = Acc::sub(Acc::sub(Acc::sub(C, q.a), b), d);
+    const T bt = Acc::sub(q.A, q.at);
+    const T Bw = (w <= 0) ? q.Braw : Acc::sub(C, q.Braw);
+    const T gt = Acc::sub(Bw, bt);
+    const T dt = Acc::sub(Acc::sub(Acc::sub(C, q.at), bt), gt);
+    Ratios r;
+    r.a = Acc::scale(q.a, inv_c); r.b = Acc::scale(b, inv_c); r.g = Acc::scale(g, inv_c); r.d = Acc::scale(d, inv_c);
+    r.at = Acc::scale(q.at, inv_c); r.bt = Acc::scale(bt, inv_c); r.gt = Acc::scale(gt, inv_c);
+    r.dt = Acc::scale(dt, inv_c);
+    return r;
+}
+
+// Two horizontally adjacent (S, T) pairs of the interleaved table starting at
+// element p = 2 (j n + i): one 16-byte load when p is a multiple of 4 (FP32,
+// i even), else two 8-byte loads; 64-bit and compensated pairs are 16 bytes
+// each.
+template <class T>
+__device__ __forceinline__ void load_two_pairs(const T* ST, size_t p, T& s0, T& t0, T& s1, T& t1) {
+    if constexpr (sizeof(T) == 4) {
+        if ((p & 3) == 0) {
+            const float4 v = *reinterpret_cast<const float4*>(ST + p);
+            s0 = v.x; t0 = v.y; s1 = v.z; t1 = v.w;
+        } else {
+            const float2 u = *reinterpret_cast<const float2*>(ST + p);
+            const float2 v = *reinterpret_cast<const float2*>(ST + p + 2);
+            s0 = u.x; t0 = u.y; s1 = v.x; t1 = v.y;
+        }
+    } else {
+        const uint4 u = *reinterpret_cast<const uint4*>(ST + p);
+        const uint4 v = *reinterpret_cast<const uint4*>(ST + p + 2);
+        s0 = *reinterpret_cast<const T*>(&u.x); t0 = *reinterpret_cast<const T*>(&u.z);
+        s1 = *reinterpret_cast<const T*>(&v.x); t1 = *reinterpret_cast<const T*>(&v.z);
+    }
+}
+
+// The sums of the four corners (i0, j0), (i0 + 1, j0), (i0, j0 + 1),
+// (i0 + 1, j0 + 1) from the interleaved table, loaded together: two
+// 16-byte rows of (S, T) pairs, the two column ends, the two row ends, three
+// consecutive A and three consecutive B entries.
+template <class Acc>
+__device__ __forceinline__ void load_corners(const Job& J, int i0, int j0, CornerSums<Acc> (&q)[4]) {
+    using T = typename Acc::T;
+    const int n = J.n;
+    const T* ST = reinterpret_cast<const T*>(J.ST);
+    const T* A = reinterpret_cast<const T*>(J.A);
+    const T* B = reinterpret_cast<const T*>(J.B);
+    const T* RC = reinterpret_cast<const T*>(J.rowcum);
+    const size_t p0 = 2 * ((size_t)j0 * n + i0);
+    const size_t pc = 2 * ((size_t)(n - 1) * n + i0);
+    T dummy0, dummy1;
+    load_two_pairs<T>(ST, p0, q[0].a, q[0].at, q[1].a, q[1].at);
+    load_two_pairs<T>(ST, p0 + 2 * (size_t)n, q[2].a, q[2].at, q[3].a, q[3].at);
+    load_two_pairs<T>(ST, pc, q[0].colcum, dummy0, q[1].colcum, dummy1);
+    q[2].colcum = q[0].colcum;
+    q[3].colcum = q[1].colcum;
+    q[0].rc = q[1].rc = RC[j0];
+    q[2].rc = q[3].rc = RC[j0 + 1];
+    const int s = i0 + j0;
+    q[0].A = A[s];
+    q[1].A = q[2].A = A[s + 1];
+    q[3].A = A[s + 2];
+    const int w0 = i0 - j0 + n - 1;             // stored index of w = i0 - j0
+    q[0].Braw = q[3].Braw = B[w0];
+    q[1].Braw = B[w0 + 1];
+    q[2].Braw = B[w0 - 1];
+}
+
+// #{(i', j') : i' + j' <= s} (anti_count32) in FP32: every count is an
+// integer below 2^24 + 1, so the arithmetic is exact
+__device__ __forceinline__ float anti_count_f(int s, int n, float nn) {
+    if (s < 0) return 0.0f;
+    if (s >= 2 * n - 2) return nn;
+    if (s <= n - 1) return (float)(((s + 1) * (s + 2)) >> 1);
+    const int m = 2 * n - 3 - s;
+    return nn - (float)(((m + 1) * (m + 2)) >> 1);
+}
+
+// uniform_ratios of the four corners (i0, j0), (i0 + 1, j0), (i0, j0 + 1),
+// (i0 + 1, j0 + 1) with their shared factors and the three distinct values
+// of each diagonal count computed once; exact integer counts in FP32, then
+// the power-of-two scaling (the same values as uniform_ratios)
+__device__ __forceinline__ void uniform_ratios4(int i0, int j0, int n, float inv_c0, Ratios (&r0)[4]) {
+    const float nn = (float)n * (float)n;
+    const float I[2] = {(float)(i0 + 1), (float)(i0 + 2)};              // i + 1
+    const float Ni[2] = {(float)(n - 1 - i0), (float)(n - 2 - i0)};     // n - 1 - i
+    const float Jp[2] = {(float)(j0 + 1), (float)(j0 + 2)};             // j + 1
+    const float Nj[2] = {(float)(n - 1 - j0), (float)(n - 2 - j0)};     // n - 1 - j
+    float A3[3], B3[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        A3[q] = anti_count_f(i0 + j0 + q, n, nn);                        // i + j = i0 + j0 + q
+        B3[q] = anti_count_f(i0 - j0 + n - 2 + q, n, nn);                // i - j + n - 1, q = di - dj + 1
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int di = c & 1, dj = c >> 1;
+        const int i = i0 + di, j = j0 + dj;
+        const float a = I[di] * Jp[dj], b = I[di] * Nj[dj], g = Ni[di] * Nj[dj], d = Ni[di] * Jp[dj];
+        const int m = i + 1;
+        const int k1 = min(i, j), k2 = min(i, n - 1 - j);
+        const float L = (float)(m + (k1 * m - ((k1 * (k1 + 1)) >> 1)) + (k2 * m - ((k2 * (k2 + 1)) >> 1)));
+        const float at = A3[di + dj] - L;
+        const float gt = B3[di - dj + 1] - L;
+        const float dt = nn - L - at - gt;
+        Ratios& r = r0[c];
+        r.a = a * inv_c0; r.b = b * inv_c0; r.g = g * inv_c0; r.d = d * inv_c0;
+        r.at = at * inv_c0; r.bt = L * inv_c0; r.gt = gt * inv_c0; r.dt = dt * inv_c0;
+    }
+}
+
 template <class Acc>
 __device__ __forceinline__ float2 displacement_at_c(const Job& J, float2 p, typename Acc::T C) {
     const int n = J.n;
@@ -116,10 +240,23 @@ __device__ __forceinline__ float2 displacement_at_c(const Job& J, float2 p, type
     const float a = fminf(fmaxf(fx - (float)i0, 0.0f), 1.0f);
     const float b = fminf(fmaxf(fy - (float)j0, 0.0f), 1.0f);
     float2 f[4];
+    if (J.ST) {
+        CornerSums<Acc> q[4];
+        load_corners<Acc>(J, i0, j0, q);
+        Ratios r0[4];
+        uniform_ratios4(i0, j0, n, inv_c0, r0);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int i = i0 + (c & 1), j = j0 + (c >> 1);
-        f[c] = delta_at_pixel(corner_ratios<Acc>(J, i, j, C, inv_c), uniform_ratios(i, j, n, inv_c0), i, j, inv_n);
+        for (int c = 0; c < 4; ++c) {
+            const int i = i0 + (c & 1), j = j0 + (c >> 1);
+            f[c] = delta_at_pixel(ratios_from<Acc>(q[c], i - j, C, inv_c), r0[c], i, j, inv_n);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = i0 + (c & 1), j = j0 + (c >> 1);
+            f[c] = delta_at_pixel(corner_ratios<Acc>(J, i, j, C, inv_c), uniform_ratios(i, j, n, inv_c0), i, j,
+                                  inv_n);
+        }
     }
     const float2 top = make_float2((1.0f - a) * f[0].x + a * f[1].x, (1.0f - a) * f[0].y + a * f[1].y);
     const float2 bot = make_float2((1.0f - a) * f[2].x + a * f[3].x, (1.0f - a) * f[2].y + a * f[3].y);

@@ -46,6 +46,7 @@ struct AccF32 {
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
     static __device__ __forceinline__ float ratio(T a, T c) { return a / c; }
     static __device__ __forceinline__ double inv(T c) { return (double)(1.0f / c); }
     static __device__ __forceinline__ float scale(T a, double inv_c) { return a * (float)inv_c; }
@@ -58,6 +59,7 @@ struct AccFix {   // 64-bit fixed point, exact sums
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
     static __device__ __forceinline__ float ratio(T a, T c) { return (float)((double)a / (double)c); }
     static __device__ __forceinline__ double inv(T c) { return 1.0 / (double)c; }
     static __device__ __forceinline__ float scale(T a, double inv_c) { return (float)((double)a * inv_c); }
@@ -80,6 +82,9 @@ struct AccKahan {   // compensated float pairs: value = hi + lo
     static __device__ __forceinline__ T sub(T a, T b) { return add(a, make_float2(-b.x, -b.y)); }
     static __device__ __forceinline__ T shfl_up(T v, int o) {
         return make_float2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
+    }
+    static __device__ __forceinline__ T shfl(T v, int src) {
+        return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
     }
     static __device__ __forceinline__ float ratio(T a, T c) {
         return (float)(((double)a.x + (double)a.y) / ((double)c.x + (double)c.y));

@@ -475,6 +475,31 @@ def test_every_scan_tile_is_exact_in_fixed_point(tile):
     np.testing.assert_array_equal(B, I["B"])
 
 
+@pytest.mark.parametrize("H", [8, 16])
+@pytest.mark.parametrize("precision", [P.INIM_FIX64, P.INIM_KAHAN, P.INIM_FP32])
+def test_parallel_rows_tiles_at_512(H, precision):
+    # the parallel-rows band scan at N = 512 (two columns a thread in its
+    # second stage, 8-byte windows for four-byte sums): exact in fixed point,
+    # within the bounds of the other precisions
+    k = 9
+    d = texture(k, 78)
+    try:
+        P.inim_set_scan_tile(k, precision, 0, H, 0, 256)
+        got = gpu_inims(d, k, precision, 30)
+    finally:
+        P.inim_set_scan_tile(k, precision, 0, 0, 0, 0)
+    if precision == P.INIM_FIX64:
+        I = O.inims(np.rint(d.astype(np.float64) * 2.0 ** 30).astype(np.int64))
+        for g, o in zip(got, (I["a"], I["at"], I["A"], I["B"])):
+            np.testing.assert_array_equal(g, o)
+        return
+    I = O.inims(d.astype(np.float64))
+    N = 1 << k
+    tol = (2 * (N / 8 + 64) * 2.0 ** -24 if precision == P.INIM_FP32 else 1e-10) * I["C"]
+    for g, o in zip(got, (I["a"], I["at"], I["A"], I["B"])):
+        assert np.abs(g.astype(np.float64) - o).max() <= tol
+
+
 def test_every_scan_tile_gives_identical_iterations_in_fixed_point():
     # the label path (rows staged by bulk copies) in every tile: the 64-bit
     # tables are exact, so the moved vertices must not depend on the tile
