@@ -86,6 +86,7 @@ TRAFFIC = {
     ("chain3", "areas_errors", 8, 0, 256): 1.987e6,
     ("direct72", "scan_phase3", 16, 4, 256): 755.632e6,
     ("direct72", "scan_phase3", 32, 4, 256): 731.673e6,
+    ("direct72", "gather_move", 64, 4, 256): 191.709e6,
 }
 
 
@@ -522,6 +523,64 @@ def batched_config(args):
 
 
 # ---------------------------------------------------------------------------
+# in-graph kernel timeline of both batch shapes of the sweep
+# ---------------------------------------------------------------------------
+def timeline_study(args):
+    """The sweep's two batch shapes run alone (the 72-solve direct batch and
+    the 3-solve batch of the cumulative chain), 50 iterations each under the
+    library's CUDA graphs with programmatic launches, with the kernel
+    timeline on: per kernel the median time from its first block's start to
+    its last block's end, the median gap to the next kernel's first block,
+    and the time per iteration (medians over iterations 5-49).  Scan tiles
+    from --tiles (default: the tiles the sweep uses)."""
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import _lib, synth
+    lib = _lib.load()
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = np.ascontiguousarray(w["values"].astype(np.float32))
+    m = P.inim_map_create(mesh)
+    tl = [tuple(int(x) for x in t.split(",")) for t in args.tiles.split(":")] if args.tiles else \
+        [(64, 4, 256), (8, 0, 256)]
+    P.inim_set_scan_tile(k, P.INIM_FP32, 1, *tl[0])
+    P.inim_set_scan_tile(k, P.INIM_FP32, 0, *tl[1])
+    P.inim_timeline(True)
+    names = P.TIMELINE_KERNELS
+    res = {"timeline": w["name"], "tiles": {"large": tl[0], "small": tl[1]}, "iterations": ITERS, "batches": {}}
+    for name, jobs in (("chain3", [(sh, 0) for sh in SHAPES]),
+                       ("direct72", [(sh, t) for sh in SHAPES for t in range(T_STEPS)])):
+        arr = (P.inim_job * len(jobs))()
+        outs = [np.empty((mesh.n_verts, 2), np.float32) for _ in jobs]
+        for q, (sh, t) in enumerate(jobs):
+            arr[q].map = m.handle
+            arr[q].values = vals[t].ctypes.data
+            arr[q].init_xy = None
+            arr[q].out_xy = outs[q].ctypes.data
+            arr[q].params = P.params(log2_res=k, shape=sh, max_iters=ITERS, xi_stop=0.0, stall_window=0)
+            arr[q].stats = None
+        for _ in range(2):                                # graphs, buffers, warm caches
+            _lib.check(lib.inim_run_batch(arr, len(arr), None), "timeline")
+        P.inim_timeline_read()
+        _lib.check(lib.inim_run_batch(arr, len(arr), None), "timeline")
+        st, en = P.inim_timeline_read()
+        ran = [q for q in range(len(names)) if st[q, 5] > 0]
+        lo, hi = 5, ITERS
+        kern = {names[q]: float(np.median(en[q, lo:hi] - st[q, lo:hi])) / 1e3 for q in ran}
+        path = [q for q in ran if names[q] != "areas_errors"]
+        gaps = {f"{names[a]}->{names[b]}": float(np.median(st[b, lo:hi] - en[a, lo:hi])) / 1e3
+                for a, b in zip(path[:-1], path[1:])}
+        gaps[f"{names[path[-1]]}->next {names[path[0]]}"] = float(
+            np.median(st[path[0], lo + 1:hi] - en[path[-1], lo:hi - 1])) / 1e3
+        res["batches"][name] = {"jobs": len(jobs), "us_per_iteration": float(np.median(np.diff(st[0, lo:hi]))) / 1e3,
+                                "kernel_us": kern, "gap_us": gaps}
+    P.inim_timeline(False)
+    print(json.dumps(res))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # small fixed cases for profiler captures (ncu): one batch, two iterations
 # ---------------------------------------------------------------------------
 def ncu_case(args):
@@ -584,6 +643,8 @@ def main():
     ap.add_argument("--coherence-sigma", type=float, default=0.6)
     ap.add_argument("--quality", type=int, default=0, metavar="K",
                     help="instead of the sweep: time K calls of inim_quality on the sweep's map")
+    ap.add_argument("--timeline", action="store_true",
+                    help="instead of the sweep: in-graph kernel timeline of the sweep's two batch shapes")
     ap.add_argument("--config", choices=["sweep", "batched"], default="sweep",
                     help="batched: the 64-map batched workload instead of the time-varying sweep")
     ap.add_argument("--ncu-case", choices=["direct72", "chain3"], default=None,
@@ -602,6 +663,8 @@ def main():
         return coherence_study(args)
     if args.config == "batched":
         return batched_config(args)
+    if args.timeline:
+        return timeline_study(args)
 
     import torch
     import paper_2604_13880_gb300 as P

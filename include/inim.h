@@ -293,6 +293,24 @@ int inim_set_persistent(int32_t enable);
 int inim_set_single_pass_scan(int32_t enable);
 
 /*
+ * Kernel timeline (a profiling aid; no counterpart in the paper).  With
+ * enable = 1 every batch built afterwards records, per launch of each kernel
+ * of the iteration, when its first block starts working (after waiting for
+ * the previous kernel) and when its last block ends, from the GPU's global
+ * nanosecond timer; the graphs keep their programmatic launches, so the
+ * durations and gaps are those of the real iteration.  Kernels: 0 crossing
+ * keys, 1 rows, 2 scan phase 1 (or the single-pass scan), 3 carries, 4 scan
+ * phase 3, 5 gather and move, 6 areas and errors.  Each kernel keeps its last
+ * 128 launches (slot = launch index mod 128, counted from the last read).
+ * inim_timeline drops the cached batches; enable = 0 frees the buffer.
+ * inim_timeline_read copies start_ns[k * 128 + i] and end_ns[k * 128 + i]
+ * (n >= 8 * 128 entries each, zero where nothing ran) and clears the record;
+ * INIM_E_STATE when the timeline is off.
+ */
+int inim_timeline(int32_t enable);
+int inim_timeline_read(uint64_t* start_ns, uint64_t* end_ns, int32_t n);
+
+/*
  * Failure detection of device-side waits (no counterpart in the paper).
  * The grid barrier of the persistent launch polls at most `spins` times
  * (each poll sleeps up to 256 ns); a wait that runs out records

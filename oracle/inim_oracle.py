@@ -14,11 +14,13 @@ shape blend, the desired area w(v)).
 Pins: every function is checked in ``tests/test_oracle_*.py`` against brute
 force on tiny inputs, closed forms, invariants of Eq. (1)-(3) and hand-derived
 golden values (``tests/golden``); the dynamic-area background of Eq. (Mb) by
-the fixed point of a map at its target area fraction and the direction in
-which a map away from it moves; the animation frames of Sec. 5.5 by closed
-forms.  Parity unpinned by the paper (pinned only
-by the shared reading): the shape-blend reading, the desired area w(v) and
-the pixel-sample convention.
+the fixed point of a map at its target area fraction, the direction in which
+a map away from it moves and hand-worked values away from the target; the
+desired areas and the cartographic errors by hand-worked cases; the
+animation frames of Sec. 5.5 by closed forms.  Readings the paper does not
+fix (pinned only by the shared reading; their arithmetic is pinned as
+above): the shape-blend reading, the definition of the desired area w(v)
+and the pixel-sample convention.
 """
 from __future__ import annotations
 

@@ -342,6 +342,25 @@ def inim_set_single_pass_scan(enable: bool) -> None:
     _lib.check(_lib.load().inim_set_single_pass_scan(1 if enable else 0), "inim_set_single_pass_scan")
 
 
+TIMELINE_KERNELS = ("crossings", "rows", "scan_phase1", "scan_carry", "scan_phase3", "gather_move", "areas_errors")
+
+
+def inim_timeline(enable: bool) -> None:
+    """Record the first-block start and last-block end of every kernel launch of
+    batches built from now on (global-timer ns); False switches it off."""
+    _lib.check(_lib.load().inim_timeline(1 if enable else 0), "inim_timeline")
+
+
+def inim_timeline_read():
+    """(start_ns, end_ns): int64 arrays [8, 128] (kernel, launch slot), 0 where
+    nothing ran; clears the record."""
+    n = 8 * 128
+    a, b = (ctypes.c_uint64 * n)(), (ctypes.c_uint64 * n)()
+    _lib.check(_lib.load().inim_timeline_read(a, b, n), "inim_timeline_read")
+    return (np.frombuffer(a, dtype=np.uint64).astype(np.int64).reshape(8, 128),
+            np.frombuffer(b, dtype=np.uint64).astype(np.int64).reshape(8, 128))
+
+
 def inim_set_wait_cap(spins: int) -> None:
     """Polls of a device-side barrier wait before it gives up (INIM_E_TIMEOUT); <= 0: the default."""
     _lib.check(_lib.load().inim_set_wait_cap(int(spins)), "inim_set_wait_cap")

@@ -229,6 +229,10 @@ struct Group {
 // and their phases run slower next to blocks in other phases.
 int g_single_pass = 0;
 
+// kernel timeline buffer (inim_timeline); set in the jobs of batches built
+// while it is on
+unsigned long long* g_tl = nullptr;
+
 int fused_for(const ScanTile& t, int size_cls, bool maps) {
     return (g_single_pass && maps && t.cpt > 0 && size_cls == 1) ? 1 : 0;
 }
@@ -398,6 +402,7 @@ int build_batch(Batch& B, const std::vector<JobSpec>& spec,
         J.H = tile.H; J.nb = nb; J.agg = b.agg; J.carry = b.carry;
         J.bflags = b.flags; J.binc = b.binc;
         J.areas = b.areas; J.st = B.d_states + k;
+        J.tl = g_tl;
         B.h_jobs[k] = J;
         if (m) {
             for (int q = 0; q < (m->n_edges + kEdgesPerItem - 1) / kEdgesPerItem; ++q) eb.push_back(make_int2(k, q));
@@ -1393,6 +1398,33 @@ int inim_set_single_pass_scan(int32_t enable) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_single_pass = enable ? 1 : 0;
     g_cache.clear();                  // cached batches keep the form they were built with
+    return INIM_OK;
+}
+
+int inim_timeline(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    CUDA_TRY(cudaDeviceSynchronize());
+    g_cache.clear();                  // cached batches carry the buffer pointer (or none)
+    if (enable && !g_tl) {
+        CUDA_TRY(cudaMalloc(&g_tl, kTlWords * sizeof(unsigned long long)));
+        CUDA_TRY(cudaMemset(g_tl, 0, kTlWords * sizeof(unsigned long long)));
+    } else if (!enable && g_tl) {
+        dfree(g_tl);
+    }
+    return INIM_OK;
+}
+
+int inim_timeline_read(uint64_t* start_ns, uint64_t* end_ns, int32_t n) {
+    if (!start_ns || !end_ns || n < kTlKernels * kTlSlots) return fail(INIM_E_ARG, "timeline buffers too small");
+    if (!g_tl) return fail(INIM_E_STATE, "the timeline is off");
+    std::vector<unsigned long long> h(kTlWords);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(h.data(), g_tl, kTlWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(g_tl, 0, kTlWords * sizeof(unsigned long long)));
+    for (int i = 0; i < kTlKernels * kTlSlots; ++i) {
+        start_ns[i] = h[i];
+        end_ns[i] = h[kTlEnd + i];
+    }
     return INIM_OK;
 }
 

@@ -24,7 +24,9 @@ __global__ void __launch_bounds__(256) k_areas_errors(const Job* __restrict__ jo
     const AreaPre pre = areas_prefetch(J, m.y);
     pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
+    tl_begin(J.tl, kTlAreas);
     areas_body(J, m.y, update_state, pre);
+    tl_end(J.tl, kTlAreas);
     pdl_release();
 }
 

@@ -29,7 +29,9 @@ __global__ void __launch_bounds__(256) k_gather_move(const Job* __restrict__ job
     const float2 p = J.xy[v];
     const typename Acc::T C = grand_total<Acc>(J);
     if (!act) return;
+    tl_begin(J.tl, kTlGather);
     move_vertex<Acc>(J, v, p, C);
+    tl_end(J.tl, kTlGather);
     pdl_release();
 }
 

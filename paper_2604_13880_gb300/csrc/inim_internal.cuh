@@ -97,6 +97,7 @@ struct Job {
     // areas and errors
     double*   areas;           // [n_regions] signed shoelace areas
     JobState* st;
+    unsigned long long* tl;    // kernel timeline (inim_timeline), NULL when off
 };
 
 // Warps per region (log2) of a job: about 128 edges per warp, 1..8 warps.
@@ -129,6 +130,40 @@ __device__ __forceinline__ void pdl_start(bool early) {
 }
 
 bool pdl_enabled();   // INIM_PDL=0 in the environment turns the attribute off
+
+// ---------------------------------------------------------------------------
+// kernel timeline (inim_timeline): per kernel of the iteration and per launch,
+// the time the first block starts its work (after the programmatic-launch
+// wait) and the time the last block ends, from the GPU's global timer.
+// Layout of the buffer (64-bit words): start[k][i] at k * kTlSlots + i,
+// end[k][i] at kTlEnd + k * kTlSlots + i, launch i modulo kTlSlots; block
+// counters (32-bit) after kTlCount.  Kernel ids: kTl* below.
+// ---------------------------------------------------------------------------
+constexpr int kTlSlots = 128, kTlKernels = 8, kTlEnd = kTlKernels * kTlSlots, kTlCount = 2 * kTlEnd;
+constexpr int kTlWords = kTlCount + kTlKernels;          // + 2 x 8 32-bit counters
+enum { kTlCrossings = 0, kTlRows, kTlScan1, kTlCarry, kTlScan3, kTlGather, kTlAreas };
+
+__device__ __forceinline__ unsigned long long tl_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// thread 0 of every block; the first block of a launch records its start
+__device__ __forceinline__ void tl_begin(unsigned long long* tl, int k) {
+    if (!tl || threadIdx.x != 0) return;
+    const unsigned long long t = tl_now();
+    unsigned* c = reinterpret_cast<unsigned*>(tl + kTlCount);
+    const unsigned old = atomicAdd(c + k, 1u);
+    if (old % gridDim.x == 0) tl[k * kTlSlots + (old / gridDim.x) % kTlSlots] = t;
+}
+// thread 0 of every block; the last block of a launch records its end
+__device__ __forceinline__ void tl_end(unsigned long long* tl, int k) {
+    if (!tl || threadIdx.x != 0) return;
+    const unsigned long long t = tl_now();
+    unsigned* c = reinterpret_cast<unsigned*>(tl + kTlCount);
+    const unsigned old = atomicAdd(c + kTlKernels + k, 1u);
+    if (old % gridDim.x == gridDim.x - 1) tl[kTlEnd + k * kTlSlots + (old / gridDim.x) % kTlSlots] = t;
+}
 
 // records msg as the calling thread's last error (inim_last_error) and
 // returns code

@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(256, 5) k_crossings(const Job* __restrict__ jo
         }
     }
     if (!act) return;
+    tl_begin(J.tl, kTlCrossings);
     emit_crossings_lane<kEdgesPerLane>(J, valid, reg, p, q);
     if (m.y == 0) reset_raster_block(J);
+    tl_end(J.tl, kTlCrossings);
     pdl_release();
 }
 
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5) k_raster_rows(const Jo
     const int2 m = bmap[blockIdx.x];                 // (job, first row)
     const Job J = jobs[m.x];                         // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
+    tl_begin(J.tl, kTlRows);
     const int jb = raster_rows_item(J, m.y, rows_smem, true, true);
     if ((threadIdx.x & 31) == 0) big[threadIdx.x >> 5] = jb;
     __syncthreads();
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5) k_raster_rows(const Jo
             __syncthreads();
         }
     }
+    tl_end(J.tl, kTlRows);
     pdl_release();
 }
 

@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<Acc, CPT, NT>())) k_scan
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
+    tl_begin(J.tl, kTlScan1);
     const int band = m.y, n = J.n, nb = J.nb, H = J.H;
     uint16_t* ring_rows = reinterpret_cast<uint16_t*>(scan_ring);
     unsigned* my_flag = J.bflags + band;
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<Acc, CPT, NT>())) k_scan
     //    to it after the block barrier)
     scan_band_body<Acc, CPT, NT, 3, kLabelDepth>(J, band, nullptr, sh, LabelRing<kLabelDepth>{ring_rows, bars3}, false,
                                                  fix_bits, nullptr);
+    tl_end(J.tl, kTlScan1);
     pdl_release();
 }
 

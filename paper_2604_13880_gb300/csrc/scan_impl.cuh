@@ -491,8 +491,10 @@ __global__ void __launch_bounds__(NT) k_scan_band(const Job* __restrict__ jobs,
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
+    tl_begin(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
     LabelRing<kLabelDepth> ring{reinterpret_cast<uint16_t*>(scan_ring), bars};
     scan_band_body<Acc, CPT, NT, PHASE, kLabelDepth>(J, m.y, dtex, sh, ring, J.fuse_table != 0);
+    tl_end(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
     pdl_release();
 }
 
@@ -585,7 +587,9 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
+    tl_begin(J.tl, kTlCarry);
     scan_carry_body<Acc>(J, m.y * blockDim.x + threadIdx.x);
+    tl_end(J.tl, kTlCarry);
 }
 
 // Two-level form of the same carries, for many short bands: a block covers
@@ -615,6 +619,7 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
+    tl_begin(J.tl, kTlCarry);
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int nb = J.nb;
     int q = m.y * 32 + lane;
@@ -650,6 +655,7 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
             }
         }
     }
+    tl_end(J.tl, kTlCarry);
     pdl_release();
 }
 

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
     if (!J.st->active) return;
+    tl_begin(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
     const int band = m.y, nb = J.nb, j0 = band * H;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool from_labels = (dtex == nullptr);
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
             }
         }
     }
+    tl_end(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
     pdl_release();
     if constexpr (PHASE == 1) {
         T* agg = reinterpret_cast<T*>(J.agg);
