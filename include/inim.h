@@ -430,27 +430,46 @@ int inim_inims_noalloc(const float* density, int32_t log2_res, float* S, float* 
 int inim_density_pooled(const inim_map* map, const float* xy, int32_t log2_res, const float* values,
                         int32_t pool, float* out, void* stream);
 
-typedef struct inim_cnn inim_cnn;   /* encoder-decoder CNN, 64^2 -> 64^2 x 2 */
+typedef struct inim_cnn inim_cnn;   /* encoder-decoder CNN, r^2 -> 64^2 x 2, r = 64, 128 or 256 */
 
-/* Create with He-initialised weights (seeded); 1,163,234 f32 parameters. */
+/* Create with He-initialised weights (seeded); 1,163,234 f32 parameters;
+ * input resolution 64^2. */
 int inim_cnn_create(int32_t seed, inim_cnn** out);
+/*
+ * The same network for an input of in_res^2 (64, 128 or 256; else
+ * INIM_E_ARG): the first convolution (1 -> 32 channels) runs at in_res and its
+ * output is 2x2 average-pooled down to 64^2 before the second; the parameter
+ * blob is the same.  inim_cnn_input_res returns in_res.
+ */
+int inim_cnn_create_res(int32_t seed, int32_t in_res, inim_cnn** out);
+int inim_cnn_input_res(const inim_cnn* cnn);
 int inim_cnn_destroy(inim_cnn* cnn);
 long long inim_cnn_num_params(const inim_cnn* cnn);   /* cnn may be NULL */
 /* Parameter blob (per layer: weights [cout][3][3][cin], bias [cout]) to / from host or device. */
 int inim_cnn_get_params(const inim_cnn* cnn, float* out, long long n);
 int inim_cnn_set_params(inim_cnn* cnn, const float* in, long long n);
 /*
- * x: [B][64][64] f32 pooled log densities, y: [B][64][64][2] f32 predicted
- * displacement x 10 (unit-square units); device memory.
+ * x: [B][r][r] f32 pooled log densities (r = the input resolution), y:
+ * [B][64][64][2] f32 predicted displacement x 10 (unit-square units); device
+ * memory.
  */
 int inim_cnn_forward(inim_cnn* cnn, const float* x, int32_t B, float* y, void* stream);
 /* Mean squared error against targets y and its gradient w.r.t. every parameter
  * (grads: host or device [n_params], may be NULL; loss: host, may be NULL). */
 int inim_cnn_gradients(inim_cnn* cnn, const float* x, const float* y, int32_t B, float* loss, float* grads,
                        void* stream);
-/* One Adam step (beta 0.9 / 0.999) on the mean squared error. */
+/*
+ * One Adam step (beta 0.9 / 0.999) on the mean squared error.  x and y are
+ * copied on `stream` (after its earlier work; the caller may reuse them in
+ * that stream's order); the step then runs on the network's own stream.  With
+ * loss != NULL (host) the call waits for the step and returns its loss; with
+ * loss = NULL it returns at once, and inim_cnn_loss_mean later gives the mean
+ * loss of the steps since its previous call.  Calls on one network are
+ * ordered.
+ */
 int inim_cnn_train_step(inim_cnn* cnn, const float* x, const float* y, int32_t B, float lr, float* loss,
                         void* stream);
+int inim_cnn_loss_mean(inim_cnn* cnn, double* mean);
 const char* inim_cnn_last_error(void);
 
 /*
@@ -460,6 +479,9 @@ const char* inim_cnn_last_error(void);
  * iterate as usual.
  */
 int inim_warmstart_load(const void* weights, size_t bytes);
+/* The same for a network of input resolution in_res (64, 128 or 256): the
+ * solve's density texture is pooled by N / in_res (N >= in_res). */
+int inim_warmstart_load_res(const void* weights, size_t bytes, int32_t in_res);
 
 /* ---------------- scan tiles and their autotuner ------------------------- */
 
@@ -495,12 +517,16 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps);
 /*
  * Average device time of every kernel stage of one fused iteration of the
  * batch used most recently by inim_run / inim_run_batch / inim_iterate: each
- * stage is launched `reps` times back to back between two CUDA events on the
- * library's stream (ms[i] = elapsed / reps).  Stages, in iteration order:
+ * stage is launched `reps` times back to back, captured into one CUDA graph
+ * (with programmatic dependent launch, as in the iteration graphs), and one
+ * replay is timed between two CUDA events on the library's stream
+ * (ms[i] = elapsed / reps).  Stages, in iteration order:
  * crossings, raster_rows, density_table, scan_phase1, scan_carry,
  * scan_phase3, gather_move, areas_errors, scan_fused (names from
- * inim_stage_name); the two raster kernels run as pairs, each timed between
- * its own events.  For batches whose maps have at most 2047 regions the
+ * inim_stage_name); the two raster kernels run as pairs: the crossing kernel
+ * is timed alone (its keys overflow the buckets, whose guard skips the
+ * stores) and the rows get the pairs' time minus that; the buckets are
+ * emptied afterwards.  For batches whose maps have at most 2047 regions the
  * density table is built by scan_phase1 (there is no density_table kernel in
  * the iteration) and ms[2] = 0.  Large batches (at least 2^23 pixels per
  * resolution) scan in one pass: scan_fused holds that kernel and the three

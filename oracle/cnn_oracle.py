@@ -22,7 +22,10 @@ Pins (tests/test_oracle_cnn.py): the convolution against its definition
 written as explicit loops on tiny inputs, every gradient against central
 finite differences, and the BF16 rounding against the bit patterns of its
 definition.  The network is resolution-generic here (any input side
-divisible by 8) so that the pins run on small inputs.
+divisible by 8) so that the pins run on small inputs.  stem = s (1 or 2)
+gives the library's higher-resolution input variant: the first convolution
+runs on the input of side 2^s x the rest's and its output is 2x2
+average-pooled s times before the second convolution.
 """
 from __future__ import annotations
 
@@ -107,9 +110,10 @@ def up2_backward(gy):
     return gy.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def forward(params, x, bf16=False):
-    """x [N, H, W] pooled log densities -> (prediction [N, H, W, 2], saved tensors).
-    bf16: round what the library stores in BF16 (see the module docstring)."""
+def forward(params, x, bf16=False, stem=0):
+    """x [N, H, W] pooled log densities -> (prediction [N, H / 2^stem, W / 2^stem, 2],
+    saved tensors).  bf16: round what the library stores in BF16 (see the
+    module docstring); stem: pools after the first convolution."""
     r = bf16_round if bf16 else (lambda a: a)
     P = unpack(params)
     if bf16:
@@ -122,7 +126,12 @@ def forward(params, x, bf16=False):
             return r(np.maximum(y, 0.0))
         return y                                  # the linear head: full precision
 
-    s["a0"] = L(0, s["x0"]); s["e1"] = L(1, s["a0"]); s["p1"] = r(pool2(s["e1"]))
+    s["a0f"] = L(0, s["x0"])                      # the first convolution at the input resolution
+    a0 = s["a0f"]
+    for _ in range(stem):
+        a0 = r(pool2(a0))
+    s["a0"] = a0
+    s["e1"] = L(1, s["a0"]); s["p1"] = r(pool2(s["e1"]))
     s["a2"] = L(2, s["p1"]); s["e2"] = L(3, s["a2"]); s["p2"] = r(pool2(s["e2"]))
     s["a4"] = L(4, s["p2"]); s["e3"] = L(5, s["a4"]); s["p3"] = r(pool2(s["e3"]))
     s["bt"] = L(6, s["p3"]); s["u3"] = up2(s["bt"])
@@ -133,7 +142,7 @@ def forward(params, x, bf16=False):
     return s["out"], s
 
 
-def loss_and_grads(params, x, target, bf16=False, saved=None):
+def loss_and_grads(params, x, target, bf16=False, saved=None, stem=0):
     """Mean squared error over all outputs and its gradient blob.  bf16: the
     forward and backward roundings of the library (module docstring).
     saved: a dict that receives every stored activation gradient by name."""
@@ -141,7 +150,7 @@ def loss_and_grads(params, x, target, bf16=False, saved=None):
     P = unpack(params)
     if bf16:
         P = [(r(w), b) for w, b in P]
-    out, s = forward(params, x, bf16=bf16)
+    out, s = forward(params, x, bf16=bf16, stem=stem)
     n = out.size
     loss = float(((out - target) ** 2).sum() / n)
     g = [None] * len(LAYERS)
@@ -173,7 +182,9 @@ def loss_and_grads(params, x, target, bf16=False, saved=None):
     gp1 = back(2, ga2, s["p1"], s["a2"])
     ge1 = r(r(pool2_backward(gp1)) + gd1)
     ga0 = back(1, ge1, s["a0"], s["e1"])
-    back(0, ga0, s["x0"], s["a0"])
+    for _ in range(stem):                          # back through the stem's pools
+        ga0 = r(pool2_backward(ga0))
+    back(0, ga0, s["x0"], s["a0f"])
     if saved is not None:
         saved.update(gout=gout, gd1b=gd1b, gd1=gd1, gu1=gu1, gd2b=gd2b, gd2=gd2, gu2=gu2, gd3b=gd3b, gd3=gd3,
                      gu3=gu3, gbt=gbt, gp3=gp3, ge3=ge3, ga4=ga4, gp2=gp2, ge2=ge2, ga2=ga2, gp1=gp1, ge1=ge1,

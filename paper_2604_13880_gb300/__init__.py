@@ -386,14 +386,15 @@ def inim_density_pooled(m: Map, xy, log2_res: int, values, pool: int, out, strea
 
 
 class Cnn:
-    """Owner of an inim_cnn handle (encoder-decoder, 64^2 -> 64^2 x 2)."""
+    """Owner of an inim_cnn handle (encoder-decoder, in_res^2 -> 64^2 x 2)."""
 
-    def __init__(self, seed: int = 0):
+    def __init__(self, seed: int = 0, in_res: int = 64):
         lib = _lib.load()
         h = ctypes.c_void_p()
-        _lib.check_cnn(lib.inim_cnn_create(seed, ctypes.byref(h)), "inim_cnn_create")
+        _lib.check_cnn(lib.inim_cnn_create_res(seed, in_res, ctypes.byref(h)), "inim_cnn_create_res")
         self.handle = h.value
         self.n_params = int(lib.inim_cnn_num_params(self.handle))
+        self.in_res = int(lib.inim_cnn_input_res(self.handle))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -407,8 +408,8 @@ class Cnn:
             pass
 
 
-def inim_cnn_create(seed: int = 0) -> Cnn:
-    return Cnn(seed)
+def inim_cnn_create(seed: int = 0, in_res: int = 64) -> Cnn:
+    return Cnn(seed, in_res)
 
 
 def inim_cnn_destroy(c: Cnn) -> None:
@@ -432,14 +433,31 @@ def inim_cnn_set_params(c: Cnn, blob) -> None:
     _lib.check_cnn(_lib.load().inim_cnn_set_params(c.handle, _lib.ptr(blob), c.n_params), "inim_cnn_set_params")
 
 
+def _cnn_shapes(c: Cnn, x, y) -> None:
+    """The C entry points take only the batch size: the binding checks the rest
+    of both shapes, so that no call reads or writes past a tensor."""
+    B = int(x.shape[0])
+    if tuple(x.shape) != (B, c.in_res, c.in_res):
+        raise ValueError(f"input of shape {tuple(x.shape)}; this network takes [B, {c.in_res}, {c.in_res}]")
+    if tuple(y.shape) != (B, 64, 64, 2):
+        raise ValueError(f"field of shape {tuple(y.shape)}; expected [{B}, 64, 64, 2]")
+    for t in (x, y):
+        if hasattr(t, "is_contiguous") and not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
 def inim_cnn_forward(c: Cnn, x, y, stream=None) -> None:
-    """x [B, 64, 64] f32, y [B, 64, 64, 2] f32; device tensors."""
+    """x [B, in_res, in_res] f32, y [B, 64, 64, 2] f32; device tensors."""
+    _cnn_shapes(c, x, y)
     _lib.check_cnn(_lib.load().inim_cnn_forward(c.handle, _lib.ptr(x), int(x.shape[0]), _lib.ptr(y),
                                                 stream or _lib.stream_of(x)), "inim_cnn_forward")
 
 
 def inim_cnn_gradients(c: Cnn, x, y, grads=None, stream=None) -> float:
     """Mean squared error of the prediction for x against y; its gradient into grads [n_params]."""
+    _cnn_shapes(c, x, y)
+    if grads is not None and int(np.prod(grads.shape)) != c.n_params:
+        raise ValueError(f"gradient buffer of {int(np.prod(grads.shape))} values; expected {c.n_params}")
     loss = ctypes.c_float()
     _lib.check_cnn(_lib.load().inim_cnn_gradients(c.handle, _lib.ptr(x), _lib.ptr(y), int(x.shape[0]),
                                                   ctypes.byref(loss), _lib.ptr(grads), stream or _lib.stream_of(x)),
@@ -447,16 +465,28 @@ def inim_cnn_gradients(c: Cnn, x, y, grads=None, stream=None) -> float:
     return loss.value
 
 
-def inim_cnn_train_step(c: Cnn, x, y, lr: float, stream=None) -> float:
-    """One Adam step; returns the batch loss before the step."""
+def inim_cnn_train_step(c: Cnn, x, y, lr: float, stream=None, wait: bool = True):
+    """One Adam step; returns the batch loss before the step (wait=True), or
+    None without waiting for the step (wait=False; see inim_cnn_loss_mean)."""
+    _cnn_shapes(c, x, y)
     loss = ctypes.c_float()
     _lib.check_cnn(_lib.load().inim_cnn_train_step(c.handle, _lib.ptr(x), _lib.ptr(y), int(x.shape[0]), lr,
-                                                   ctypes.byref(loss), stream or _lib.stream_of(x)),
+                                                   ctypes.byref(loss) if wait else None,
+                                                   stream or _lib.stream_of(x)),
                    "inim_cnn_train_step")
-    return loss.value
+    return loss.value if wait else None
 
 
-def inim_warmstart_load(blob) -> None:
-    """Install the network used by params(warm_start=1) (an f32 parameter blob)."""
+def inim_cnn_loss_mean(c: Cnn) -> float:
+    """Mean loss of the training steps since the previous call (waits for them)."""
+    m = ctypes.c_double()
+    _lib.check_cnn(_lib.load().inim_cnn_loss_mean(c.handle, ctypes.byref(m)), "inim_cnn_loss_mean")
+    return m.value
+
+
+def inim_warmstart_load(blob, in_res: int = 64) -> None:
+    """Install the network used by params(warm_start=1) (an f32 parameter blob
+    of a network with the given input resolution)."""
     blob = np.ascontiguousarray(blob, dtype=np.float32)
-    _lib.check_cnn(_lib.load().inim_warmstart_load(blob.ctypes.data, blob.nbytes), "inim_warmstart_load")
+    _lib.check_cnn(_lib.load().inim_warmstart_load_res(blob.ctypes.data, blob.nbytes, int(in_res)),
+                   "inim_warmstart_load_res")

@@ -144,7 +144,11 @@ _SIGS = {
     "inim_cnn_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "inim_cnn_last_error": (ctypes.c_char_p, []),
+    "inim_cnn_loss_mean": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "inim_warmstart_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t]),
+    "inim_warmstart_load_res": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]),
+    "inim_cnn_create_res": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "inim_cnn_input_res": (ctypes.c_int, [ctypes.c_void_p]),
     "inim_set_scan_tile": (ctypes.c_int, [ctypes.c_int32] * 6),
     "inim_get_scan_tile": (ctypes.c_int, [ctypes.c_int32] * 3 + [ctypes.POINTER(ctypes.c_int32)] * 3),
     "inim_autotune_scan": (ctypes.c_int, [ctypes.POINTER(inim_job), ctypes.c_int32, ctypes.c_int32]),

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <functional>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -300,6 +301,7 @@ struct Batch {
     // learned warm start: pooled inputs, predicted fields, per-job field pointers
     float* ws_in = nullptr;
     float* ws_out = nullptr;
+    int ws_res = 0;                      // input resolution ws_in was sized for
     const float** ws_ptrs = nullptr;
 
     void free_rounds() {
@@ -880,18 +882,22 @@ int apply_warm_start(Batch& B, const std::vector<char>& warm) {
     for (int k = 0; k < nj; ++k) if (warm[k]) idx.push_back(k);
     if (idx.empty()) return INIM_OK;
     const size_t cell = (size_t)kFieldRes * kFieldRes;
-    if (!B.ws_in) {
-        CUDA_TRY(cudaMalloc(&B.ws_in, nj * cell * sizeof(float)));
+    const int in_res = warmstart_input_res();          // the network's input: N / in_res pooling
+    const size_t in_cell = (size_t)in_res * in_res;
+    if (!B.ws_in || B.ws_res != in_res) {
+        dfree(B.ws_in); dfree(B.ws_out); dfree(B.ws_ptrs);
+        CUDA_TRY(cudaMalloc(&B.ws_in, nj * in_cell * sizeof(float)));
         CUDA_TRY(cudaMalloc(&B.ws_out, nj * cell * 2 * sizeof(float)));
         CUDA_TRY(cudaMalloc(&B.ws_ptrs, nj * sizeof(float*)));
+        B.ws_res = in_res;
     }
     CUDA_TRY(enqueue_prologue(B, B.stream));
     CUDA_TRY(launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream));
     CUDA_TRY(launch_density_table(B.d_jobs, nj, B.stream));
     for (int q = 0; q < (int)idx.size(); ++q) {
         const Job& J = B.h_jobs[idx[q]];
-        if (J.n % kFieldRes) return fail(INIM_E_ARG, "warm start needs N >= 64");
-        CUDA_TRY(launch_density_pooled(B.d_jobs + idx[q], J.n, J.n / kFieldRes, B.ws_in + q * cell, B.stream));
+        if (J.n < in_res || J.n % in_res) return fail(INIM_E_ARG, "warm start needs N >= the network's input resolution");
+        CUDA_TRY(launch_density_pooled(B.d_jobs + idx[q], J.n, J.n / in_res, B.ws_in + q * in_cell, B.stream));
     }
     const int st = warmstart_predict(B.ws_in, (int)idx.size(), B.ws_out, B.stream);
     if (st != INIM_OK) return fail(st, "warm-start prediction failed");
@@ -1978,45 +1984,54 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
         }
     };
     int rc = INIM_OK;
-    // the rasteriser's two kernels only run as a pair (the rows empty the
-    // buckets the crossings fill): events around each, summed over the pairs
+    // reps launches captured into one CUDA graph (with the launches'
+    // programmatic dependent-launch edges, as in the iteration graphs), timed
+    // between two events around one replay: the host's launch rate does not
+    // enter the per-launch time
+    auto graph_ms = [&](const std::function<cudaError_t()>& fn, float* out) -> cudaError_t {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = fn();
+        const cudaError_t e2 = cudaStreamEndCapture(B.stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, B.stream);                 // warm
+        if (e == cudaSuccess) e = cudaEventRecord(e0, B.stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, B.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, B.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        *out = t / (float)reps;
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        return e;
+    };
+    // the rasteriser's two kernels run as pairs (the rows empty the buckets
+    // the crossings fill); the crossing kernel alone is timed on its own graph
+    // (its keys then overflow the buckets, whose guard skips the stores) and
+    // the rows get the difference; the buckets are emptied afterwards
     {
-        cudaEvent_t ev[3];
-        for (auto& x : ev) CUDA_TRY(cudaEventCreate(&x));
-        cudaError_t e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream);   // warm
-        float tc = 0.0f, tr = 0.0f;
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-            e = cudaEventRecord(ev[0], B.stream);
-            if (e == cudaSuccess) e = launch_raster_crossings(B.d_jobs, B.edge_blocks, B.stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[1], B.stream);
-            if (e == cudaSuccess) e = launch_raster_rows(B.d_jobs, B.row_blocks, B.max_n, B.stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2], B.stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-            float a = 0.0f, b = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
-            tc += a;
-            tr += b;
-        }
-        for (auto& x : ev) cudaEventDestroy(x);
+        float t_pair = 0.0f, t_c = 0.0f;
+        cudaError_t e = graph_ms([&] { return launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n,
+                                                                 B.stream); }, &t_pair);
+        if (e == cudaSuccess) e = graph_ms([&] { return launch_raster_crossings(B.d_jobs, B.edge_blocks, B.stream); },
+                                           &t_c);
+        if (e == cudaSuccess) e = launch_raster_prologue(B.d_jobs, nj, B.edge_blocks, B.stream);
+        if (e == cudaSuccess) e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, B.stream);
         if (e != cudaSuccess) rc = fail(INIM_E_CUDA, std::string("profile: ") + cudaGetErrorString(e));
-        ms[0] = tc / (float)reps;
-        ms[1] = tr / (float)reps;
+        ms[0] = t_c;
+        ms[1] = t_pair > t_c ? t_pair - t_c : 0.0f;
     }
     for (int i = 2; i < kNumStages && rc == INIM_OK; ++i) {
         if (i == 2 && B.fuse_table) { ms[i] = 0.0f; continue; }     // built by the scan's first phase
         bool any_fused = false, any_split = false;
         for (auto& g : B.groups) (g.tile.fused ? any_fused : any_split) = true;
         if ((i >= 3 && i <= 5 && !any_split) || (i == 8 && !any_fused)) { ms[i] = 0.0f; continue; }
-        cudaError_t e = stage(i);                       // warm
-        if (e == cudaSuccess) e = cudaEventRecord(e0, B.stream);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = stage(i);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, B.stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float t = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        const cudaError_t e = graph_ms([&] { return stage(i); }, &ms[i]);
         if (e != cudaSuccess) rc = fail(INIM_E_CUDA, std::string("profile: ") + cudaGetErrorString(e));
-        ms[i] = t / (float)reps;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -13,6 +13,12 @@
 //   64^2:  conv 64->32 + e1, conv 32->32, conv 32->2 (linear)
 // Every conv is 3x3, stride 1, padding 1, followed by ReLU except the last;
 // pooling is 2x2 average, up-sampling nearest.  1,163,234 parameters.
+//
+// Input resolution: 64^2 by default; a network created with a 128^2 or
+// 256^2 input (the density texture pooled less) runs its first convolution
+// (1 -> 32) at that resolution and average-pools its output down to 64^2
+// (a stem), the rest unchanged: the same parameters, more detail seen by
+// the first layer.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -81,23 +87,39 @@ struct inim_cnn {
     __nv_bfloat16* wb[kLayers] = {};     // bf16 weights [cout][9][cin]
     __nv_bfloat16* wf[kLayers] = {};     // bf16 flipped weights [cin][9][cout] (data gradient)
     int step = 0;
+    int in_res = 64;                     // input resolution: 64, 128 or 256
+    int stem = 0;                        // log2(in_res / 64): pools after the first convolution
+    // stem tensors (stem > 0): [0] the input (1 channel, in_res^2), [1 + k]
+    // the first convolution's output pooled k times (32 channels)
+    std::vector<__nv_bfloat16*> s_act, s_grd;
     // activations / gradients for a batch of B
     int B = 0;
     std::vector<__nv_bfloat16*> act, grd;
     float* out = nullptr;                // [B][64][64][2]
     float* loss = nullptr;               // device scalar
+    double* loss_sum = nullptr;          // device: sum of the step losses since the last read
+    int loss_steps = 0;                  // steps in loss_sum
+    float* xin = nullptr;                // training inputs copied on the caller's stream
+    float* yin = nullptr;
+    int in_B = 0;                        // batch the copies are sized for
+    cudaEvent_t ev_in = nullptr;         // the copies are done (caller's stream)
+    cudaEvent_t ev_done = nullptr;       // the last step's kernels are done (network's stream)
     cudaStream_t stream = nullptr;
 
     ~inim_cnn() {
         release_batch();
         for (int l = 0; l < kLayers; ++l) { dfree(wb[l]); dfree(wf[l]); }
-        dfree(params); dfree(grads); dfree(m1); dfree(m2); dfree(loss);
+        dfree(params); dfree(grads); dfree(m1); dfree(m2); dfree(loss); dfree(loss_sum); dfree(xin); dfree(yin);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_done) cudaEventDestroy(ev_done);
         if (stream) cudaStreamDestroy(stream);
     }
     void release_batch() {
         for (auto& p : act) dfree(p);
         for (auto& p : grd) dfree(p);
-        act.clear(); grd.clear();
+        for (auto& p : s_act) dfree(p);
+        for (auto& p : s_grd) dfree(p);
+        act.clear(); grd.clear(); s_act.clear(); s_grd.clear();
         dfree(out);
         B = 0;
     }
@@ -123,6 +145,16 @@ int ensure_batch(inim_cnn& c, int B) {
         CK(cudaMalloc(&c.act[t], tsize(t, B) * sizeof(__nv_bfloat16)));
         CK(cudaMalloc(&c.grd[t], tsize(t, B) * sizeof(__nv_bfloat16)));
     }
+    if (c.stem > 0) {
+        c.s_act.assign(c.stem + 1, nullptr);
+        c.s_grd.assign(c.stem + 1, nullptr);
+        for (int k = 0; k <= c.stem; ++k) {
+            const size_t r = (size_t)(k == 0 ? c.in_res : c.in_res >> (k - 1));
+            const size_t n = (size_t)B * r * r * (k == 0 ? 1 : 32);
+            CK(cudaMalloc(&c.s_act[k], n * sizeof(__nv_bfloat16)));
+            CK(cudaMalloc(&c.s_grd[k], n * sizeof(__nv_bfloat16)));
+        }
+    }
     CK(cudaMalloc(&c.out, (size_t)B * kRes * kRes * 2 * sizeof(float)));
     c.B = B;
     return INIM_OK;
@@ -147,15 +179,18 @@ void conv(inim_cnn& c, int B, int res, const __nv_bfloat16* x, const __nv_bfloat
     k_conv3x3_fwd<<<grid, kConvThreads, 0, c.stream>>>(a);
 }
 
-void layer_fwd(inim_cnn& c, int l, int B, const __nv_bfloat16* x, __nv_bfloat16* y, float* yf = nullptr) {
+void layer_fwd(inim_cnn& c, int l, int B, const __nv_bfloat16* x, __nv_bfloat16* y, float* yf = nullptr,
+               int res = 0) {
     const LayerSpec& s = kSpec[l];
-    conv(c, B, s.res, x, c.wb[l], c.params + c.b_off[l], s.cin, s.cout, s.relu, y, yf);
+    conv(c, B, res ? res : s.res, x, c.wb[l], c.params + c.b_off[l], s.cin, s.cout, s.relu, y, yf);
 }
 
 // weight / bias gradient of layer l from dz (already masked) and its input x;
 // the data gradient into dx when dx != nullptr
-void layer_bwd(inim_cnn& c, int l, int B, const __nv_bfloat16* dz, const __nv_bfloat16* x, __nv_bfloat16* dx) {
-    const LayerSpec& s = kSpec[l];
+void layer_bwd(inim_cnn& c, int l, int B, const __nv_bfloat16* dz, const __nv_bfloat16* x, __nv_bfloat16* dx,
+               int res_override = 0) {
+    LayerSpec s = kSpec[l];
+    if (res_override) s.res = res_override;
     const int P = B * s.res * s.res;
     WgradArgs a{};
     a.dz = dz; a.x = x; a.dw = c.grads + c.w_off[l];
@@ -180,9 +215,23 @@ int forward(inim_cnn& c, const float* x, int B) {
     int st = ensure_batch(c, B);
     if (st != INIM_OK) return st;
     auto& A = c.act;
-    const size_t n0 = (size_t)B * kRes * kRes;
-    k_to_bf16<<<grid_for(n0), 256, 0, c.stream>>>(A[X0], x, n0);
-    layer_fwd(c, 0, B, A[X0], A[A0]);
+    if (c.stem > 0) {
+        // stem: the first convolution at the input resolution, then 2x2
+        // average pools down to 64^2
+        auto& S = c.s_act;
+        const size_t n0 = (size_t)B * c.in_res * c.in_res;
+        k_to_bf16<<<grid_for(n0), 256, 0, c.stream>>>(S[0], x, n0);
+        layer_fwd(c, 0, B, S[0], S[1], nullptr, c.in_res);
+        for (int k = 1; k <= c.stem; ++k) {
+            const int r = c.in_res >> (k - 1);
+            __nv_bfloat16* dst = k == c.stem ? A[A0] : S[k + 1];
+            k_pool2<<<grid_for((size_t)B * (r / 2) * (r / 2) * 32), 256, 0, c.stream>>>(dst, S[k], B, r, r, 32);
+        }
+    } else {
+        const size_t n0 = (size_t)B * kRes * kRes;
+        k_to_bf16<<<grid_for(n0), 256, 0, c.stream>>>(A[X0], x, n0);
+        layer_fwd(c, 0, B, A[X0], A[A0]);
+    }
     layer_fwd(c, 1, B, A[A0], A[E1]);
     k_pool2<<<grid_for(tsize(P1, B)), 256, 0, c.stream>>>(A[P1], A[E1], B, 64, 64, 32);
     layer_fwd(c, 2, B, A[P1], A[A2]);
@@ -256,8 +305,23 @@ int backward(inim_cnn& c, const float* y, int B) {
     k_accum<<<grid_for(tsize(E1, B)), 256, 0, c.stream>>>(G[E1], G[D1], tsize(E1, B));   // skip into d1
     relu_grad(c, E1, B);
     layer_bwd(c, 1, B, G[E1], A[A0], G[A0]);
-    relu_grad(c, A0, B);
-    layer_bwd(c, 0, B, G[A0], A[X0], nullptr);
+    if (c.stem > 0) {
+        // back through the stem's pools to the first convolution's output,
+        // its ReLU mask, and its weights at the input resolution
+        auto& S = c.s_act;
+        auto& GS = c.s_grd;
+        for (int k = c.stem; k >= 1; --k) {
+            const int r = c.in_res >> (k - 1);
+            const __nv_bfloat16* src = k == c.stem ? G[A0] : GS[k + 1];
+            k_pool2_grad<<<grid_for((size_t)B * r * r * 32), 256, 0, c.stream>>>(GS[k], src, B, r, r, 32);
+        }
+        const size_t n1 = (size_t)B * c.in_res * c.in_res * 32;
+        k_relu_grad<<<grid_for(n1), 256, 0, c.stream>>>(GS[1], S[1], n1);
+        layer_bwd(c, 0, B, GS[1], S[0], nullptr, c.in_res);
+    } else {
+        relu_grad(c, A0, B);
+        layer_bwd(c, 0, B, G[A0], A[X0], nullptr);
+    }
     CK(cudaGetLastError());
     return INIM_OK;
 }
@@ -291,13 +355,20 @@ int warmstart_predict(const float* x, int B, float* y, cudaStream_t s) {
     return INIM_OK;
 }
 bool warmstart_loaded() { return g_warmstart != nullptr; }
+int warmstart_input_res() {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    return g_warmstart ? g_warmstart->in_res : kRes;
+}
 }  // namespace inim
 
 extern "C" {
 
-int inim_cnn_create(int32_t seed, inim_cnn** out) {
+int inim_cnn_create_res(int32_t seed, int32_t in_res, inim_cnn** out) {
     if (!out) return cfail(INIM_E_ARG, "out is NULL");
+    if (in_res != 64 && in_res != 128 && in_res != 256) return cfail(INIM_E_ARG, "input resolution must be 64, 128 or 256");
     auto c = new inim_cnn();
+    c->in_res = in_res;
+    c->stem = in_res == 256 ? 2 : (in_res == 128 ? 1 : 0);
     size_t off = 0;
     for (int l = 0; l < kLayers; ++l) {
         c->w_off[l] = off;
@@ -321,6 +392,10 @@ int inim_cnn_create(int32_t seed, inim_cnn** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->m1, off * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c->m2, off * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->loss_sum, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->loss_sum, 0, sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
         e = cudaMalloc(&c->wb[l], w_count(l) * 2);
         if (e == cudaSuccess) e = cudaMalloc(&c->wf[l], w_count(l) * 2);
@@ -339,6 +414,10 @@ int inim_cnn_create(int32_t seed, inim_cnn** out) {
     *out = c;
     return INIM_OK;
 }
+
+int inim_cnn_create(int32_t seed, inim_cnn** out) { return inim_cnn_create_res(seed, kRes, out); }
+
+int inim_cnn_input_res(const inim_cnn* c) { return c ? c->in_res : 0; }
 
 int inim_cnn_destroy(inim_cnn* c) {
     std::lock_guard<std::mutex> lk(g_ws_mu);
@@ -393,28 +472,62 @@ int inim_cnn_gradients(inim_cnn* c, const float* x, const float* y, int32_t B, f
 int inim_cnn_train_step(inim_cnn* c, const float* x, const float* y, int32_t B, float lr, float* loss,
                         void* stream) {
     if (!c || !x || !y || B < 1 || !(lr > 0.0f)) return cfail(INIM_E_ARG, "bad arguments");
-    CK(cudaStreamSynchronize((cudaStream_t)stream));   // the caller's earlier work (NULL: legacy stream)
-    int st = forward(*c, x, B);
-    if (st == INIM_OK) st = backward(*c, y, B);
+    cudaStream_t cs = (cudaStream_t)stream;
+    const size_t nx = (size_t)B * c->in_res * c->in_res, ny = (size_t)B * kRes * kRes * 2;
+    if (c->in_B < B) {
+        CK(cudaStreamSynchronize(c->stream));
+        dfree(c->xin);
+        dfree(c->yin);
+        CK(cudaMalloc(&c->xin, nx * sizeof(float)));
+        CK(cudaMalloc(&c->yin, ny * sizeof(float)));
+        c->in_B = B;
+    }
+    // the inputs are copied on the caller's stream (after its producers; the
+    // caller may free or reuse its buffers in that stream's order), once the
+    // previous step no longer reads the copies; the step runs on the
+    // network's stream after the copies, and the host does not wait for it
+    CK(cudaStreamWaitEvent(cs, c->ev_done, 0));
+    CK(cudaMemcpyAsync(c->xin, x, nx * sizeof(float), cudaMemcpyDefault, cs));
+    CK(cudaMemcpyAsync(c->yin, y, ny * sizeof(float), cudaMemcpyDefault, cs));
+    CK(cudaEventRecord(c->ev_in, cs));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+    int st = forward(*c, c->xin, B);
+    if (st == INIM_OK) st = backward(*c, c->yin, B);
     if (st != INIM_OK) return st;
     c->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - std::pow(b1, (float)c->step), c2 = 1.0f - std::pow(b2, (float)c->step);
     k_adam<<<grid_for(c->n_params), 256, 0, c->stream>>>(c->params, c->grads, c->m1, c->m2, c->n_params, lr, b1, b2,
                                                          1e-8f, c1, c2);
+    k_accum_loss<<<1, 1, 0, c->stream>>>(c->loss_sum, c->loss);
+    c->loss_steps += 1;
     CK(refresh_bf16(*c));
-    if (loss) CK(cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(c->ev_done, c->stream));
+    if (loss) {
+        CK(cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return INIM_OK;
+}
+
+int inim_cnn_loss_mean(inim_cnn* c, double* mean) {
+    if (!c || !mean) return cfail(INIM_E_ARG, "bad arguments");
+    double sum = 0.0;
+    CK(cudaMemcpyAsync(&sum, c->loss_sum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemsetAsync(c->loss_sum, 0, sizeof(double), c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    *mean = c->loss_steps > 0 ? sum / c->loss_steps : 0.0;
+    c->loss_steps = 0;
     return INIM_OK;
 }
 
 const char* inim_cnn_last_error(void) { return g_cnn_err.c_str(); }
 
-int inim_warmstart_load(const void* weights, size_t bytes) {
+int inim_warmstart_load_res(const void* weights, size_t bytes, int32_t in_res) {
     const size_t n = total_params();
     if (!weights || bytes != n * sizeof(float)) return cfail(INIM_E_ARG, "weights must be the f32 parameter blob");
     inim_cnn* c = nullptr;
-    int st = inim_cnn_create(0, &c);
+    int st = inim_cnn_create_res(0, in_res, &c);
     if (st != INIM_OK) return st;
     st = inim_cnn_set_params(c, static_cast<const float*>(weights), (long long)n);
     if (st != INIM_OK) { inim_cnn_destroy(c); return st; }
@@ -423,5 +536,7 @@ int inim_warmstart_load(const void* weights, size_t bytes) {
     g_warmstart = c;
     return INIM_OK;
 }
+
+int inim_warmstart_load(const void* weights, size_t bytes) { return inim_warmstart_load_res(weights, bytes, kRes); }
 
 }  // extern "C"

@@ -344,6 +344,9 @@ __global__ void k_flip_weights(__nv_bfloat16* wt, const float* w, int Cin, int C
 }
 
 // mean squared error of pred vs target (f32); dpred (bf16) = 2 (pred - target) / n
+// running sum of the step losses (one thread)
+__global__ void k_accum_loss(double* sum, const float* loss) { *sum += (double)*loss; }
+
 __global__ void k_mse(const float* pred, const float* target, __nv_bfloat16* dpred, float* loss, size_t n) {
     float s = 0.0f;
     const float inv = 1.0f / (float)n;

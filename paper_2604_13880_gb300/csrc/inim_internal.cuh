@@ -324,8 +324,9 @@ constexpr float kFieldScale = 10.0f;   // the CNN predicts 10 x the displacement
 cudaError_t launch_density_pooled(const Job* d_job, int n, int pool, float* out, cudaStream_t s);
 cudaError_t launch_apply_field(const Job* d_jobs, const BlockMap& vert_blocks, const float* const* fields, int m,
                                float inv_scale, cudaStream_t s);
-int warmstart_predict(const float* x, int B, float* y, cudaStream_t s);
+int warmstart_predict(const float* x, int B, float* y, cudaStream_t s);   // x [B][r][r], r = warmstart_input_res()
 bool warmstart_loaded();
+int warmstart_input_res();             // input resolution of the loaded network (64, 128, 256)
 
 // geographic quality measures (Sec. 3.3).  Bounding-box mask layout of one
 // region in raster 0 (the map) and 1 (the cartogram): origin (x0, y0), size

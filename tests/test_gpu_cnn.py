@@ -33,12 +33,12 @@ def _P():
     return P
 
 
-def _fields(B, seed, scale=1.0):
-    """Smooth random log-density-like inputs [B, 64, 64] (sums of Gaussian bumps)."""
+def _fields(B, seed, scale=1.0, res=64):
+    """Smooth random log-density-like inputs [B, res, res] (sums of Gaussian bumps)."""
     rng = np.random.default_rng(seed)
-    c = (np.arange(64) + 0.5) / 64
+    c = (np.arange(res) + 0.5) / res
     y, x = np.meshgrid(c, c, indexing="ij")
-    out = np.zeros((B, 64, 64))
+    out = np.zeros((B, res, res))
     for b in range(B):
         for _ in range(12):
             cx, cy, s, a = rng.uniform(0, 1), rng.uniform(0, 1), rng.uniform(0.03, 0.2), rng.normal(0, 1)
@@ -182,6 +182,48 @@ def test_gradients_elementwise_vs_bf16_oracle(net):
         off += nw + co
 
 
+@pytest.mark.parametrize("in_res", [128, 256])
+def test_stem_variant_matches_oracle(in_res):
+    # the higher-resolution input: the first convolution at in_res, then
+    # 2x2 pools down to 64^2; forward and gradients against the oracle with
+    # the same stem, in its BF16 mode (two extra stored roundings per pool)
+    P = _P()
+    stem = {128: 1, 256: 2}[in_res]
+    c = P.inim_cnn_create(0, in_res)
+    assert c.in_res == in_res and P.inim_cnn_num_params(c) == C.n_params()
+    blob = C.he_init(61).astype(np.float32)
+    P.inim_cnn_set_params(c, blob)
+    B = 2
+    x = _fields(B, 61, res=in_res).astype(np.float32)
+    rng = np.random.default_rng(62)
+    target = (0.3 * _fields(2 * B, 63).reshape(B, 2, 64, 64).transpose(0, 2, 3, 1)
+              + 0.01 * rng.normal(size=(B, 64, 64, 2))).astype(np.float32)
+    xd = torch.as_tensor(x, device="cuda").contiguous()
+    td = torch.as_tensor(target, device="cuda").contiguous()
+    yd = torch.empty((B, 64, 64, 2), dtype=torch.float32, device="cuda")
+    P.inim_cnn_forward(c, xd, yd)
+    got = yd.cpu().numpy().astype(np.float64)
+    want, _ = C.forward(blob.astype(np.float64), x.astype(np.float64), bf16=True, stem=stem)
+    rms = float(np.sqrt((want ** 2).mean()))
+    assert np.abs(got - want).max() <= 0.15 * rms, np.abs(got - want).max() / rms
+    want64, _ = C.forward(blob.astype(np.float64), x.astype(np.float64), stem=stem)
+    assert _rel(got, want64) < 3e-2 and _cos(got, want64) > 0.999
+    gd = torch.empty(C.n_params(), dtype=torch.float32, device="cuda")
+    loss = P.inim_cnn_gradients(c, xd, td, gd)
+    g = gd.cpu().numpy().astype(np.float64)
+    wl, wg = C.loss_and_grads(blob.astype(np.float64), x.astype(np.float64), target.astype(np.float64),
+                              stem=stem)
+    assert abs(loss - wl) <= 2e-2 * wl, (loss, wl)
+    assert _cos(g, wg) > 0.998, _cos(g, wg)
+    ci, co, _ = C.LAYERS[0]
+    nw = co * 9 * ci                                  # the stem's convolution sees the full input
+    assert _rel(g[:nw], wg[:nw]) < 6e-2 and _rel(g[nw:nw + co], wg[nw:nw + co]) < 6e-2
+    # the wrong input size is refused
+    with pytest.raises(ValueError):
+        P.inim_cnn_forward(c, torch.zeros((B, 64, 64), device="cuda"), yd)
+    c.close()
+
+
 def test_training_lowers_loss():
     P = _P()
     c = P.inim_cnn_create(3)
@@ -193,9 +235,17 @@ def test_training_lowers_loss():
     xd = torch.as_tensor(x, dtype=torch.float32, device="cuda").contiguous()
     td = torch.as_tensor(t, dtype=torch.float32, device="cuda").contiguous()
     losses = [P.inim_cnn_train_step(c, xd, td, 1e-3) for _ in range(80)]
-    c.close()
     assert all(np.isfinite(losses))
     assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
+    # the asynchronous form: no host wait inside the steps; the mean of their
+    # losses is read once afterwards
+    P.inim_cnn_loss_mean(c)                                   # resets the running sum
+    for _ in range(10):
+        assert P.inim_cnn_train_step(c, xd, td, 1e-3, wait=False) is None
+    mean = P.inim_cnn_loss_mean(c)
+    last = P.inim_cnn_train_step(c, xd, td, 1e-3)
+    assert np.isfinite(mean) and 0 < mean < losses[0] and last <= 1.5 * mean, (mean, last)
+    c.close()
 
 
 def test_density_pooled_matches_oracle():

@@ -1,5 +1,6 @@
 """Pins of the CPU oracle of the warm-start network."""
 import numpy as np
+import pytest
 
 from oracle import cnn_oracle as C
 
@@ -116,3 +117,57 @@ def test_bf16_mode_rounds_only_what_is_stored():
     assert np.array_equal(C.bf16_round(saved["ge1"]), saved["ge1"])
     assert abs(l16 - l64) < 3e-2 * l64
     assert np.dot(g16, g64) / (np.linalg.norm(g16) * np.linalg.norm(g64)) > 0.99
+
+
+def _center_only_first_layer(params):
+    # the first convolution reduced to its centre tap with positive weights:
+    # on a non-negative input it is a per-pixel affine map followed by an
+    # identity ReLU, so it commutes with 2x2 average pooling
+    p = params.copy()
+    ci, co, _ = C.LAYERS[0]
+    w = p[:co * 9 * ci].reshape(co, 9, ci)
+    w[:] = 0.0
+    w[:, 4, :] = np.abs(np.random.default_rng(9).normal(size=(co, ci))) + 0.1
+    p[co * 9 * ci:co * 9 * ci + co] = np.abs(p[co * 9 * ci:co * 9 * ci + co])
+    return p
+
+
+@pytest.mark.parametrize("stem", [1, 2])
+def test_stem_equals_pooled_input_for_pointwise_first_layer(stem):
+    params = _center_only_first_layer(C.he_init(8))
+    rng = np.random.default_rng(10 + stem)
+    x = rng.uniform(0.0, 2.0, size=(2, 16 << stem, 16 << stem))
+    f = 1 << stem
+    xp = x.reshape(2, 16, f, 16, f).mean(axis=(2, 4))
+    got, _ = C.forward(params, x, stem=stem)
+    want, _ = C.forward(params, xp)
+    assert got.shape == (2, 16, 16, 2)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+    # the same holds for the loss, and for every gradient past the first layer
+    t = rng.normal(size=(2, 16, 16, 2)) * 0.1
+    l1, g1 = C.loss_and_grads(params, x, t, stem=stem)
+    l2, g2 = C.loss_and_grads(params, xp, t)
+    ci, co, _ = C.LAYERS[0]
+    n0 = co * 9 * ci + co
+    assert abs(l1 - l2) <= 1e-12 * l2
+    np.testing.assert_allclose(g1[n0:], g2[n0:], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("stem", [1, 2])
+def test_stem_gradient_finite_differences(stem):
+    params = C.he_init(12)
+    rng = np.random.default_rng(13)
+    x = rng.normal(size=(1, 16 << stem, 16 << stem))
+    t = rng.normal(size=(1, 16, 16, 2)) * 0.1
+    _, g = C.loss_and_grads(params, x, t, stem=stem)
+    h = 1e-5
+    ci, co, _ = C.LAYERS[0]
+    ci1, co1, _ = C.LAYERS[1]
+    n0 = co * 9 * ci
+    # first-layer weights and bias (seen through the pools), and a second-layer weight
+    for k in (0, n0 // 2, n0 - 1, n0, n0 + co - 1, n0 + co + (co1 * 9 * ci1) // 2):
+        p1, p2 = params.copy(), params.copy()
+        p1[k] += h
+        p2[k] -= h
+        fd = (C.loss_and_grads(p1, x, t, stem=stem)[0] - C.loss_and_grads(p2, x, t, stem=stem)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 + 1e-4 * abs(fd), (k, fd, g[k])

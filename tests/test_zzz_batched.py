@@ -3,9 +3,9 @@ with textures drawn from {256, 512, 1024, 2048}^2, solved in one batch.
 
 Every solve of the batch equals the same solve run alone: bit-exactly in
 64-bit fixed point (the integral images are exact integer sums whatever the
-band tiles, and the 1024^2 and 2048^2 groups scan in one pass here while a
-single solve uses the three-kernel scan), and within the N-iteration bound in
-FP32.  Sampled solves (the largest 2048^2 map and a 256^2 map) follow the
+band tiles, and a size group of the batch shares its scan launches and tiles
+while a single solve scans alone with its own), and within the N-iteration
+bound in FP32.  Sampled solves (the largest 2048^2 map and a 256^2 map) follow the
 FP64 oracle within the N-iteration bound.
 """
 import numpy as np
