@@ -596,9 +596,11 @@ __global__ void __launch_bounds__(256) k_scan_carry(const Job* __restrict__ jobs
 // 32 consecutive q (the lanes, so loads and stores stay coalesced) times 8
 // groups of consecutive bands (the warps).  Each thread sums the terms of its
 // group's bands, the 8 group totals are scanned in shared memory, and each
-// thread then reads its terms again and writes the exclusive prefixes of its
-// own bands.  The same sums
+// thread then writes the exclusive prefixes of its own bands.  The same sums
 // as the serial walk, associated by group, with 1/8 of its dependent chain.
+// Up to 128 bands a thread's terms (at most 16) are loaded in one round and
+// kept in registers across the barrier; beyond, they are loaded in rounds of
+// kCarryUG and loaded again (L1 hits) for the prefixes.
 constexpr int kCarryGroups = 8;
 constexpr int kCarryUG = 8;               // loads in flight per thread in the grouped form
 
@@ -612,9 +614,10 @@ __host__ __device__ inline int carry_q_per_block(int nb, int size_class) {
 
 template <class Acc>
 __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const Job* __restrict__ jobs,
-                                                                           const int2* __restrict__ bmap) {
+                                                                const int2* __restrict__ bmap) {
     using T = typename Acc::T;
-    __shared__ T tot[kCarryGroups][32];
+    constexpr int G = kCarryGroups;
+    __shared__ T tot[G][32];
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
@@ -625,16 +628,24 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     int q = m.y * 32 + lane;
     const int kind = carry_kind(q, J.n, nb, J.H);
     const CarryChain<Acc> ch(J, kind, q);
-    const int cb = (nb + kCarryGroups - 1) / kCarryGroups;
+    const int cb = (nb + G - 1) / G;
     const int b_lo = min(nb, g * cb), b_hi = min(nb, b_lo + cb);
+    constexpr int HOLD = 128 / G;             // terms a thread keeps in registers across the barrier
     T s = Acc::zero();
-    if (kind >= 0) {
+    T v[HOLD];
+    if (cb <= HOLD) {
+        // all terms of the group in one round of loads, kept for the prefix pass
+#pragma unroll
+        for (int u = 0; u < HOLD; ++u) v[u] = (kind >= 0 && b_lo + u < b_hi) ? ch.term(b_lo + u) : Acc::zero();
+#pragma unroll
+        for (int u = 0; u < HOLD; ++u) s = Acc::add(s, v[u]);
+    } else if (kind >= 0) {
         for (int b0 = b_lo; b0 < b_hi; b0 += kCarryUG) {
-            T v[kCarryUG];
+            T w[kCarryUG];
 #pragma unroll
-            for (int u = 0; u < kCarryUG; ++u) v[u] = (b0 + u < b_hi) ? ch.term(b0 + u) : Acc::zero();
+            for (int u = 0; u < kCarryUG; ++u) w[u] = (b0 + u < b_hi) ? ch.term(b0 + u) : Acc::zero();
 #pragma unroll
-            for (int u = 0; u < kCarryUG; ++u) if (b0 + u < b_hi) s = Acc::add(s, v[u]);
+            for (int u = 0; u < kCarryUG; ++u) if (b0 + u < b_hi) s = Acc::add(s, w[u]);
         }
     }
     tot[g][lane] = s;
@@ -642,21 +653,39 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     if (kind < 0) return;
     T acc = Acc::zero();
     for (int k = 0; k < g; ++k) acc = Acc::add(acc, tot[k][lane]);
-    // the terms again (this thread's own loads: L1 hits), now with their carries
-    for (int b0 = b_lo; b0 < b_hi; b0 += kCarryUG) {
-        T v[kCarryUG];
+    if (cb <= HOLD) {
 #pragma unroll
-        for (int u = 0; u < kCarryUG; ++u) v[u] = (b0 + u < b_hi) ? ch.term(b0 + u) : Acc::zero();
-#pragma unroll
-        for (int u = 0; u < kCarryUG; ++u) {
-            if (b0 + u < b_hi) {
-                ch.store(b0 + u, acc);
+        for (int u = 0; u < HOLD; ++u) {
+            if (b_lo + u < b_hi) {
+                ch.store(b_lo + u, acc);
                 acc = Acc::add(acc, v[u]);
+            }
+        }
+    } else {
+        // the terms again (this thread's own loads: L1 hits), now with their carries
+        for (int b0 = b_lo; b0 < b_hi; b0 += kCarryUG) {
+            T w[kCarryUG];
+#pragma unroll
+            for (int u = 0; u < kCarryUG; ++u) w[u] = (b0 + u < b_hi) ? ch.term(b0 + u) : Acc::zero();
+#pragma unroll
+            for (int u = 0; u < kCarryUG; ++u) {
+                if (b0 + u < b_hi) {
+                    ch.store(b0 + u, acc);
+                    acc = Acc::add(acc, w[u]);
+                }
             }
         }
     }
     tl_end(J.tl, kTlCarry);
     pdl_release();
+}
+
+// the carry kernel of a group: the serial walk, or the grouped form
+template <class Acc>
+cudaError_t launch_carry(const Job* d_jobs, const BlockMap& carry, cudaStream_t s) {
+    const int2* cm = carry.d_map;
+    if (carry.q_per_block != 32) return launch_pdl(k_scan_carry<Acc>, carry.n_blocks, 256, 0, s, d_jobs, cm);
+    return launch_pdl(k_scan_carry_grouped<Acc>, carry.n_blocks, 32 * kCarryGroups, 0, s, d_jobs, cm);
 }
 
 // ---------------------------------------------------------------------------
@@ -680,8 +709,7 @@ cudaError_t launch_scan_tile(const Job* d_jobs, const BlockMap& band, const Bloc
     if (phase == 0 || phase == 1)
         e = launch_pdl(k_scan_band<Acc, CPT, NT, 1>, band.n_blocks, NT, ring_bytes, s, d_jobs, bm, dtex);
     if (e == cudaSuccess && (phase == 0 || phase == 2)) {
-        if (carry.q_per_block == 32) e = launch_pdl(k_scan_carry_grouped<Acc>, carry.n_blocks, 32 * kCarryGroups, 0, s, d_jobs, cm);
-        else e = launch_pdl(k_scan_carry<Acc>, carry.n_blocks, 256, 0, s, d_jobs, cm);
+        e = launch_carry<Acc>(d_jobs, carry, s);
     }
     if (e == cudaSuccess && (phase == 0 || phase == 3))
         e = launch_pdl(k_scan_band<Acc, CPT, NT, 3>, band.n_blocks, NT, ring_bytes, s, d_jobs, bm, dtex);

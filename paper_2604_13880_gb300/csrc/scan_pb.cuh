@@ -13,7 +13,11 @@
 //          (E1) and left (E2), so no thread needs a neighbour's results;
 //          T = E1(i + 1, r - 1) - E2(i - 1, r - 1) plus the band's carries.
 // Phase 1 stores the band's aggregates, phase 3 S, T and the 1-D arrays,
-// exactly as the row-serial form does (same carries, same layout).
+// exactly as the row-serial form does (same carries, same layout).  Phase 3
+// stages the band's three carry rows into shared memory by bulk copies next
+// to the label rows and reads each thread's windows of them only for stage
+// B, so that no carry occupies registers during stage A (at three blocks per
+// SM the register budget is 80 a thread).
 #pragma once
 
 // included at the end of scan_impl.cuh (uses its helpers)
@@ -36,7 +40,8 @@ struct PbLayout {
     static constexpr size_t kTot = 16 * sizeof(T);
     static constexpr size_t kDens = (size_t)kPbDens * sizeof(float);
     static constexpr size_t kRing = (size_t)H * N * 2;
-    static constexpr size_t kBytes = kR + kTot + kDens + kRing;
+    static constexpr size_t kCarry = (size_t)3 * N * sizeof(T);     // phase 3: S, E1, E2 carries
+    static constexpr size_t kBytes = kR + kTot + kDens + kRing + kCarry;
     static __device__ __forceinline__ int at(int x) { return x + x / CW; }
 };
 
@@ -55,7 +60,8 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     T* rowtot = reinterpret_cast<T*>(pb_smem + L::kR);
     float* dens = reinterpret_cast<float*>(pb_smem + L::kR + L::kTot);
     uint16_t* ring = reinterpret_cast<uint16_t*>(pb_smem + L::kR + L::kTot + L::kDens);
-    __shared__ uint64_t bars[H];
+    T* csm = reinterpret_cast<T*>(pb_smem + L::kR + L::kTot + L::kDens + L::kRing);   // [3][N]
+    __shared__ uint64_t bars[H + 1];                      // label rows, then the carry rows
 
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
@@ -68,13 +74,22 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
 
     // stage: every label row of the band, one bulk copy each
     if (tid == 0) {
-        for (int q = 0; q < H; ++q) mbar_init(bars + q, 1);
+        for (int q = 0; q <= H; ++q) mbar_init(bars + q, 1);
         mbar_init_fence();
     }
     __syncthreads();
     if (from_labels && tid == 0)
         for (int q = 0; q < H; ++q)
             tma_load_1d(ring + q * N, J.labels + (size_t)(j0 + q) * N, 2u * N, bars + q);
+    if (PHASE == 3 && tid == 0) {
+        // the carry rows of this band: S at band, E1 at nb + band, E2 at 2 nb + band
+        const T* carry = reinterpret_cast<const T*>(J.carry);
+        constexpr unsigned row_bytes = (unsigned)(N * sizeof(T));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bars + H)),
+                     "r"(3u * row_bytes) : "memory");
+        for (int k = 0; k < 3; ++k)
+            tma_copy_1d(csm + k * N, carry + (size_t)(k * nb + band) * N, row_bytes, bars + H);
+    }
     const float* table = J.dens;
     int fix_bits;
     if (PHASE == 1 && from_labels && J.fuse_table) {
@@ -91,69 +106,88 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     }
     const float qscale = ldexpf(1.0f, fix_bits);   // fixed-point unit (FIX64 only)
 
-    // phase-3 carries of this thread's columns and diagonals, loaded early
     const int i0 = tid * CB;
-    T c1v[W - 1], c2v[W - 1], Sacc[CB];
-    T rc_above = Acc::zero();
-    if constexpr (PHASE == 3) {
-        const T* carry = reinterpret_cast<const T*>(J.carry);
-        const T* cS = carry + (size_t)band * N;
-        const T* c1 = carry + (size_t)(nb + band) * N;
-        const T* c2 = carry + (size_t)(2 * nb + band) * N;
-        rc_above = cS[N - 1];
-#pragma unroll
-        for (int q = 0; q < W - 1; ++q) {
-            const int x1 = i0 + 1 + q;                    // c1 at i + r + 1 = i0 + 1 + (k + r)
-            c1v[q] = x1 < N ? c1[x1] : rc_above;
-            const int x2 = i0 - H + q;                    // c2 at i - r - 1 = i0 - H + (k - r + H - 1)
-            c2v[q] = x2 >= 0 ? c2[x2] : Acc::zero();
-        }
-#pragma unroll
-        for (int k = 0; k < CB; ++k) Sacc[k] = cS[i0 + k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < CB; ++k) Sacc[k] = Acc::zero();
-    }
     __syncthreads();                                      // region table in shared memory
 
-    // A: row prefixes, one warp per row
+    // A: row prefixes, one warp per row, in segments of 32 x CWS columns
+    // (a lane owns CWS contiguous columns of each segment; the segment's
+    // offset is the row's running total, so at most CWS prefixes are live)
+    constexpr int NSEG = CW > 16 ? CW / 16 : 1;
+    constexpr int CWS = CW / NSEG;
     bool ok = true;
     for (int r = warp; r < H; r += kPbThreads / 32) {
-        float d[CW];
-        if (from_labels) {
-            ok = ok && mbar_wait(bars + r, 0u);
-            labels_to_density<CW>(smem_labels<CW>(ring + r * N, lane * CW), table, d);
-        } else {
-            const float* src = dtex + (size_t)(j0 + r) * N + lane * CW;
+        if (from_labels) ok = ok && mbar_wait(bars + r, 0u);
+        T seg_off = Acc::zero();
 #pragma unroll
-            for (int k = 0; k < CW; k += 4) {
-                const float4 v = *reinterpret_cast<const float4*>(src + k);
-                d[k] = v.x; d[k + 1] = v.y; d[k + 2] = v.z; d[k + 3] = v.w;
+        for (int sg = 0; sg < NSEG; ++sg) {
+            const int c0 = sg * 32 * CWS + lane * CWS;
+            float d[CWS];
+            if (from_labels) {
+                labels_to_density<CWS>(smem_labels<CWS>(ring + r * N, c0), table, d);
+            } else {
+                const float* src = dtex + (size_t)(j0 + r) * N + c0;
+#pragma unroll
+                for (int k = 0; k < CWS; k += 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(src + k);
+                    d[k] = v.x; d[k + 1] = v.y; d[k + 2] = v.z; d[k + 3] = v.w;
+                }
             }
+            T run = Acc::zero();
+            T p[CWS];
+#pragma unroll
+            for (int k = 0; k < CWS; ++k) { run = Acc::add(run, Acc::from(d[k], qscale)); p[k] = run; }
+            T incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T t = Acc::shfl_up(incl, o);
+                if (lane >= o) incl = Acc::add(incl, t);
+            }
+            const T off = Acc::add(seg_off, Acc::sub(incl, run));
+            T* row = Rs + r * L::kRowStride + L::at(c0);
+#pragma unroll
+            for (int k = 0; k < CWS; ++k) row[k] = Acc::add(off, p[k]);
+            seg_off = Acc::add(seg_off, Acc::shfl(incl, 31));
         }
-        T run = Acc::zero();
-        T p[CW];
-#pragma unroll
-        for (int k = 0; k < CW; ++k) { run = Acc::add(run, Acc::from(d[k], qscale)); p[k] = run; }
-        T incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const T t = Acc::shfl_up(incl, o);
-            if (lane >= o) incl = Acc::add(incl, t);
-        }
-        const T off = Acc::sub(incl, run);
-        T* row = Rs + r * L::kRowStride + L::at(lane * CW);
-#pragma unroll
-        for (int k = 0; k < CW; ++k) row[k] = Acc::add(off, p[k]);
-        if (lane == 31) rowtot[r] = incl;
+        if (lane == 31) rowtot[r] = seg_off;
     }
+    if (PHASE == 3) ok = ok && mbar_wait(bars + H, 0u);   // the carry rows
     if (__syncthreads_or(!ok)) {
         // a staged row never arrived: record it, drain the copies (bounded)
         if (tid == 0) {
             atomicExch(&J.st->error, INIM_E_TIMEOUT);
             for (int q = 0; q < H; ++q) mbar_wait(bars + q, 0u);
+            if (PHASE == 3) mbar_wait(bars + H, 0u);
         }
         return;
+    }
+
+    // phase-3 carries of this thread's columns and diagonals, read from the
+    // staged rows as sliding windows: at row r, c1w[k] = E1 carry at
+    // i0 + 1 + k + r and c2w[k] = E2 carry at i0 + k - r - 1 (E1 past the right
+    // edge is the row sum above the band, E2 past the left edge is 0); each
+    // row shifts both windows by one and reads one new entry of each
+    const T* cS = csm;
+    T rc_above = Acc::zero();
+    T Sacc[CB], c1w[CB], c2w[CB];
+    auto C1 = [&](int q) -> T {
+        const int x1 = i0 + 1 + q;
+        return x1 < N ? csm[N + x1] : rc_above;
+    };
+    auto C2 = [&](int q) -> T {
+        const int x2 = i0 - H + q;
+        return x2 >= 0 ? csm[2 * N + x2] : Acc::zero();
+    };
+    if constexpr (PHASE == 3) {
+        rc_above = cS[N - 1];
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+            Sacc[k] = cS[i0 + k];
+            c1w[k] = C1(k);
+            c2w[k] = C2(k + H - 1);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < CB; ++k) Sacc[k] = Acc::zero();
     }
 
     // B: this thread's columns over the band's rows
@@ -162,6 +196,31 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
         if (x < 0) return Acc::zero();
         return Rs[r * L::kRowStride + L::at(x)];
     };
+    if constexpr (PHASE == 1) {
+        // the band's aggregates at its last row with zero carries, as direct
+        // sums over the rows in the order and operand order of the ray
+        // recurrences below (so the same values):
+        //   S(x) = sum_r R(x, r),  E1(x) = sum_r R'(x + H-1-r, r),  E2(x) = sum_r R'(x - (H-1-r), r)
+        T a1[CB], a2[CB];
+#pragma unroll
+        for (int k = 0; k < CB; ++k) { a1[k] = Acc::zero(); a2[k] = Acc::zero(); }
+#pragma unroll
+        for (int r = 0; r < H; ++r) {
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                Sacc[k] = Acc::add(Sacc[k], Rp(i0 + k, r));
+                a1[k] = Acc::add(Rp(i0 + k + H - 1 - r, r), a1[k]);
+                a2[k] = Acc::add(Rp(i0 + k - (H - 1 - r), r), a2[k]);
+            }
+        }
+        tl_end(J.tl, kTlScan1);
+        pdl_release();
+        T* agg = reinterpret_cast<T*>(J.agg);
+        store_row<Acc, CB>(agg + (size_t)band * N + i0, Sacc);
+        store_row<Acc, CB>(agg + (size_t)(nb + band) * N + i0, a1);
+        store_row<Acc, CB>(agg + (size_t)(2 * nb + band) * N + i0, a2);
+        return;
+    }
     T e1[W], e2[W];                                      // e1[q] ~ x = i0 + q; e2[q] ~ x = i0 - H + q
 #pragma unroll
     for (int q = 0; q < W; ++q) { e1[q] = Acc::zero(); e2[q] = Acc::zero(); }
@@ -179,8 +238,8 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
             T Tv[CB];
 #pragma unroll
             for (int k = 0; k < CB; ++k) {
-                const T a = Acc::add(e1[k + 1], c1v[k + r]);              // E1(i + 1, j - 1)
-                const T b = Acc::add(e2[H + k - 1], c2v[k - r + H - 1]);  // E2(i - 1, j - 1)
+                const T a = Acc::add(e1[k + 1], c1w[k]);                  // E1(i + 1, j - 1)
+                const T b = Acc::add(e2[H + k - 1], c2w[k]);              // E2(i - 1, j - 1)
                 Tv[k] = Acc::sub(a, b);
             }
 #pragma unroll
@@ -191,9 +250,6 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
                 store_row<Acc, CB>(Sout + rowbase, Sacc);
                 store_row<Acc, CB>(Tout + rowbase, Tv);
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < CB; ++k) Sacc[k] = Acc::add(Sacc[k], Rp(i0 + k, r));
         }
         // advance the rays to row r (old values of row r - 1 shift by one column)
 #pragma unroll
@@ -201,32 +257,31 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
 #pragma unroll
         for (int q = W - 1; q >= 0; --q) e2[q] = Acc::add(Rp(i0 - H + q, r), q > 0 ? e2[q - 1] : Acc::zero());
         if constexpr (PHASE == 3) {
-            if (tid == 0) Aout[j] = Acc::add(e1[0], c1v[r]);                         // A(j) = E1(0, j)
+            if (tid == 0) Aout[j] = Acc::add(e1[0], c1w[0]);                         // A(j) = E1(0, j)
             if (tid == kPbThreads - 1) {
                 RCout[j] = Sacc[CB - 1];                                             // S(N-1, j)
                 if (j < N - 1)                                                       // w = N-1-j > 0
-                    Bout[2 * N - 2 - j] = Acc::sub(Sacc[CB - 1], Acc::add(e2[H + CB - 1], c2v[CB - 1 - r + H - 1]));
+                    Bout[2 * N - 2 - j] = Acc::sub(Sacc[CB - 1], Acc::add(e2[H + CB - 1], c2w[CB - 1]));
             }
             if (j == N - 1) {
 #pragma unroll
                 for (int k = 0; k < CB; ++k) {
-                    Aout[i0 + k + N - 1] = Acc::add(e1[k], c1v[k + r]);             // A(x+N-1) = E1(x, N-1)
-                    Bout[i0 + k] = Acc::add(e2[H + k], c2v[k - r + H - 1]);          // B(x-N+1) = E2(x, N-1)
+                    Aout[i0 + k + N - 1] = Acc::add(e1[k], c1w[k]);                 // A(x+N-1) = E1(x, N-1)
+                    Bout[i0 + k] = Acc::add(e2[H + k], c2w[k]);                      // B(x-N+1) = E2(x, N-1)
                 }
+            }
+            if (r + 1 < H) {                                 // the windows of row r + 1
+#pragma unroll
+                for (int k = 0; k < CB - 1; ++k) c1w[k] = c1w[k + 1];
+                c1w[CB - 1] = C1(CB + r);
+#pragma unroll
+                for (int k = CB - 1; k > 0; --k) c2w[k] = c2w[k - 1];
+                c2w[0] = C2(H - 2 - r);
             }
         }
     }
-    tl_end(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
+    tl_end(J.tl, kTlScan3);
     pdl_release();
-    if constexpr (PHASE == 1) {
-        T* agg = reinterpret_cast<T*>(J.agg);
-        T a1[CB], a2[CB];
-#pragma unroll
-        for (int k = 0; k < CB; ++k) { a1[k] = e1[k]; a2[k] = e2[H + k]; }
-        store_row<Acc, CB>(agg + (size_t)band * N + i0, Sacc);
-        store_row<Acc, CB>(agg + (size_t)(nb + band) * N + i0, a1);
-        store_row<Acc, CB>(agg + (size_t)(2 * nb + band) * N + i0, a2);
-    }
 }
 
 template <class Acc, int N, int H>
@@ -247,11 +302,7 @@ cudaError_t launch_scan_pb(const Job* d_jobs, const BlockMap& band, const BlockM
     const int2* cm = carry.d_map;
     if (phase == 0 || phase == 1) e = launch_pdl(k_scan_band_pb<Acc, N, H, 1>, band.n_blocks, kPbThreads, L::kBytes, s,
                                                  d_jobs, bm, dtex);
-    if (e == cudaSuccess && (phase == 0 || phase == 2)) {
-        if (carry.q_per_block == 32)
-            e = launch_pdl(k_scan_carry_grouped<Acc>, carry.n_blocks, 32 * kCarryGroups, 0, s, d_jobs, cm);
-        else e = launch_pdl(k_scan_carry<Acc>, carry.n_blocks, 256, 0, s, d_jobs, cm);
-    }
+    if (e == cudaSuccess && (phase == 0 || phase == 2)) e = launch_carry<Acc>(d_jobs, carry, s);
     if (e == cudaSuccess && (phase == 0 || phase == 3))
         e = launch_pdl(k_scan_band_pb<Acc, N, H, 3>, band.n_blocks, kPbThreads, L::kBytes, s, d_jobs, bm, dtex);
     return e;
