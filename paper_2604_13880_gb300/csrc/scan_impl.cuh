@@ -46,6 +46,7 @@ struct AccF32 {
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ T shfl_down(T v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
     static __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
     static __device__ __forceinline__ float ratio(T a, T c) { return a / c; }
     static __device__ __forceinline__ double inv(T c) { return (double)(1.0f / c); }
@@ -59,6 +60,7 @@ struct AccFix {   // 64-bit fixed point, exact sums
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T shfl_up(T v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ T shfl_down(T v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
     static __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
     static __device__ __forceinline__ float ratio(T a, T c) { return (float)((double)a / (double)c); }
     static __device__ __forceinline__ double inv(T c) { return 1.0 / (double)c; }
@@ -82,6 +84,9 @@ struct AccKahan {   // compensated float pairs: value = hi + lo
     static __device__ __forceinline__ T sub(T a, T b) { return add(a, make_float2(-b.x, -b.y)); }
     static __device__ __forceinline__ T shfl_up(T v, int o) {
         return make_float2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
+    }
+    static __device__ __forceinline__ T shfl_down(T v, int o) {
+        return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
     }
     static __device__ __forceinline__ T shfl(T v, int src) {
         return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
@@ -620,9 +625,6 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     __shared__ T tot[G][32];
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
-    pdl_start(J.pdl_early != 0);
-    if (!J.st->active) return;
-    tl_begin(J.tl, kTlCarry);
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int nb = J.nb;
     int q = m.y * 32 + lane;
@@ -631,6 +633,11 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
     const int cb = (nb + G - 1) / G;
     const int b_lo = min(nb, g * cb), b_hi = min(nb, b_lo + cb);
     constexpr int HOLD = 128 / G;             // terms a thread keeps in registers across the barrier
+    pdl_start(J.pdl_early != 0);
+    tl_begin(J.tl, kTlCarry);
+    // the active flag is read with the terms (one round trip); the same in
+    // every thread of the block
+    const int act = J.st->active;
     T s = Acc::zero();
     T v[HOLD];
     if (cb <= HOLD) {
@@ -647,6 +654,10 @@ __global__ void __launch_bounds__(32 * kCarryGroups) k_scan_carry_grouped(const 
 #pragma unroll
             for (int u = 0; u < kCarryUG; ++u) if (b0 + u < b_hi) s = Acc::add(s, w[u]);
         }
+    }
+    if (!act) {
+        tl_end(J.tl, kTlCarry);
+        return;
     }
     tot[g][lane] = s;
     __syncthreads();

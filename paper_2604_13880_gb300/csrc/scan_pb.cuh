@@ -1,23 +1,26 @@
 // Parallel-rows form of the band scan (phases 1 and 3 of scan_impl.cuh) for
-// short bands: the same outputs, computed without a block barrier per row.
+// short bands: the same outputs, computed with few block barriers.
 //
-//   stage  all H label rows of the band arrive by bulk copies at once;
-//   A      each warp takes whole rows: a lane owns N/32 contiguous columns,
-//          so a row's prefix R(x, r) is a lane-serial scan plus one warp
-//          scan (shuffles only); R and the row totals go to shared memory;
-//   B      after one barrier each thread owns N/256 columns and walks the H
-//          rows: S accumulates R down its columns; the diagonal rays
-//            E1(x, r) = R'(x, r) + E1(x + 1, r - 1)   (R'(x >= N) = row total)
-//            E2(x, r) = R'(x, r) + E2(x - 1, r - 1)   (R'(x < 0) = 0)
-//          are carried in registers over a halo of H columns to the right
-//          (E1) and left (E2), so no thread needs a neighbour's results;
-//          T = E1(i + 1, r - 1) - E2(i - 1, r - 1) plus the band's carries.
-// Phase 1 stores the band's aggregates, phase 3 S, T and the 1-D arrays,
-// exactly as the row-serial form does (same carries, same layout).  Phase 3
-// stages the band's three carry rows into shared memory by bulk copies next
-// to the label rows and reads each thread's windows of them only for stage
-// B, so that no carry occupies registers during stage A (at three blocks per
-// SM the register budget is 80 a thread).
+//   stage  all H label rows of the band arrive by bulk copies at once (and,
+//          in phase 3, the band's three carry rows);
+//   A      each warp takes whole rows: a lane owns contiguous columns of a
+//          row segment, so a row's prefix R(x, r) is a lane-serial scan plus
+//          one warp scan per segment (shuffles only); R and the row totals go
+//          to shared memory;
+//   B      after one barrier each thread owns N/256 columns.
+//          Phase 1: the band's aggregates with zero carries are direct sums
+//          over its rows, S(x) = sum_r R(x, r), E1(x) = sum_r R'(x + H-1-r, r),
+//          E2(x) = sum_r R'(x - (H-1-r), r) (R'(x >= N) = row total,
+//          R'(x < 0) = 0): no thread needs another's results.
+//          Phase 3: the thread walks the H rows with the full rays
+//            E1(x, r) = R'(x, r) + E1(x + 1, r - 1)
+//            E2(x, r) = R'(x, r) + E2(x - 1, r - 1)
+//          started from the carries; the neighbouring value each row needs
+//          comes by a shuffle inside a warp and through shared memory across
+//          warps (one barrier per row); S accumulates R down its columns and
+//          T = E1(i + 1, r - 1) - E2(i - 1, r - 1).
+// Phase 1 stores the band's aggregates, phase 3 S, T and the 1-D arrays with
+// the same carries and layout as the row-serial form.
 #pragma once
 
 // included at the end of scan_impl.cuh (uses its helpers)
@@ -53,7 +56,6 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     using L = PbLayout<Acc, N, H>;
     constexpr int CW = L::CW;
     constexpr int CB = N / kPbThreads;                 // columns per thread in stage B
-    constexpr int W = CB + H;                          // stage-B register window (halo included)
     static_assert(H % 8 == 0 && CW % 8 == 0 && CB >= 1, "tile");
     extern __shared__ __align__(128) unsigned char pb_smem[];
     T* Rs = reinterpret_cast<T*>(pb_smem);
@@ -65,19 +67,21 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
 
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
-    pdl_start(J.pdl_early != 0);
-    if (!J.st->active) return;
-    tl_begin(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
     const int band = m.y, nb = J.nb, j0 = band * H;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool from_labels = (dtex == nullptr);
-
-    // stage: every label row of the band, one bulk copy each
     if (tid == 0) {
         for (int q = 0; q <= H; ++q) mbar_init(bars + q, 1);
         mbar_init_fence();
     }
     __syncthreads();
+    pdl_start(J.pdl_early != 0);
+    tl_begin(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
+
+    // after the wait the bulk copies go out first, and the job's active flag
+    // is read together with the loads of the region table (one round trip);
+    // a stopped job's block leaves once its copies have landed.
+    // stage: every label row of the band, one bulk copy each
     if (from_labels && tid == 0)
         for (int q = 0; q < H; ++q)
             tma_load_1d(ring + q * N, J.labels + (size_t)(j0 + q) * N, 2u * N, bars + q);
@@ -90,12 +94,13 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
         for (int k = 0; k < 3; ++k)
             tma_copy_1d(csm + k * N, carry + (size_t)(k * nb + band) * N, row_bytes, bars + H);
     }
+    const int act = J.st->active;
     const float* table = J.dens;
     int fix_bits;
     if (PHASE == 1 && from_labels && J.fuse_table) {
         // this iteration's density table, built here (every band block the
-        // same; band 0 publishes it with the job state)
-        fix_bits = region_table(J, dens, band == 0).fix_bits;
+        // same; band 0 of an active job publishes it with the job state)
+        fix_bits = region_table(J, dens, band == 0 && act).fix_bits;
         table = dens;
     } else {
         if (from_labels && J.n_regions + 1 <= kPbDens) {
@@ -108,6 +113,15 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
 
     const int i0 = tid * CB;
     __syncthreads();                                      // region table in shared memory
+    if (!act) {
+        if (tid == 0) {
+            if (from_labels)
+                for (int q = 0; q < H; ++q) mbar_wait(bars + q, 0u);
+            if (PHASE == 3) mbar_wait(bars + H, 0u);
+        }
+        tl_end(J.tl, PHASE == 1 ? kTlScan1 : kTlScan3);
+        return;
+    }
 
     // A: row prefixes, one warp per row, in segments of 32 x CWS columns
     // (a lane owns CWS contiguous columns of each segment; the segment's
@@ -161,35 +175,6 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
         return;
     }
 
-    // phase-3 carries of this thread's columns and diagonals, read from the
-    // staged rows as sliding windows: at row r, c1w[k] = E1 carry at
-    // i0 + 1 + k + r and c2w[k] = E2 carry at i0 + k - r - 1 (E1 past the right
-    // edge is the row sum above the band, E2 past the left edge is 0); each
-    // row shifts both windows by one and reads one new entry of each
-    const T* cS = csm;
-    T rc_above = Acc::zero();
-    T Sacc[CB], c1w[CB], c2w[CB];
-    auto C1 = [&](int q) -> T {
-        const int x1 = i0 + 1 + q;
-        return x1 < N ? csm[N + x1] : rc_above;
-    };
-    auto C2 = [&](int q) -> T {
-        const int x2 = i0 - H + q;
-        return x2 >= 0 ? csm[2 * N + x2] : Acc::zero();
-    };
-    if constexpr (PHASE == 3) {
-        rc_above = cS[N - 1];
-#pragma unroll
-        for (int k = 0; k < CB; ++k) {
-            Sacc[k] = cS[i0 + k];
-            c1w[k] = C1(k);
-            c2w[k] = C2(k + H - 1);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < CB; ++k) Sacc[k] = Acc::zero();
-    }
-
     // B: this thread's columns over the band's rows
     auto Rp = [&](int x, int r) -> T {                   // R'(x, r)
         if (x >= N) return rowtot[r];
@@ -198,12 +183,11 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     };
     if constexpr (PHASE == 1) {
         // the band's aggregates at its last row with zero carries, as direct
-        // sums over the rows in the order and operand order of the ray
-        // recurrences below (so the same values):
+        // sums over the rows:
         //   S(x) = sum_r R(x, r),  E1(x) = sum_r R'(x + H-1-r, r),  E2(x) = sum_r R'(x - (H-1-r), r)
-        T a1[CB], a2[CB];
+        T Sacc[CB], a1[CB], a2[CB];
 #pragma unroll
-        for (int k = 0; k < CB; ++k) { a1[k] = Acc::zero(); a2[k] = Acc::zero(); }
+        for (int k = 0; k < CB; ++k) { Sacc[k] = Acc::zero(); a1[k] = Acc::zero(); a2[k] = Acc::zero(); }
 #pragma unroll
         for (int r = 0; r < H; ++r) {
 #pragma unroll
@@ -221,9 +205,27 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
         store_row<Acc, CB>(agg + (size_t)(2 * nb + band) * N + i0, a2);
         return;
     }
-    T e1[W], e2[W];                                      // e1[q] ~ x = i0 + q; e2[q] ~ x = i0 - H + q
+    // phase 3: the full rays at the band's rows, each thread its CB columns.
+    // They start from the carries (the rays at row j0 - 1) and advance one
+    // row at a time; the one value a row needs from beyond a thread's own
+    // columns (E1 right of its last column, E2 left of its first) comes from
+    // the neighbouring lane by a shuffle, or, at a warp's edge, from the
+    // neighbouring warp through shared memory (one barrier per row).  Past
+    // the texture's right edge E1 is the row sum so far, past its left edge
+    // E2 is 0.
+    constexpr int NW = kPbThreads / 32;
+    __shared__ T edge1[2][NW], edge2[2][NW];
+    T e1[CB], e2[CB], Sacc[CB];
 #pragma unroll
-    for (int q = 0; q < W; ++q) { e1[q] = Acc::zero(); e2[q] = Acc::zero(); }
+    for (int k = 0; k < CB; ++k) {
+        Sacc[k] = csm[i0 + k];
+        e1[k] = csm[N + i0 + k];
+        e2[k] = csm[2 * N + i0 + k];
+    }
+    T rcum = csm[N - 1];                                 // E1 past the right edge at row j0 - 1
+    if (lane == 0) edge1[0][warp] = e1[0];
+    if (lane == 31) edge2[0][warp] = e2[CB - 1];
+    __syncthreads();
     T* STout = reinterpret_cast<T*>(J.ST);
     T* Sout = reinterpret_cast<T*>(J.S);
     T* Tout = reinterpret_cast<T*>(J.T);
@@ -232,52 +234,48 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     T* RCout = reinterpret_cast<T*>(J.rowcum);
 #pragma unroll
     for (int r = 0; r < H; ++r) {
-        const int j = j0 + r;
-        if constexpr (PHASE == 3) {
-            // T from the previous row's local rays plus the carries
-            T Tv[CB];
+        const int j = j0 + r, buf = r & 1;
+        // E1(i0 + CB, j - 1) and E2(i0 - 1, j - 1)
+        T n1 = Acc::shfl_down(e1[0], 1);
+        T n2 = Acc::shfl_up(e2[CB - 1], 1);
+        if (lane == 31) n1 = warp + 1 < NW ? edge1[buf][warp + 1] : rcum;
+        if (lane == 0) n2 = warp > 0 ? edge2[buf][warp - 1] : Acc::zero();
+        // T(i, j) = E1(i + 1, j - 1) - E2(i - 1, j - 1)
+        T Tv[CB], Rv[CB];
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+            Tv[k] = Acc::sub(k + 1 < CB ? e1[k + 1] : n1, k > 0 ? e2[k - 1] : n2);
+            Rv[k] = Rp(i0 + k, r);
+            Sacc[k] = Acc::add(Sacc[k], Rv[k]);
+        }
+        const size_t rowbase = (size_t)j * N + i0;
+        if (STout) store_row_pairs<Acc, CB>(STout + 2 * rowbase, Sacc, Tv);
+        else {
+            store_row<Acc, CB>(Sout + rowbase, Sacc);
+            store_row<Acc, CB>(Tout + rowbase, Tv);
+        }
+        // the rays at row j (ascending for E1, descending for E2: old values)
+#pragma unroll
+        for (int k = 0; k < CB; ++k) e1[k] = Acc::add(Rv[k], k + 1 < CB ? e1[k + 1] : n1);
+#pragma unroll
+        for (int k = CB - 1; k >= 0; --k) e2[k] = Acc::add(Rv[k], k > 0 ? e2[k - 1] : n2);
+        rcum = Acc::add(rcum, rowtot[r]);
+        if (tid == 0) Aout[j] = e1[0];                                           // A(j) = E1(0, j)
+        if (tid == kPbThreads - 1) {
+            RCout[j] = Sacc[CB - 1];                                             // S(N-1, j)
+            if (j < N - 1) Bout[2 * N - 2 - j] = Acc::sub(Sacc[CB - 1], e2[CB - 1]);   // w = N-1-j > 0
+        }
+        if (j == N - 1) {
 #pragma unroll
             for (int k = 0; k < CB; ++k) {
-                const T a = Acc::add(e1[k + 1], c1w[k]);                  // E1(i + 1, j - 1)
-                const T b = Acc::add(e2[H + k - 1], c2w[k]);              // E2(i - 1, j - 1)
-                Tv[k] = Acc::sub(a, b);
-            }
-#pragma unroll
-            for (int k = 0; k < CB; ++k) Sacc[k] = Acc::add(Sacc[k], Rp(i0 + k, r));
-            const size_t rowbase = (size_t)j * N + i0;
-            if (STout) store_row_pairs<Acc, CB>(STout + 2 * rowbase, Sacc, Tv);
-            else {
-                store_row<Acc, CB>(Sout + rowbase, Sacc);
-                store_row<Acc, CB>(Tout + rowbase, Tv);
+                Aout[i0 + k + N - 1] = e1[k];                                    // A(x+N-1) = E1(x, N-1)
+                Bout[i0 + k] = e2[k];                                            // B(x-N+1) = E2(x, N-1)
             }
         }
-        // advance the rays to row r (old values of row r - 1 shift by one column)
-#pragma unroll
-        for (int q = 0; q < W; ++q) e1[q] = Acc::add(Rp(i0 + q, r), q + 1 < W ? e1[q + 1] : Acc::zero());
-#pragma unroll
-        for (int q = W - 1; q >= 0; --q) e2[q] = Acc::add(Rp(i0 - H + q, r), q > 0 ? e2[q - 1] : Acc::zero());
-        if constexpr (PHASE == 3) {
-            if (tid == 0) Aout[j] = Acc::add(e1[0], c1w[0]);                         // A(j) = E1(0, j)
-            if (tid == kPbThreads - 1) {
-                RCout[j] = Sacc[CB - 1];                                             // S(N-1, j)
-                if (j < N - 1)                                                       // w = N-1-j > 0
-                    Bout[2 * N - 2 - j] = Acc::sub(Sacc[CB - 1], Acc::add(e2[H + CB - 1], c2w[CB - 1]));
-            }
-            if (j == N - 1) {
-#pragma unroll
-                for (int k = 0; k < CB; ++k) {
-                    Aout[i0 + k + N - 1] = Acc::add(e1[k], c1w[k]);                 // A(x+N-1) = E1(x, N-1)
-                    Bout[i0 + k] = Acc::add(e2[H + k], c2w[k]);                      // B(x-N+1) = E2(x, N-1)
-                }
-            }
-            if (r + 1 < H) {                                 // the windows of row r + 1
-#pragma unroll
-                for (int k = 0; k < CB - 1; ++k) c1w[k] = c1w[k + 1];
-                c1w[CB - 1] = C1(CB + r);
-#pragma unroll
-                for (int k = CB - 1; k > 0; --k) c2w[k] = c2w[k - 1];
-                c2w[0] = C2(H - 2 - r);
-            }
+        if (r + 1 < H) {
+            if (lane == 0) edge1[buf ^ 1][warp] = e1[0];
+            if (lane == 31) edge2[buf ^ 1][warp] = e2[CB - 1];
+            __syncthreads();
         }
     }
     tl_end(J.tl, kTlScan3);
