@@ -23,9 +23,8 @@ __global__ void __launch_bounds__(256) k_areas_errors(const Job* __restrict__ jo
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     const AreaPre pre = areas_prefetch(J, m.y);
     pdl_start(J.pdl_early != 0);
-    if (!J.st->active) return;
     tl_begin(J.tl, kTlAreas);
-    areas_body(J, m.y, update_state, pre);
+    areas_body(J, m.y, update_state, pre, true);
     tl_end(J.tl, kTlAreas);
     pdl_release();
 }

@@ -119,12 +119,16 @@ __device__ __forceinline__ AreaPre areas_prefetch(const Job& J, int item) {
 
 // update_state: 1 = errors + stop rule, 0 = errors only, -1 = areas only.
 // Edges go in groups of four, in order; the next group's edges are loaded
-// while the current group's vertices are in flight.
-__device__ inline void areas_body(const Job& J, int item, int update_state, const AreaPre& pre) {
+// while the current group's vertices are in flight.  check_active: the job's
+// active flag is read with the first vertices (one round trip) and a stopped
+// job's block leaves (the same in every thread of the block).
+__device__ inline void areas_body(const Job& J, int item, int update_state, const AreaPre& pre,
+                                  bool check_active = false) {
     __shared__ double wpart[kRegionsPerBlock];
     const int lw = area_warps_log2(J.n_edges, J.n_regions);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int v = pre.v, wr = pre.wr;
+    const int act = check_active ? J.st->active : 1;
     double acc = 0.0;
     if (v < J.n_regions) {
         float hi = 0.0f, lo = 0.0f;
@@ -136,8 +140,11 @@ __device__ inline void areas_body(const Job& J, int item, int update_state, cons
         for (int e = pre.e; e < e1; e += 4 * stride) {
             float2 p[4], q[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                p[u] = q[u] = make_float2(0.0f, 0.0f);
                 if (e + u * stride < e1) { p[u] = J.xy[ab[u].x]; q[u] = J.xy[ab[u].y]; }
+            }
+            if (!act) break;
             const int en = e + 4 * stride;
 #pragma unroll
             for (int u = 0; u < 4; ++u) ab[u] = (en + u * stride < e1) ? __ldg(J.edges + en + u * stride) : ab[u];
@@ -149,6 +156,7 @@ __device__ inline void areas_body(const Job& J, int item, int update_state, cons
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     }
+    if (!act) return;
     if (lane == 0) wpart[warp] = acc;
     __syncthreads();
     if (v < J.n_regions && wr == 0 && lane == 0) {

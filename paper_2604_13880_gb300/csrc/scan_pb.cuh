@@ -39,7 +39,12 @@ struct PbLayout {
     using T = typename Acc::T;
     static constexpr int CW = N / 32;                   // columns per lane in stage A
     static constexpr int kRowStride = N + N / CW;       // padded row of R
-    static constexpr size_t kR = (size_t)H * kRowStride * sizeof(T);
+    // phase 1 uses the R region for its bins: two [256][CB + H - 1] partial
+    // tables and the column sums, later the three prefix arrays
+    static constexpr int CB = N / kPbThreads;
+    static constexpr size_t kBins = ((size_t)2 * kPbThreads * (CB + H - 1) + N) * sizeof(T);
+    static constexpr size_t kRrows = (size_t)H * kRowStride * sizeof(T);
+    static constexpr size_t kR = kRrows > kBins ? kRrows : kBins;
     static constexpr size_t kTot = 16 * sizeof(T);
     static constexpr size_t kDens = (size_t)kPbDens * sizeof(float);
     static constexpr size_t kRing = (size_t)H * N * 2;
@@ -123,6 +128,120 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
         return;
     }
 
+    if constexpr (PHASE == 1) {
+        // The band's aggregates at its last row with zero carries need no row
+        // prefixes: with d the band's densities (local rows r = 0 .. H-1),
+        //   S(x)  = sum_{x' <= x} c(x'),            c(x')  = sum_r d(x', r)
+        //   E1(x) = sum_{t <= x + H - 1} D1(t),     D1(t)  = sum_{x' + r = t} d(x', r)
+        //   E2(x) = sum_{t <= x} D2(t),             D2(t)  = sum_{x' - r + H - 1 = t} d(x', r)
+        // (the sets of pixels that the rays of the recurrences cover).  Each
+        // thread bins its CB columns over the H rows (the diagonal bins in a
+        // window of CB + H - 1), the partial bins are added across threads in
+        // thread order, and three block scans give the prefixes.
+        constexpr int NBW = CB + H - 1;                  // a thread's diagonal bins
+        constexpr int M = N + H - 1;                     // diagonal bins of the band
+        constexpr int BPT = (M + kPbThreads - 1) / kPbThreads;
+        T cs[CB], b1[NBW], b2[NBW];
+#pragma unroll
+        for (int k = 0; k < CB; ++k) cs[k] = Acc::zero();
+#pragma unroll
+        for (int q = 0; q < NBW; ++q) { b1[q] = Acc::zero(); b2[q] = Acc::zero(); }
+        bool ok1 = true;
+#pragma unroll
+        for (int r = 0; r < H; ++r) {
+            float d[CB];
+            if (from_labels) {
+                ok1 = ok1 && mbar_wait(bars + r, 0u);
+                labels_to_density<CB>(smem_labels<CB>(ring + r * N, i0), table, d);
+            } else {
+#pragma unroll
+                for (int k = 0; k < CB; ++k) d[k] = dtex[(size_t)(j0 + r) * N + i0 + k];
+            }
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                const T v = Acc::from(d[k], qscale);
+                cs[k] = Acc::add(cs[k], v);
+                b1[k + r] = Acc::add(b1[k + r], v);
+                b2[k + H - 1 - r] = Acc::add(b2[k + H - 1 - r], v);
+            }
+        }
+        if (__syncthreads_or(!ok1)) {
+            if (tid == 0) {
+                atomicExch(&J.st->error, INIM_E_TIMEOUT);
+                for (int q = 0; q < H; ++q) mbar_wait(bars + q, 0u);
+            }
+            return;
+        }
+        T* P1 = Rs;                                      // [kPbThreads][NBW] partial D1 bins
+        T* P2 = Rs + kPbThreads * NBW;                   // [kPbThreads][NBW] partial D2 bins
+#pragma unroll
+        for (int q = 0; q < NBW; ++q) { P1[tid * NBW + q] = b1[q]; P2[tid * NBW + q] = b2[q]; }
+        __syncthreads();
+        // this thread's bins g = tid * BPT + u: the partials of the threads
+        // whose windows hold g, in thread order; then the local prefixes
+        T f1[BPT], f2[BPT];
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+            const int g = tid * BPT + u;
+            T a = Acc::zero(), b = Acc::zero();
+            if (g < M) {
+                const int t_lo = g >= NBW ? (g - NBW) / CB + 1 : 0;
+                const int t_hi = min(kPbThreads - 1, g / CB);
+                for (int t = t_lo; t <= t_hi; ++t) {
+                    a = Acc::add(a, P1[t * NBW + g - t * CB]);
+                    b = Acc::add(b, P2[t * NBW + g - t * CB]);
+                }
+            }
+            f1[u] = u ? Acc::add(f1[u - 1], a) : a;
+            f2[u] = u ? Acc::add(f2[u - 1], b) : b;
+        }
+#pragma unroll
+        for (int k = 1; k < CB; ++k) cs[k] = Acc::add(cs[k - 1], cs[k]);
+        // block exclusive offsets of the three local totals
+        __shared__ T wt[3][kPbThreads / 32];
+        T x1 = f1[BPT - 1], x2 = f2[BPT - 1], x3 = cs[CB - 1];
+        T i1 = x1, i2 = x2, i3 = x3;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y1 = Acc::shfl_up(i1, o), y2 = Acc::shfl_up(i2, o), y3 = Acc::shfl_up(i3, o);
+            if (lane >= o) { i1 = Acc::add(i1, y1); i2 = Acc::add(i2, y2); i3 = Acc::add(i3, y3); }
+        }
+        if (lane == 31) { wt[0][warp] = i1; wt[1][warp] = i2; wt[2][warp] = i3; }
+        __syncthreads();
+        // exclusive within the warp (the previous lane's inclusive value),
+        // then the earlier warps' totals in order
+        T o1 = Acc::shfl_up(i1, 1), o2 = Acc::shfl_up(i2, 1), o3 = Acc::shfl_up(i3, 1);
+        if (lane == 0) { o1 = Acc::zero(); o2 = Acc::zero(); o3 = Acc::zero(); }
+        for (int w = 0; w < warp; ++w) {
+            o1 = Acc::add(wt[0][w], o1); o2 = Acc::add(wt[1][w], o2); o3 = Acc::add(wt[2][w], o3);
+        }
+        // the prefixes: D1 and D2 to shared memory (read at shifted columns),
+        // the column sums' prefix in registers (this thread's own columns)
+        T* F1 = Rs;                                      // [M] (the partial bins are read)
+        T* F2 = Rs + M;
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+            const int g = tid * BPT + u;
+            if (g < M) { F1[g] = Acc::add(o1, f1[u]); F2[g] = Acc::add(o2, f2[u]); }
+        }
+        T Sagg[CB], a1[CB], a2[CB];
+#pragma unroll
+        for (int k = 0; k < CB; ++k) Sagg[k] = Acc::add(o3, cs[k]);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+            a1[k] = F1[i0 + k + H - 1];                  // E1(x) = P1(x + H - 1)
+            a2[k] = F2[i0 + k];                          // E2(x) = P2(x)
+        }
+        tl_end(J.tl, kTlScan1);
+        pdl_release();
+        T* agg = reinterpret_cast<T*>(J.agg);
+        store_row<Acc, CB>(agg + (size_t)band * N + i0, Sagg);
+        store_row<Acc, CB>(agg + (size_t)(nb + band) * N + i0, a1);
+        store_row<Acc, CB>(agg + (size_t)(2 * nb + band) * N + i0, a2);
+        return;
+    }
+
     // A: row prefixes, one warp per row, in segments of 32 x CWS columns
     // (a lane owns CWS contiguous columns of each segment; the segment's
     // offset is the row's running total, so at most CWS prefixes are live)
@@ -181,30 +300,6 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
         if (x < 0) return Acc::zero();
         return Rs[r * L::kRowStride + L::at(x)];
     };
-    if constexpr (PHASE == 1) {
-        // the band's aggregates at its last row with zero carries, as direct
-        // sums over the rows:
-        //   S(x) = sum_r R(x, r),  E1(x) = sum_r R'(x + H-1-r, r),  E2(x) = sum_r R'(x - (H-1-r), r)
-        T Sacc[CB], a1[CB], a2[CB];
-#pragma unroll
-        for (int k = 0; k < CB; ++k) { Sacc[k] = Acc::zero(); a1[k] = Acc::zero(); a2[k] = Acc::zero(); }
-#pragma unroll
-        for (int r = 0; r < H; ++r) {
-#pragma unroll
-            for (int k = 0; k < CB; ++k) {
-                Sacc[k] = Acc::add(Sacc[k], Rp(i0 + k, r));
-                a1[k] = Acc::add(Rp(i0 + k + H - 1 - r, r), a1[k]);
-                a2[k] = Acc::add(Rp(i0 + k - (H - 1 - r), r), a2[k]);
-            }
-        }
-        tl_end(J.tl, kTlScan1);
-        pdl_release();
-        T* agg = reinterpret_cast<T*>(J.agg);
-        store_row<Acc, CB>(agg + (size_t)band * N + i0, Sacc);
-        store_row<Acc, CB>(agg + (size_t)(nb + band) * N + i0, a1);
-        store_row<Acc, CB>(agg + (size_t)(2 * nb + band) * N + i0, a2);
-        return;
-    }
     // phase 3: the full rays at the band's rows, each thread its CB columns.
     // They start from the carries (the rays at row j0 - 1) and advance one
     // row at a time; the one value a row needs from beyond a thread's own

@@ -70,4 +70,8 @@ def test_roofline_entry_arithmetic():
     assert r["achieved"] == pytest.approx(algo["scan_phase3"] / 0.02e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["traffic"] == bench.TRAFFIC[("chain3", "scan_phase3", 8, 0, 256)]
+    assert bench.roofline(batches, "chain3", "scan_phase1", pk)["traffic"] == \
+        bench.TRAFFIC[("chain3", "scan_phase1", 8, 0, 256)]
+    # no capture of this tile: no traffic
+    batches["chain3"]["tile"] = dict(band_rows=16, cols_per_thread=0, threads=256)
     assert bench.roofline(batches, "chain3", "scan_phase1", pk)["traffic"] is None
