@@ -699,6 +699,12 @@ cudaError_t launch_carry(const Job* d_jobs, const BlockMap& carry, cudaStream_t 
     return launch_pdl(k_scan_carry_grouped<Acc>, carry.n_blocks, 32 * kCarryGroups, 0, s, d_jobs, cm);
 }
 
+// phase 1 of a row-serial tile: the binned form (scan_agg.cuh) for up to 8
+// columns a thread, the row-serial form beyond
+template <class Acc, int CPT, int NT>
+cudaError_t launch_scan_phase1(const Job* d_jobs, const BlockMap& band, const float* dtex, size_t ring_bytes,
+                               cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // launch: one (CPT, NT) instantiation per tile shape, N = CPT * NT
 // ---------------------------------------------------------------------------
@@ -717,8 +723,7 @@ cudaError_t launch_scan_tile(const Job* d_jobs, const BlockMap& band, const Bloc
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (phase == 0 || phase == 1)
-        e = launch_pdl(k_scan_band<Acc, CPT, NT, 1>, band.n_blocks, NT, ring_bytes, s, d_jobs, bm, dtex);
+    if (phase == 0 || phase == 1) e = launch_scan_phase1<Acc, CPT, NT>(d_jobs, band, dtex, ring_bytes, s);
     if (e == cudaSuccess && (phase == 0 || phase == 2)) {
         e = launch_carry<Acc>(d_jobs, carry, s);
     }
@@ -787,3 +792,26 @@ cudaError_t launch_scan_acc(const Job* d_jobs, const BlockMap& band, const Block
 
 #include "scan_pb.cuh"
 #include "scan_fused.cuh"
+#include "scan_agg.cuh"
+
+namespace inim {
+
+template <class Acc, int CPT, int NT>
+cudaError_t launch_scan_phase1(const Job* d_jobs, const BlockMap& band, const float* dtex, size_t ring_bytes,
+                               cudaStream_t s) {
+    if constexpr (CPT <= 8) {
+        using L = AggLayout<Acc, CPT, NT>;
+        static bool attr_set = false;
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(k_scan_band_agg<Acc, CPT, NT>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        return launch_pdl(k_scan_band_agg<Acc, CPT, NT>, band.n_blocks, NT, L::kBytes, s, d_jobs, band.d_map, dtex);
+    } else {
+        return launch_pdl(k_scan_band<Acc, CPT, NT, 1>, band.n_blocks, NT, ring_bytes, s, d_jobs, band.d_map, dtex);
+    }
+}
+
+}  // namespace inim
