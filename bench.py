@@ -746,21 +746,31 @@ def main():
         P.inim_autotune_scan(plan_d[2], reps=20)
     # The autotuner times each batch's scan alone; in the step the 72-solve
     # batch shares the GPU with the latency-bound cumulative chain, where
-    # other band heights can win.  Time the step with the tuned large tile
-    # and two other band heights, keep the fastest.
+    # other tiles can win.  Time the step with the tuned large tile, two other
+    # band heights of its form and the parallel-rows tile, keep the fastest.
     tuned = P.inim_get_scan_tile(k, P.INIM_FP32, 1)
+    tuned_t = (tuned["band_rows"], tuned["cols_per_thread"], tuned["threads"])
+    cands = []
+    if not fixed:
+        cands = [tuned_t]
+        if tuned_t[1] > 0:
+            cands += [(h, tuned_t[1], tuned_t[2]) for h in (16, 32, 64) if h != tuned_t[0]]
+        else:
+            cands += [(h, 4, 256) for h in (16, 32, 64)]
+        if (1 << k) in (512, 1024):
+            cands += [(h, 0, 256) for h in (8, 16) if (h, 0, 256) != tuned_t]
     step_times = {}
-    for H in ([] if fixed else sorted({tuned["band_rows"], 16, 32})):
-        P.inim_set_scan_tile(k, P.INIM_FP32, 1, H, tuned["cols_per_thread"], tuned["threads"])
+    for t in cands:
+        P.inim_set_scan_tile(k, P.INIM_FP32, 1, *t)
         run_step(plan_d)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         run_step(plan_d)
         torch.cuda.synchronize()
-        step_times[H] = time.perf_counter() - t0
+        step_times[t] = time.perf_counter() - t0
     if step_times:
-        best_H = min(step_times, key=step_times.get)
-        P.inim_set_scan_tile(k, P.INIM_FP32, 1, best_H, tuned["cols_per_thread"], tuned["threads"])
+        best_t = min(step_times, key=step_times.get)
+        P.inim_set_scan_tile(k, P.INIM_FP32, 1, *best_t)
     tiles = {cls: P.inim_get_scan_tile(k, P.INIM_FP32, large) for cls, large in (("large", 1), ("small", 0))}
 
     def barrier():
@@ -821,7 +831,8 @@ def main():
                        "l2": "inputs larger than L2 (72 solves x ~13 MB of textures per batched iteration)",
                        "parallelism": f"replicas{world}",
                        ("scan_tiles_fixed" if fixed else "scan_tiles_autotuned"): tiles,
-                       "large_band_rows_by_step_ms": {str(h): round(1e3 * t, 2) for h, t in step_times.items()}},
+                       "large_tile_by_step_ms": {",".join(map(str, h)): round(1e3 * t, 2)
+                                                 for h, t in step_times.items()}},
             "e2e": {"value": e2e_value, "unit": "iterations/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "host_buffers": "pinned"},
             "gpu_launches": int(launches), "wall_s_timed": wall,

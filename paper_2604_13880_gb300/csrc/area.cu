@@ -8,9 +8,10 @@
 // One kernel: a warp per region sums the shoelace terms of the region's edges
 // (contiguous in the edge list, coalesced loads) with exact FP32 products and
 // compensated FP32 sums (the FP64 pipe of this GPU is narrow; double is used
-// only for the per-lane partials and the error reduction); the last block of a job to
-// finish (atomic ticket) reduces the errors over the job's regions in a fixed
-// order and applies the stop rule, so the result does not depend on timing.
+// only for the per-lane partials and the region areas); the last block of a
+// job to finish (atomic ticket) forms the regions' relative errors in FP32,
+// reduces them in a fixed order (compensated sum, maximum) and applies the
+// stop rule, so the result does not depend on timing.
 #include "area_impl.cuh"
 
 namespace inim {

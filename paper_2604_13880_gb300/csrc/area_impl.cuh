@@ -8,9 +8,10 @@
 // One kernel: a warp per region sums the shoelace terms of the region's edges
 // (contiguous in the edge list, coalesced loads) with exact FP32 products and
 // compensated FP32 sums (the FP64 pipe of this GPU is narrow; double is used
-// only for the per-lane partials and the error reduction); the last block of a job to
-// finish (atomic ticket) reduces the errors over the job's regions in a fixed
-// order and applies the stop rule, so the result does not depend on timing.
+// only for the per-lane partials and the region areas); the last block of a
+// job to finish (atomic ticket) forms the regions' relative errors in FP32,
+// reduces them in a fixed order (compensated sum, maximum) and applies the
+// stop rule, so the result does not depend on timing.
 #pragma once
 
 #include "raster_common.cuh"
@@ -20,53 +21,88 @@ namespace inim {
 
 constexpr int kRegionsPerBlock = 8;
 
+// (hi, lo) += x exactly in hi + err, err accumulated into lo (two-sum)
+__device__ __forceinline__ void err_pair_add(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+    hi = s;
+}
+
+// The relative errors |o - w| / max(o, w) of the job's regions and their mean
+// (eps) and maximum (xi).  Every input is loaded at once (the mass of both
+// iteration parities, the state the stop rule reads), the per-region errors
+// are FP32 (relative error ~1e-7: this GPU's FP64 divisions are slow) and
+// their sum a compensated FP32 pair, reduced in a fixed order.
 __device__ inline void errors_and_stop(const Job& J, int update_state) {
-    __shared__ double ssum[kRegionsPerBlock], smax[kRegionsPerBlock];
+    __shared__ float shi[kRegionsPerBlock], slo[kRegionsPerBlock], smax[kRegionsPerBlock];
     __shared__ int sfold[kRegionsPerBlock];
     JobState* st = J.st;
-    const double M = st->mass_it[st->area_it & 1];       // this iteration's raster
-    double sum = 0.0, mx = 0.0;
+    const int area_it = __ldcg(&st->area_it);
+    const double m0 = __ldcg(&st->mass_it[0]), m1 = __ldcg(&st->mass_it[1]);
+    // thread 0: what the stop rule reads, loaded with the regions' data
+    int iters = 0, max_iters = 0, since = 0, stall = 0, stop_rule = 0, err = 0;
+    float xi_stop = 0.0f, eps_stop = 0.0f;
+    double best_xi = 0.0;
+    if (threadIdx.x == 0 && update_state) {
+        iters = __ldcg(&st->iters); max_iters = __ldcg(&st->max_iters); since = __ldcg(&st->since);
+        stall = __ldcg(&st->stall_window); stop_rule = __ldcg(&st->stop_on_rule); err = __ldcg(&st->error);
+        xi_stop = __ldcg(&st->xi_stop); eps_stop = __ldcg(&st->eps_stop); best_xi = __ldcg(&st->best_xi);
+    }
+    const double M = (area_it & 1) ? m1 : m0;     // this iteration's raster
+    const float inv_m = __frcp_rn((float)M);
+    float hi = 0.0f, lo = 0.0f, mx = 0.0f;
     int fold = 0;
     for (int v = threadIdx.x; v < J.n_regions; v += blockDim.x) {
         const double a = __ldcg(J.areas + v);
-        const double o = fabs(a);
-        const double w = (double)J.values[v] / M;
-        const double den = fmax(o, w);
-        const double e = den > 0.0 ? fabs(o - w) / den : 0.0;
-        sum += e;
-        mx = fmax(mx, e);
+        const float o = (float)fabs(a);
+        const float w = __fmul_rn(J.values[v], inv_m);
+        const float den = fmaxf(o, w);
+        const float e = den > 0.0f ? __fdiv_rn(fabsf(__fsub_rn(o, w)), den) : 0.0f;
+        err_pair_add(hi, lo, e);
+        mx = fmaxf(mx, e);
         const float s0 = J.sign0[v];
         if (s0 != 0.0f && ((a > 0.0) != (s0 > 0.0f) || a == 0.0)) fold = 1;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        err_pair_add(hi, lo, h2);
+        lo = __fadd_rn(lo, l2);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         fold |= __shfl_xor_sync(0xffffffffu, fold, o);
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { ssum[w] = sum; smax[w] = mx; sfold[w] = fold; }
+    if (lane == 0) { shi[w] = hi; slo[w] = lo; smax[w] = mx; sfold[w] = fold; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double S = 0.0, X = 0.0;
+        float H = 0.0f, L = 0.0f, X = 0.0f;
         int F = 0;
-        for (int k = 0; k < kRegionsPerBlock; ++k) { S += ssum[k]; X = fmax(X, smax[k]); F |= sfold[k]; }
-        const double eps = S / (double)J.n_regions;
+        for (int k = 0; k < kRegionsPerBlock; ++k) {
+            err_pair_add(H, L, shi[k]);
+            L = __fadd_rn(L, slo[k]);
+            X = fmaxf(X, smax[k]);
+            F |= sfold[k];
+        }
+        const double eps = ((double)H + (double)L) / (double)J.n_regions;
+        const double xi = (double)X;
         st->eps = eps;
-        st->xi = X;
-        st->area_it += 1;
+        st->xi = xi;
+        st->area_it = area_it + 1;
         if (F) st->foldover = 1;
         if (update_state) {
-            st->iters += 1;
-            if (X < st->best_xi) { st->best_xi = X; st->since = 0; }
-            else st->since += 1;
-            bool stop = st->iters >= st->max_iters;
-            if (st->stop_on_rule) {
-                if (st->xi_stop > 0.0f && X < (double)st->xi_stop) stop = true;
-                if (st->eps_stop > 0.0f && eps < (double)st->eps_stop) stop = true;
-                if (st->stall_window > 0 && st->since >= st->stall_window) stop = true;
+            iters += 1;
+            st->iters = iters;
+            if (xi < best_xi) { st->best_xi = xi; since = 0; }
+            else since += 1;
+            st->since = since;
+            bool stop = iters >= max_iters;
+            if (stop_rule) {
+                if (xi_stop > 0.0f && xi < (double)xi_stop) stop = true;
+                if (eps_stop > 0.0f && eps < (double)eps_stop) stop = true;
+                if (stall > 0 && since >= stall) stop = true;
             }
-            if (st->error != 0) stop = true;
+            if (err != 0) stop = true;
             if (stop) st->active = 0;
         }
     }
