@@ -169,14 +169,29 @@ cudaError_t refresh_bf16(inim_cnn& c) {
     return cudaGetLastError();
 }
 
+// log2 of a power of two, -1 otherwise
+int ilog2_exact(int v) {
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
 void conv(inim_cnn& c, int B, int res, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, int cin,
           int cout, int relu, __nv_bfloat16* y, float* yf) {
     ConvArgs a{};
     a.x = x; a.w = w; a.bias = bias; a.y_bf16 = y; a.y_f32 = yf;
     a.B = B; a.H = res; a.W = res; a.Cin = cin; a.Cout = cout; a.relu = relu;
+    a.lw = ilog2_exact(res);
+    a.lc = ilog2_exact(cin);
     const int M = B * res * res;
-    dim3 grid((M + kBM - 1) / kBM, (cout + kBN - 1) / kBN);
-    k_conv3x3_fwd<<<grid, kConvThreads, 0, c.stream>>>(a);
+    if (cout <= 32) {                  // 128 x 32 tiles: no idle half for the 32-channel layers
+        dim3 grid((M + 127) / 128, (cout + 31) / 32);
+        k_conv3x3_fwd<128, 32><<<grid, kConvThreads, 0, c.stream>>>(a);
+    } else {
+        dim3 grid((M + kBM - 1) / kBM, (cout + kBN - 1) / kBN);
+        k_conv3x3_fwd<kBM, kBN><<<grid, kConvThreads, 0, c.stream>>>(a);
+    }
 }
 
 void layer_fwd(inim_cnn& c, int l, int B, const __nv_bfloat16* x, __nv_bfloat16* y, float* yf = nullptr,
@@ -195,13 +210,20 @@ void layer_bwd(inim_cnn& c, int l, int B, const __nv_bfloat16* dz, const __nv_bf
     WgradArgs a{};
     a.dz = dz; a.x = x; a.dw = c.grads + c.w_off[l];
     a.B = B; a.H = s.res; a.W = s.res; a.Cin = s.cin; a.Cout = s.cout;
+    a.lw = ilog2_exact(s.res);
+    a.lc = ilog2_exact(s.cin);
     const int splits = std::max(1, std::min(256, P / 2048));
-    a.p_per_split = ((P + splits - 1) / splits + kBK - 1) / kBK * kBK;
+    a.p_per_split = ((P + splits - 1) / splits + kWK - 1) / kWK * kWK;
     dim3 grid((s.cout + kBM - 1) / kBM, (9 * s.cin + kBN - 1) / kBN, (P + a.p_per_split - 1) / a.p_per_split);
     k_conv3x3_wgrad<<<grid, kConvThreads, 0, c.stream>>>(a);
-    const int lanes = std::max(1, 256 / s.cout);
-    k_bias_grad<<<std::min(1024, (P + lanes - 1) / lanes), lanes * s.cout <= 256 ? lanes * s.cout : 256, 0, c.stream>>>(
-        dz, c.grads + c.b_off[l], P, s.cout);
+    if (s.cout % 8 == 0 && s.cout <= 256) {
+        const int ppb = 256 / (s.cout / 8);
+        k_bias_grad8<<<std::min(1024, (P + ppb - 1) / ppb), 256, 0, c.stream>>>(dz, c.grads + c.b_off[l], P, s.cout);
+    } else {
+        const int lanes = std::max(1, 256 / s.cout);
+        k_bias_grad<<<std::min(1024, (P + lanes - 1) / lanes), lanes * s.cout <= 256 ? lanes * s.cout : 256, 0,
+                      c.stream>>>(dz, c.grads + c.b_off[l], P, s.cout);
+    }
     if (dx) conv(c, B, s.res, dz, c.wf[l], nullptr, s.cout, s.cin, 0, dx, nullptr);
 }
 

@@ -5,8 +5,11 @@
 // Tensor cores: mma.sync.aligned.m16n8k16 (bf16 x bf16 -> f32).  Shared
 // tiles hold A as [m][k] and B as [n][k] (k contiguous, rows padded to 40
 // elements so that the fragment loads hit distinct banks).  A block computes
-// a 64 x 64 output tile with 4 warps (32 x 32 each = 2 x 4 mma tiles) and
-// walks K in steps of 32 with double-buffered shared tiles.
+// a BM x BN output tile with 4 warps of 32 x 32 (2 x 4 mma tiles each): 64 x 64,
+// or 128 x 32 for layers of at most 32 output channels, so that no half of
+// the tile is idle; K is walked in steps of 32 with double-buffered shared
+// tiles.  Feature maps have power-of-two sides and (past the first layer)
+// power-of-two channel counts: pixel and tap indices are shifts and masks.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -67,21 +70,36 @@ struct ConvArgs {
     float* y_f32;
     int B, H, W, Cin, Cout;
     int relu;
+    int lw;                   // log2 W (W = H, a power of two)
+    int lc;                   // log2 Cin, or -1 when Cin is not a power of two
 };
 
-// one 8-wide k chunk of the im2col row of output pixel p (zero outside)
-__device__ __forceinline__ uint4 im2col_chunk(const ConvArgs& a, int p, int k) {
+// the output pixel p as (b, y, x) of a square map of side 2^lw
+struct Pix { int b, y, x; bool in; };
+__device__ __forceinline__ Pix pix_of(const ConvArgs& a, int p) {
+    Pix q;
+    q.in = p < (a.B << (2 * a.lw));
+    q.x = p & ((1 << a.lw) - 1);
+    q.y = (p >> a.lw) & ((1 << a.lw) - 1);
+    q.b = p >> (2 * a.lw);
+    return q;
+}
+
+// one 8-wide k chunk of the im2col row of output pixel q (zero outside)
+__device__ __forceinline__ uint4 im2col_chunk_at(const ConvArgs& a, const Pix& q, int k) {
     const int K = 9 * a.Cin;
-    uint4 z = make_uint4(0, 0, 0, 0);
-    if (p >= a.B * a.H * a.W || k >= K) return z;
-    const int x = p % a.W, y = (p / a.W) % a.H, b = p / (a.W * a.H);
-    if ((a.Cin & 7) == 0) {
-        const int tap = k / a.Cin, ci = k - tap * a.Cin;
-        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    if (!q.in || k >= K) return z;
+    if (a.lc >= 3) {                                   // Cin a power of two >= 8: whole chunks
+        const int tap = k >> a.lc, ci = k & (a.Cin - 1);
+        const int dy = (tap * 11) >> 5, dx = tap - 3 * dy;   // tap / 3, tap % 3 for tap < 9
+        const int yy = q.y + dy - 1, xx = q.x + dx - 1;
         if (yy < 0 || yy >= a.H || xx < 0 || xx >= a.W) return z;
-        return *reinterpret_cast<const uint4*>(a.x + (((size_t)b * a.H + yy) * a.W + xx) * a.Cin + ci);
+        return *reinterpret_cast<const uint4*>(a.x + ((((size_t)q.b << a.lw) + yy) << a.lw) * a.Cin +
+                                               (size_t)xx * a.Cin + ci);
     }
-    // generic (Cin not a multiple of 8): element by element
+    const int x = q.x, y = q.y, b = q.b;
+    // generic (Cin not a power of two of at least 8): element by element
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -96,6 +114,10 @@ __device__ __forceinline__ uint4 im2col_chunk(const ConvArgs& a, int p, int k) {
     return *reinterpret_cast<const uint4*>(v);
 }
 
+__device__ __forceinline__ uint4 im2col_chunk(const ConvArgs& a, int p, int k) {
+    return im2col_chunk_at(a, pix_of(a, p), k);
+}
+
 __device__ __forceinline__ uint4 weight_chunk(const ConvArgs& a, int co, int k) {
     const int K = 9 * a.Cin;
     if (co >= a.Cout || k >= K) return make_uint4(0, 0, 0, 0);
@@ -106,20 +128,33 @@ __device__ __forceinline__ uint4 weight_chunk(const ConvArgs& a, int co, int k) 
     return *reinterpret_cast<const uint4*>(v);
 }
 
+template <int BM, int BN>
 __global__ void __launch_bounds__(kConvThreads) k_conv3x3_fwd(ConvArgs a) {
-    __shared__ __align__(16) __nv_bfloat16 As[2][kBM * kPad];
-    __shared__ __align__(16) __nv_bfloat16 Bs[2][kBN * kPad];
+    static_assert((BM / 32) * (BN / 32) == kConvThreads / 32, "4 warps of 32 x 32");
+    constexpr int WN = BN / 32;                           // warps along N
+    constexpr int RA = BM * 4 / kConvThreads;             // A chunks a thread loads per k step
+    constexpr int RB = BN * 4 / kConvThreads;             // B chunks
+    __shared__ __align__(16) __nv_bfloat16 As[2][BM * kPad];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][BN * kPad];
     const int M = a.B * a.H * a.W, K = 9 * a.Cin;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-    const int tid = threadIdx.x, warp = tid >> 5, wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, warp = tid >> 5, wm = warp / WN, wn = warp % WN;
     float acc[2][4][4] = {};
-    // each thread loads 2 chunks of A and 2 of B per k step (64 rows x 4 chunks)
+    // this thread's A rows (output pixels) do not change along K
+    Pix rows[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) rows[r] = pix_of(a, m0 + ((tid + r * kConvThreads) >> 2));
     auto load = [&](int buf, int k0) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int idx = tid + r * kConvThreads;       // 0..255
+        for (int r = 0; r < RA; ++r) {
+            const int idx = tid + r * kConvThreads;
             const int row = idx >> 2, ch = (idx & 3) * 8;
-            *reinterpret_cast<uint4*>(&As[buf][row * kPad + ch]) = im2col_chunk(a, m0 + row, k0 + ch);
+            *reinterpret_cast<uint4*>(&As[buf][row * kPad + ch]) = im2col_chunk_at(a, rows[r], k0 + ch);
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const int idx = tid + r * kConvThreads;
+            const int row = idx >> 2, ch = (idx & 3) * 8;
             *reinterpret_cast<uint4*>(&Bs[buf][row * kPad + ch]) = weight_chunk(a, n0 + row, k0 + ch);
         }
     };
@@ -168,20 +203,62 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_fwd(ConvArgs a) {
 // ---------------------------------------------------------------------------
 // weight gradient: dW[co][k] += sum_p dZ[p][co] * im2col(X)[p][k]
 //   GEMM: M = Cout, N = 9*Cin, reduction over the pixels p (split across
-//   blockIdx.z, FP32 atomics into dW).  A = dZ^T and B = im2col(X)^T are
-//   transposed into the [m][k] / [n][k] shared layout while loading.
+//   blockIdx.z, FP32 atomics into dW).  Both operands are staged pixel-major
+//   as they lie in memory (dZ[p][co] and im2col(X)[p][k], 16-byte chunks,
+//   rows padded to 72 elements), and the fragments of A = dZ^T and of the
+//   column-major B are read with ldmatrix.trans.  64 pixels per stage,
+//   double-buffered.
 // ---------------------------------------------------------------------------
 struct WgradArgs {
     const __nv_bfloat16* dz;   // [P][Cout]
     const __nv_bfloat16* x;    // [B][H][W][Cin]
     float* dw;                 // [Cout][9*Cin]
     int B, H, W, Cin, Cout;
-    int p_per_split;           // multiple of kBK
+    int p_per_split;           // multiple of kWK
+    int lw, lc;                // log2 W, log2 Cin (-1: not a power of two)
 };
 
+constexpr int kWK = 64;                    // pixels per stage
+constexpr int kWPad = 72;                  // padded row (elements) of the pixel-major tiles
+
+__device__ __forceinline__ void ldsm_x4_trans(unsigned (&r)[4], const __nv_bfloat16* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))));
+}
+
+// 32 x 32 warp tile of A = dZ^T (At [p][co]) times B (Bt [p][k]) over kWK pixels
+__device__ __forceinline__ void warp_mma_tile_t(const __nv_bfloat16* At, const __nv_bfloat16* Bt, int wm, int wn,
+                                                float (&acc)[2][4][4]) {
+    const int lane = threadIdx.x & 31;
+    const int q = lane >> 3, rr = lane & 7;          // matrix of the x4 load, row within it
+#pragma unroll
+    for (int kk = 0; kk < kWK; kk += 16) {
+        unsigned a[2][4], b[4][2];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) {
+            // matrices (m, k): (0, 0), (8, 0), (0, 8), (8, 8) -> a0, a1, a2, a3
+            const int k = kk + rr + ((q >> 1) << 3), m = wm * 32 + mi * 16 + ((q & 1) << 3);
+            ldsm_x4_trans(a[mi], At + k * kWPad + m);
+        }
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+            // matrices (k, n): (0, 0), (8, 0), (0, 8), (8, 8) -> b[2np][0], b[2np][1], b[2np+1][0], b[2np+1][1]
+            const int k = kk + rr + ((q & 1) << 3), n = wn * 32 + np * 16 + ((q >> 1) << 3);
+            unsigned r[4];
+            ldsm_x4_trans(r, Bt + k * kWPad + n);
+            b[2 * np][0] = r[0]; b[2 * np][1] = r[1]; b[2 * np + 1][0] = r[2]; b[2 * np + 1][1] = r[3];
+        }
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
+    }
+}
+
 __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
-    __shared__ __align__(16) __nv_bfloat16 As[kBM * kPad];   // [co][p]
-    __shared__ __align__(16) __nv_bfloat16 Bs[kBN * kPad];   // [k][p]
+    __shared__ __align__(16) __nv_bfloat16 At[2][kWK * kWPad];   // [p][co]
+    __shared__ __align__(16) __nv_bfloat16 Bt[2][kWK * kWPad];   // [p][k]
     const int P = a.B * a.H * a.W, K = 9 * a.Cin;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
     const int p_begin = blockIdx.z * a.p_per_split;
@@ -190,33 +267,37 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
     float acc[2][4][4] = {};
     ConvArgs ca{};
     ca.x = a.x; ca.B = a.B; ca.H = a.H; ca.W = a.W; ca.Cin = a.Cin; ca.Cout = a.Cout;
-    for (int p0 = p_begin; p0 < p_end; p0 += kBK) {
-        // 32 pixels x 64 co of dZ, 32 pixels x 64 k of im2col(X): 8-wide chunks
+    ca.lw = a.lw; ca.lc = a.lc;
+    const bool vec_dz = (a.Cout & 7) == 0;
+    // a thread stages chunks idx = tid + 128 r (r < 4): pixel idx >> 3, 8 channels / k at (idx & 7) * 8
+    auto load = [&](int buf, int p0) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int idx = tid + r * kConvThreads;     // 0..255
-            const int pl = idx >> 3, ch = (idx & 7) * 8;  // pixel 0..31, chunk of 8 co / k
+        for (int r = 0; r < 4; ++r) {
+            const int idx = tid + r * kConvThreads;
+            const int pl = idx >> 3, ch = (idx & 7) * 8;
             const int p = p0 + pl;
-            __align__(16) __nv_bfloat16 va[8];
-            __align__(16) __nv_bfloat16 vb[8];
             const bool pin = p < p_end;
-            if (pin && (a.Cout & 7) == 0 && m0 + ch + 8 <= a.Cout) {
-                *reinterpret_cast<uint4*>(va) = *reinterpret_cast<const uint4*>(a.dz + (size_t)p * a.Cout + m0 + ch);
-            } else {
+            uint4 va = make_uint4(0, 0, 0, 0);
+            if (pin && vec_dz && m0 + ch + 8 <= a.Cout) {
+                va = *reinterpret_cast<const uint4*>(a.dz + (size_t)p * a.Cout + m0 + ch);
+            } else if (pin) {
+                __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e)
-                    va[e] = (pin && m0 + ch + e < a.Cout) ? a.dz[(size_t)p * a.Cout + m0 + ch + e]
-                                                          : __float2bfloat16(0.0f);
+                    v[e] = m0 + ch + e < a.Cout ? a.dz[(size_t)p * a.Cout + m0 + ch + e] : __float2bfloat16(0.0f);
+                va = *reinterpret_cast<const uint4*>(v);
             }
-            *reinterpret_cast<uint4*>(vb) = pin ? im2col_chunk(ca, p, n0 + ch) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                As[(ch + e) * kPad + pl] = va[e];
-                Bs[(ch + e) * kPad + pl] = vb[e];
-            }
+            *reinterpret_cast<uint4*>(&At[buf][pl * kWPad + ch]) = va;
+            *reinterpret_cast<uint4*>(&Bt[buf][pl * kWPad + ch]) =
+                pin ? im2col_chunk(ca, p, n0 + ch) : make_uint4(0, 0, 0, 0);
         }
-        __syncthreads();
-        warp_mma_tile(As, Bs, wm, wn, acc);
+    };
+    const int ns = (p_end - p_begin + kWK - 1) / kWK;
+    if (ns > 0) load(0, p_begin);
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+        if (s + 1 < ns) load((s + 1) & 1, p_begin + (s + 1) * kWK);
+        warp_mma_tile_t(At[s & 1], Bt[s & 1], wm, wn, acc);
         __syncthreads();
     }
     const int lane = tid & 31, g = lane >> 2, t = lane & 3;
@@ -237,15 +318,47 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
 // ---------------------------------------------------------------------------
 // element-wise, pooling and optimiser kernels
 // ---------------------------------------------------------------------------
+// bias gradient for C a multiple of 8: a thread adds 8 channels of a pixel
+// at a time (16-byte loads), the block's sums meet in shared memory, one
+// global atomic per channel and block
+__global__ void __launch_bounds__(256) k_bias_grad8(const __nv_bfloat16* dz, float* db, int P, int C) {
+    __shared__ float sdb[256];
+    const int tpp = C >> 3;                          // threads per pixel
+    const int ppb = 256 / tpp;                       // pixels per block and round
+    const int gch = threadIdx.x % tpp, sub = threadIdx.x / tpp;
+    for (int c = threadIdx.x; c < C; c += 256) sdb[c] = 0.0f;
+    __syncthreads();
+    float acc[8] = {};
+    if (sub < ppb) {
+        for (int p = blockIdx.x * ppb + sub; p < P; p += gridDim.x * ppb) {
+            const uint4 v = *reinterpret_cast<const uint4*>(dz + (size_t)p * C + gch * 8);
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += __bfloat162float(e[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) atomicAdd(&sdb[gch * 8 + q], acc[q]);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += 256) atomicAdd(&db[c], sdb[c]);
+}
+
 // bias gradient: db[c] += sum_p dz[p][c]
+// (any C <= blockDim.x: the block's sums meet in shared memory first)
 __global__ void k_bias_grad(const __nv_bfloat16* dz, float* db, int P, int C) {
+    __shared__ float sdb[256];
     const int c = threadIdx.x % C;
     const int lanes = blockDim.x / C;
     const int sub = threadIdx.x / C;
-    if (sub >= lanes) return;
-    float s = 0.0f;
-    for (int p = blockIdx.x * lanes + sub; p < P; p += gridDim.x * lanes) s += __bfloat162float(dz[(size_t)p * C + c]);
-    atomicAdd(&db[c], s);
+    for (int q = threadIdx.x; q < C; q += blockDim.x) sdb[q] = 0.0f;
+    __syncthreads();
+    if (sub < lanes) {
+        float s = 0.0f;
+        for (int p = blockIdx.x * lanes + sub; p < P; p += gridDim.x * lanes) s += __bfloat162float(dz[(size_t)p * C + c]);
+        atomicAdd(&sdb[c], s);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < C; q += blockDim.x) atomicAdd(&db[q], sdb[q]);
 }
 
 // dz = dy * (z > 0), in place on dy (bf16)
