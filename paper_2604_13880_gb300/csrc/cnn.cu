@@ -185,12 +185,15 @@ void conv(inim_cnn& c, int B, int res, const __nv_bfloat16* x, const __nv_bfloat
     a.lw = ilog2_exact(res);
     a.lc = ilog2_exact(cin);
     const int M = B * res * res;
+    const bool async = a.lc >= 3;      // whole 16-byte chunks: the asynchronous-copy kernel
     if (cout <= 32) {                  // 128 x 32 tiles: no idle half for the 32-channel layers
         dim3 grid((M + 127) / 128, (cout + 31) / 32);
-        k_conv3x3_fwd<128, 32><<<grid, kConvThreads, 0, c.stream>>>(a);
+        if (async) k_conv3x3_fwd_async<128, 32><<<grid, kConvThreads, 0, c.stream>>>(a);
+        else k_conv3x3_fwd<128, 32><<<grid, kConvThreads, 0, c.stream>>>(a);
     } else {
         dim3 grid((M + kBM - 1) / kBM, (cout + kBN - 1) / kBN);
-        k_conv3x3_fwd<kBM, kBN><<<grid, kConvThreads, 0, c.stream>>>(a);
+        if (async) k_conv3x3_fwd_async<kBM, kBN><<<grid, kConvThreads, 0, c.stream>>>(a);
+        else k_conv3x3_fwd<kBM, kBN><<<grid, kConvThreads, 0, c.stream>>>(a);
     }
 }
 
