@@ -406,7 +406,10 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
     ca.x = a.x; ca.B = a.B; ca.H = a.H; ca.W = a.W; ca.Cin = a.Cin; ca.Cout = a.Cout;
     ca.lw = a.lw; ca.lc = a.lc;
     const bool vec_dz = (a.Cout & 7) == 0;
-    // a thread stages chunks idx = tid + 128 r (r < 4): pixel idx >> 3, 8 channels / k at (idx & 7) * 8
+    const bool vec_x = a.lc >= 3;
+    // a thread stages chunks idx = tid + 128 r (r < 4): pixel idx >> 3, 8 channels / k at (idx & 7) * 8;
+    // whole 16-byte chunks by asynchronous copies (zero fill outside), the
+    // others (the 2-channel head, the 1-channel input) through registers
     auto load = [&](int buf, int p0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -414,29 +417,45 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
             const int pl = idx >> 3, ch = (idx & 7) * 8;
             const int p = p0 + pl;
             const bool pin = p < p_end;
-            uint4 va = make_uint4(0, 0, 0, 0);
-            if (pin && vec_dz && m0 + ch + 8 <= a.Cout) {
-                va = *reinterpret_cast<const uint4*>(a.dz + (size_t)p * a.Cout + m0 + ch);
-            } else if (pin) {
+            __nv_bfloat16* da = &At[buf][pl * kWPad + ch];
+            if (vec_dz) {
+                const bool ok = pin && m0 + ch + 8 <= a.Cout;
+                cp_async16(da, ok ? a.dz + (size_t)p * a.Cout + m0 + ch : a.dz, ok);
+            } else {
                 __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e)
-                    v[e] = m0 + ch + e < a.Cout ? a.dz[(size_t)p * a.Cout + m0 + ch + e] : __float2bfloat16(0.0f);
-                va = *reinterpret_cast<const uint4*>(v);
+                    v[e] = (pin && m0 + ch + e < a.Cout) ? a.dz[(size_t)p * a.Cout + m0 + ch + e]
+                                                         : __float2bfloat16(0.0f);
+                *reinterpret_cast<uint4*>(da) = *reinterpret_cast<const uint4*>(v);
             }
-            *reinterpret_cast<uint4*>(&At[buf][pl * kWPad + ch]) = va;
-            *reinterpret_cast<uint4*>(&Bt[buf][pl * kWPad + ch]) =
-                pin ? im2col_chunk(ca, p, n0 + ch) : make_uint4(0, 0, 0, 0);
+            __nv_bfloat16* db = &Bt[buf][pl * kWPad + ch];
+            const int k = n0 + ch;
+            if (vec_x) {
+                const Pix q = pix_of(ca, p);
+                const int tap = k >> a.lc, ci = k & (a.Cin - 1);
+                const int dy = (tap * 11) >> 5, dx = tap - 3 * dy;
+                const int yy = q.y + dy - 1, xx = q.x + dx - 1;
+                const bool ok = pin && k < K && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                cp_async16(db, ok ? a.x + ((((size_t)q.b << a.lw) + yy) << a.lw) * a.Cin + (size_t)xx * a.Cin + ci
+                                  : a.x, ok);
+            } else {
+                *reinterpret_cast<uint4*>(db) = pin ? im2col_chunk(ca, p, k) : make_uint4(0, 0, 0, 0);
+            }
         }
     };
     const int ns = (p_end - p_begin + kWK - 1) / kWK;
     if (ns > 0) load(0, p_begin);
-    __syncthreads();
+    cp_async_commit();
     for (int s = 0; s < ns; ++s) {
-        if (s + 1 < ns) load((s + 1) & 1, p_begin + (s + 1) * kWK);
+        if (s + 1 < ns) load((s + 1) & 1, p_begin + (s + 1) * kWK);     // the buffer of stage s - 1
+        cp_async_commit();
+        cp_async_wait<1>();                   // this stage's copies (the next stage's may be in flight)
+        __syncthreads();
         warp_mma_tile_t(At[s & 1], Bt[s & 1], wm, wn, acc);
         __syncthreads();
     }
+    cp_async_wait<0>();
     const int lane = tid & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
