@@ -562,6 +562,20 @@ def timeline_study(args):
             arr[q].out_xy = outs[q].ctypes.data
             arr[q].params = P.params(log2_res=k, shape=sh, max_iters=ITERS, xi_stop=0.0, stall_window=0)
             arr[q].stats = None
+        # the same run without the timeline (its block counters are atomics on
+        # one address per kernel, which add to every launch): CUDA events
+        P.inim_timeline(False)
+        for _ in range(2):
+            _lib.check(lib.inim_run_batch(arr, len(arr), None), "timeline")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(4):
+            _lib.check(lib.inim_run_batch(arr, len(arr), None), "timeline")
+        ev1.record()
+        torch.cuda.synchronize()
+        plain_us = 1e3 * ev0.elapsed_time(ev1) / (4 * ITERS)
+        P.inim_timeline(True)
         for _ in range(2):                                # graphs, buffers, warm caches
             _lib.check(lib.inim_run_batch(arr, len(arr), None), "timeline")
         P.inim_timeline_read()
@@ -576,7 +590,7 @@ def timeline_study(args):
         gaps[f"{names[path[-1]]}->next {names[path[0]]}"] = float(
             np.median(st[path[0], lo + 1:hi] - en[path[-1], lo:hi - 1])) / 1e3
         res["batches"][name] = {"jobs": len(jobs), "us_per_iteration": float(np.median(np.diff(st[0, lo:hi]))) / 1e3,
-                                "kernel_us": kern, "gap_us": gaps}
+                                "us_per_iteration_timeline_off": plain_us, "kernel_us": kern, "gap_us": gaps}
     P.inim_timeline(False)
     print(json.dumps(res))
     return 0
