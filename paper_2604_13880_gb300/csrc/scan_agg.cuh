@@ -167,12 +167,18 @@ __global__ void __launch_bounds__(NT, (agg_min_blocks<Acc, CPT, NT>())) k_scan_b
         for (int u = 0; u < BPS; ++u) {
             const int g = tid * BPS + u;
             if (g < MSB) {
+                // at most NTB threads hold bin g: t_hi - NTB + 1 .. t_hi, in order
+                constexpr int NTB = (NBW + CPT - 1) / CPT;
                 const int t_lo = g >= NBW ? (g - NBW) / CPT + 1 : 0;
                 const int t_hi = min(NT - 1, g / CPT);
                 T a = Acc::zero(), b = Acc::zero();
-                for (int t = t_lo; t <= t_hi; ++t) {
-                    a = Acc::add(a, P1[t * NBW + g - t * CPT]);
-                    b = Acc::add(b, P2[t * NBW + g - t * CPT]);
+#pragma unroll
+                for (int v = 0; v < NTB; ++v) {
+                    const int t = t_hi - (NTB - 1) + v;
+                    if (t >= t_lo) {
+                        a = Acc::add(a, P1[t * NBW + g - t * CPT]);
+                        b = Acc::add(b, P2[t * NBW + g - t * CPT]);
+                    }
                 }
                 if (g + o1 < M) B1[g + o1] = Acc::add(B1[g + o1], a);
                 if (g + o2 >= 0 && g + o2 < M) B2[g + o2] = Acc::add(B2[g + o2], b);

@@ -185,11 +185,17 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
             const int g = tid * BPT + u;
             T a = Acc::zero(), b = Acc::zero();
             if (g < M) {
+                // at most NTB threads hold bin g: t_hi - NTB + 1 .. t_hi, in order
+                constexpr int NTB = (NBW + CB - 1) / CB;
                 const int t_lo = g >= NBW ? (g - NBW) / CB + 1 : 0;
                 const int t_hi = min(kPbThreads - 1, g / CB);
-                for (int t = t_lo; t <= t_hi; ++t) {
-                    a = Acc::add(a, P1[t * NBW + g - t * CB]);
-                    b = Acc::add(b, P2[t * NBW + g - t * CB]);
+#pragma unroll
+                for (int v = 0; v < NTB; ++v) {
+                    const int t = t_hi - (NTB - 1) + v;
+                    if (t >= t_lo) {
+                        a = Acc::add(a, P1[t * NBW + g - t * CB]);
+                        b = Acc::add(b, P2[t * NBW + g - t * CB]);
+                    }
                 }
             }
             f1[u] = u ? Acc::add(f1[u - 1], a) : a;
