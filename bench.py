@@ -80,11 +80,12 @@ def stage_bytes(n_jobs, N, V, R, E, K, nb):
 TRAFFIC = {
     ("chain3", "crossings", 8, 0, 256): 2.355e6,
     ("chain3", "raster_rows", 8, 0, 256): 0.876e6,
-    ("chain3", "scan_phase1", 8, 0, 256): 6.359e6,
+    ("chain3", "scan_phase1", 8, 0, 256): 6.363e6,
     ("chain3", "scan_carry", 8, 0, 256): 4.750e6,
     ("chain3", "scan_phase3", 8, 0, 256): 11.058e6,
     ("chain3", "gather_move", 8, 0, 256): 7.251e6,
-    ("direct72", "scan_phase1", 64, 4, 256): 156.793e6,
+    ("chain3", "areas_errors", 8, 0, 256): 1.988e6,
+    ("direct72", "scan_phase1", 64, 4, 256): 161.4e6,
     ("direct72", "scan_phase3", 16, 4, 256): 755.632e6,
     ("direct72", "scan_phase3", 32, 4, 256): 731.673e6,
     ("direct72", "scan_phase3", 64, 4, 256): 718.129e6,
