@@ -348,6 +348,46 @@ def quality_timing(args):
 
 
 # ---------------------------------------------------------------------------
+# dynamic area (Sec. 4.3, Eq. (Mb)) on the sweep's map and values
+# ---------------------------------------------------------------------------
+def dynamic_timing(args):
+    """inim_run_dynamic on the sweep's map (1024^2, 200 regions) and its 24
+    time steps, area fractions 0.45 .. 0.65, K fixed iterations per step, in
+    direct and in cumulative mode: iterations/s through the public call (host
+    values in, host vertices out, CUDA events around the call), and the same
+    steps with a fixed background (inim_run) for comparison."""
+    import torch
+    import paper_2604_13880_gb300 as P
+    from paper_2604_13880_gb300 import synth
+    w = synth.time_varying_workload()
+    mesh = w["mesh"]
+    k = w["log2_res"]
+    vals = np.ascontiguousarray(w["values"].astype(np.float32))
+    T = vals.shape[0]
+    m = P.inim_map_create(mesh)
+    a_min, a_max, K = 0.45, 0.65, args.dynamic
+    res = {"dynamic": w["name"], "steps": T, "iterations_per_step": K, "area_fractions": [a_min, a_max]}
+    bdv, frac = P.inim_background_values(vals, k, a_min, a_max)
+    res["background_value_range"] = [float(np.min(bdv)), float(np.max(bdv))]
+    for name, mode in (("direct", P.INIM_DIRECT), ("cumulative", P.INIM_CUMULATIVE)):
+        p = P.params(log2_res=k, shape=0.5, max_iters=K, xi_stop=0.0, stall_window=0, mode=mode)
+        for call, fn in (("dynamic", lambda: P.inim_run_dynamic(m, vals, p, a_min, a_max)),
+                         ("fixed_background", lambda: P.inim_run(m, vals, p))):
+            fn()                                                   # warm: batches, graphs
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            out, stats, _ = fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            res[f"{name}_{call}"] = {"ms": ms, "iterations_per_s": T * K / (ms / 1e3),
+                                     "eps_last": float(stats[-1]["eps"])}
+    print(json.dumps(res))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # direct vs cumulative (Sec. 5.5) on a random walk with large jumps
 # ---------------------------------------------------------------------------
 def coherence_study(args):
@@ -660,6 +700,8 @@ def main():
     ap.add_argument("--coherence-sigma", type=float, default=0.6)
     ap.add_argument("--quality", type=int, default=0, metavar="K",
                     help="instead of the sweep: time K calls of inim_quality on the sweep's map")
+    ap.add_argument("--dynamic", type=int, default=0, metavar="K",
+                    help="instead of the sweep: the dynamic-area series (Eq. (Mb)) with K iterations per step")
     ap.add_argument("--timeline", action="store_true",
                     help="instead of the sweep: in-graph kernel timeline of the sweep's two batch shapes")
     ap.add_argument("--config", choices=["sweep", "batched"], default="sweep",
@@ -678,6 +720,8 @@ def main():
         return quality_timing(args)
     if args.coherence_study:
         return coherence_study(args)
+    if args.dynamic:
+        return dynamic_timing(args)
     if args.config == "batched":
         return batched_config(args)
     if args.timeline:
