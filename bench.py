@@ -321,15 +321,17 @@ def precision_study(args):
 # quality measures (Sec. 3.3) of the sweep's map against a cartogram of it
 # ---------------------------------------------------------------------------
 def quality_timing(args):
-    """inim_quality on the sweep's map (1024^2, 200 regions) against its
-    cartogram after 20 iterations on the last time step's values: host wall
-    time per call (both rasters, the kernels, the call's own allocations)."""
+    """inim_quality on the sweep's map (1024^2, 200 regions; or, with
+    --quality-map 4096, the 4096^2 map of 2000 regions of the precision study)
+    against its cartogram after 20 iterations on the last time step's values:
+    host wall time per call (both rasters, the kernels, the call's own
+    allocations)."""
     import torch
     import paper_2604_13880_gb300 as P
     from paper_2604_13880_gb300 import synth
-    w = synth.time_varying_workload()
+    w = synth.precision_workload() if args.quality_map == 4096 else synth.time_varying_workload()
     mesh = w["mesh"]
-    k = w["log2_res"]
+    k = w.get("log2_res", 12)
     m = P.inim_map_create(mesh)
     x = torch.as_tensor(mesh.verts_f32(), device="cuda")
     v = torch.as_tensor(w["values"][-1].astype(np.float32), device="cuda")
@@ -700,6 +702,8 @@ def main():
     ap.add_argument("--coherence-sigma", type=float, default=0.6)
     ap.add_argument("--quality", type=int, default=0, metavar="K",
                     help="instead of the sweep: time K calls of inim_quality on the sweep's map")
+    ap.add_argument("--quality-map", type=int, default=1024, choices=[1024, 4096],
+                    help="the map of --quality: the sweep's (1024^2) or the precision study's (4096^2)")
     ap.add_argument("--dynamic", type=int, default=0, metavar="K",
                     help="instead of the sweep: the dynamic-area series (Eq. (Mb)) with K iterations per step")
     ap.add_argument("--timeline", action="store_true",
