@@ -293,6 +293,19 @@ int inim_set_persistent(int32_t enable);
 int inim_set_single_pass_scan(int32_t enable);
 
 /*
+ * Overlapped area kernel (default 1): each fused iteration's area, error and
+ * stop-rule kernel (Sec. 3.3, Sec. 4.1 step 7) runs beside the next
+ * iteration's raster and scan, and the next move waits for it.  With a stop
+ * rule the raster and scan after the stopping iteration still run on the
+ * returned vertices (the move after them sees the stop and leaves the
+ * vertices alone), so the returned vertices, iteration counts and errors are
+ * those of the sequential order (0), and the overlap flag also covers the
+ * raster of the returned vertices.  Drops no cached batch (both forms of the
+ * graphs are kept per batch).
+ */
+int inim_set_area_overlap(int32_t enable);
+
+/*
  * Kernel timeline (a profiling aid; no counterpart in the paper).  With
  * enable = 1 every batch built afterwards records, per launch of each kernel
  * of the iteration, when its first block starts working (after waiting for

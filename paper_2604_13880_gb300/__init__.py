@@ -337,6 +337,12 @@ PERSISTENT_PHASES = ("crossings", "rows", "density", "scan_phase1", "scan_carry"
                      "areas_errors")
 
 
+def inim_set_area_overlap(enable: bool) -> None:
+    """Each iteration's area kernel beside the next raster (the default), or
+    in sequence after the move."""
+    _lib.check(_lib.load().inim_set_area_overlap(1 if enable else 0), "inim_set_area_overlap")
+
+
 def inim_set_single_pass_scan(enable: bool) -> None:
     """Large batches scan in one pass, or with three kernels (the default)."""
     _lib.check(_lib.load().inim_set_single_pass_scan(1 if enable else 0), "inim_set_single_pass_scan")

@@ -158,6 +158,7 @@ _SIGS = {
     "inim_launch_count": (ctypes.c_longlong, []),
     "inim_set_wait_cap": (ctypes.c_int, [ctypes.c_int64]),
     "inim_set_single_pass_scan": (ctypes.c_int, [ctypes.c_int32]),
+    "inim_set_area_overlap": (ctypes.c_int, [ctypes.c_int32]),
     "inim_timeline": (ctypes.c_int, [ctypes.c_int32]),
     "inim_timeline_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.c_int32]),

@@ -270,9 +270,9 @@ struct Batch {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     // CUDA graphs of 1, 2, 4, ... 32 fused iterations (captured on first use),
-    // plain [0] and overlapped [1]: in the overlapped form (fixed-length runs)
-    // each iteration's area kernel runs on a side branch, next to the next
-    // iteration's raster and scan
+    // plain [0] and overlapped [1]: in the overlapped form each iteration's
+    // area kernel runs on a side branch, next to the next iteration's raster
+    // and scan
     cudaGraphExec_t graphs[2][kGraphSizes] = {};
     cudaStream_t side = nullptr;
     cudaEvent_t ev_moved = nullptr, ev_areas = nullptr;
@@ -298,6 +298,9 @@ struct Batch {
     Job* pin_jobs = nullptr;
     JobState* pin_states = nullptr;
     JobState* pin_out_states = nullptr;
+    // stop-rule polls: two pinned copies of the states, an event each
+    JobState* pin_poll = nullptr;
+    cudaEvent_t ev_poll[2] = {nullptr, nullptr};
     // learned warm start: pooled inputs, predicted fields, per-job field pointers
     float* ws_in = nullptr;
     float* ws_out = nullptr;
@@ -321,9 +324,18 @@ struct Batch {
         pin_rounds = 0;
     }
 
+    void free_poll() {
+        if (pin_poll) cudaFreeHost(pin_poll);
+        pin_poll = nullptr;
+        for (auto& e : ev_poll)
+            if (e) cudaEventDestroy(e);
+        ev_poll[0] = ev_poll[1] = nullptr;
+    }
+
     ~Batch() {
         if (stream) cudaStreamSynchronize(stream);     // no copy from the pinned buffers is still queued
         free_pinned();
+        free_poll();
         free_rounds();
         dfree(ws_in); dfree(ws_out); dfree(ws_ptrs);
         dfree(d_bar); dfree(d_err); dfree(all_band.d_map); dfree(all_carry.d_map);
@@ -560,9 +572,13 @@ cudaError_t enqueue_prologue(Batch& B, cudaStream_t s) {
 // the vertices have moved, and the next iteration's move waits for it (the
 // raster of the next iteration only reads the vertices, the move rewrites
 // them); `first` marks the first iteration of a captured sequence (the
-// previous area kernel finished with the previous graph launch).  Only for
-// runs of a fixed length: a stop decision taken by an area kernel would come
-// after the next iteration's raster started.
+// previous area kernel finished with the previous graph launch).  With a stop
+// rule the next iteration's raster and scan may start before the area kernel
+// has stopped the job: they work on the vertices the run returns and change
+// nothing the run reports but the raster flags (the overlap flag then covers
+// the returned vertices too); the move, which waits for the area kernel, sees
+// the stop and leaves the vertices alone, and every later kernel of the job
+// returns at once.
 cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s, bool overlap = false, bool first = true) {
     cudaError_t e = launch_raster_main(B.d_jobs, B.edge_blocks, B.row_blocks, B.max_n, s);
     if (e == cudaSuccess && !B.fuse_table) e = launch_density_table(B.d_jobs, (int)B.spec.size(), s);
@@ -586,6 +602,9 @@ cudaError_t enqueue_fused_iteration(Batch& B, cudaStream_t s, bool overlap = fal
 }
 
 constexpr int kPollIters = 8;   // iterations between host polls of the stop rule
+
+// the overlapped graphs (inim_set_area_overlap; see enqueue_fused_iteration)
+std::atomic<int> g_area_overlap{1};
 
 std::atomic<long long> g_launches{0};
 
@@ -654,16 +673,6 @@ cudaError_t launch_iterations(Batch& B, int iters, bool overlap = false) {
         }
     }
     return cudaSuccess;
-}
-
-// every job runs exactly max_iters iterations (no stop rule): the overlapped
-// graphs are safe
-bool fixed_length(const Batch& B, int max_iters) {
-    for (const JobState& st : B.h_states) {
-        const bool rule = st.stop_on_rule && (st.xi_stop > 0.0f || st.eps_stop > 0.0f || st.stall_window > 0);
-        if (rule || st.max_iters != max_iters) return false;
-    }
-    return true;
 }
 
 JobState initial_state(const inim_params& p, int stop_on_rule, int max_iters) {
@@ -744,7 +753,7 @@ int run_persistent(Batch& B, int iters, int rounds, const std::vector<int>& job_
 
 // enqueue a fixed-iteration run of the batch (graph replays) without waiting
 int enqueue_fused_async(Batch& B, int max_iters) {
-    const bool ov = fixed_length(B, max_iters);
+    const bool ov = g_area_overlap.load() != 0;
     int st = ensure_graph(B, ov);
     if (st != INIM_OK) return st;
     CUDA_TRY(enqueue_prologue(B, B.stream));
@@ -774,22 +783,41 @@ bool needs_poll(const inim_params& p) {
 int run_fused(Batch& B, int max_iters, bool poll) {
     const int nj = (int)B.spec.size();
     if (persistent_ok(B)) return run_persistent(B, max_iters, 1, std::vector<int>(nj, 1));
-    const bool ov = !poll && fixed_length(B, max_iters);
+    const bool ov = g_area_overlap.load() != 0;
     int st = ensure_graph(B, ov);
     if (st != INIM_OK) return st;
     CUDA_TRY(enqueue_prologue(B, B.stream));
     g_launches += 1;                                       // bucket reset
-    int done = 0;
-    while (done < max_iters) {
-        const int step = poll ? std::min(kPollIters, max_iters - done) : max_iters - done;
-        CUDA_TRY(launch_iterations(B, step, ov));
-        done += step;
-        if (poll && done < max_iters) {
-            CUDA_TRY(cudaMemcpyAsync(B.h_states.data(), B.d_states, nj * sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
-            CUDA_TRY(cudaStreamSynchronize(B.stream));
-            bool any = false;
-            for (auto& s : B.h_states) any |= (s.active != 0);
-            if (!any) break;
+    if (!poll) {
+        CUDA_TRY(launch_iterations(B, max_iters, ov));
+    } else {
+        // stop rule: graphs of kPollIters iterations; the states after each
+        // are copied to pinned memory behind an event, and the next graph is
+        // queued before the host waits for that event, so the GPU does not
+        // idle during a poll.  Graphs queued past the stop find every job
+        // inactive: their kernels return at once and change nothing.
+        if (!B.pin_poll) {
+            CUDA_TRY(cudaMallocHost(&B.pin_poll, 2 * (size_t)nj * sizeof(JobState)));
+            for (auto& e : B.ev_poll) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        int done = 0, slot = 0, pending = -1;
+        while (done < max_iters) {
+            const int step = std::min(kPollIters, max_iters - done);
+            CUDA_TRY(launch_iterations(B, step, ov));
+            done += step;
+            if (pending >= 0) {                            // the previous graph's states
+                CUDA_TRY(cudaEventSynchronize(B.ev_poll[pending]));
+                bool any = false;
+                for (int k = 0; k < nj; ++k) any |= (B.pin_poll[(size_t)pending * nj + k].active != 0);
+                if (!any) break;
+            }
+            if (done < max_iters) {
+                CUDA_TRY(cudaMemcpyAsync(B.pin_poll + (size_t)slot * nj, B.d_states, nj * sizeof(JobState),
+                                         cudaMemcpyDeviceToHost, B.stream));
+                CUDA_TRY(cudaEventRecord(B.ev_poll[slot], B.stream));
+                pending = slot;
+                slot ^= 1;
+            }
         }
     }
     CUDA_TRY(cudaMemcpyAsync(B.h_states.data(), B.d_states, nj * sizeof(JobState), cudaMemcpyDeviceToHost, B.stream));
@@ -1397,6 +1425,11 @@ int inim_run_series(const inim_series* S, int32_t n, void* stream) {
 
 int inim_set_persistent(int32_t enable) {
     g_persistent = enable ? 1 : 0;
+    return INIM_OK;
+}
+
+int inim_set_area_overlap(int32_t enable) {
+    g_area_overlap = enable ? 1 : 0;
     return INIM_OK;
 }
 

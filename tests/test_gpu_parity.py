@@ -414,21 +414,83 @@ def test_batch_mixed_resolutions_equals_single_runs():
 
 def test_overlapped_graph_equals_sequential_graph():
     # a fixed-length batch runs its area kernels next to the next iteration's
-    # raster; with a stop rule that cannot fire the same batch runs the
-    # sequential graph: vertices and the reported errors must be identical
+    # raster (the default) or after the move: vertices and the reported errors
+    # must be identical
     w = synth.time_varying_workload()
     mesh, vals = w["mesh"], w["values"].astype(np.float32)
     m = P.inim_map_create(mesh)
     res = []
-    for xi_stop in (0.0, 1e-30):
-        jobs = [dict(map=m, values=vals[t], params=P.params(log2_res=10, shape=sh, max_iters=19, xi_stop=xi_stop,
-                                                            stall_window=0))
-                for t, sh in ((0, 0.25), (5, 0.5), (11, 0.75))]
-        res.append(P.inim_run_batch(jobs))
+    try:
+        for ov in (True, False):
+            P.inim_set_area_overlap(ov)
+            jobs = [dict(map=m, values=vals[t], params=P.params(log2_res=10, shape=sh, max_iters=19, xi_stop=0.0,
+                                                                stall_window=0))
+                    for t, sh in ((0, 0.25), (5, 0.5), (11, 0.75))]
+            res.append(P.inim_run_batch(jobs))
+    finally:
+        P.inim_set_area_overlap(True)
     for b in range(3):
         np.testing.assert_array_equal(res[0][0][b], res[1][0][b])
         for key in ("iters", "eps", "xi", "foldover", "overlap"):
             assert res[0][1][b][key] == res[1][1][b][key], (b, key)
+
+
+def _stop_rule_runs(run):
+    """run() with the area kernel overlapped and in sequence"""
+    out = []
+    try:
+        for ov in (True, False):
+            P.inim_set_area_overlap(ov)
+            out.append(run())
+    finally:
+        P.inim_set_area_overlap(True)
+    return out
+
+
+def test_stop_rule_with_overlapped_area_kernel():
+    # With a stop rule the raster and scan after the stopping iteration start
+    # before the area kernel has stopped the job; the move after them must see
+    # the stop: the same vertices, iteration counts and errors as in sequence,
+    # and as a fixed run of the stopping iteration's length.  A batch whose
+    # jobs stop at different iterations (eps target, xi stall rule, cap).
+    mesh = synth.voronoi_map(40, 2500, seed=71, jitter=0.3)
+    m = P.inim_map_create(mesh)
+    vals = [synth.lognormal_values(40, seed=72 + t).astype(np.float32) for t in range(3)]
+    prm = [dict(eps_stop=0.25, xi_stop=0.0, stall_window=0, max_iters=200),
+           dict(eps_stop=0.0, xi_stop=0.0, stall_window=6, max_iters=200),
+           dict(eps_stop=0.0, xi_stop=0.0, stall_window=0, max_iters=23)]
+
+    def run():
+        jobs = [dict(map=m, values=vals[t], params=P.params(log2_res=9, shape=0.5, **prm[t])) for t in range(3)]
+        return P.inim_run_batch(jobs)
+
+    (o_ov, s_ov, _), (o_sq, s_sq, _) = _stop_rule_runs(run)
+    for t in range(3):
+        np.testing.assert_array_equal(o_ov[t], o_sq[t], err_msg=str(t))
+        for key in ("iters", "eps", "xi", "foldover"):
+            assert s_ov[t][key] == s_sq[t][key], (t, key, s_ov[t][key], s_sq[t][key])
+        assert 1 <= s_ov[t]["iters"] <= 200, s_ov[t]
+        # a fixed run of exactly that many iterations ends at the same vertices
+        n = s_ov[t]["iters"]
+        fx, fs, _ = P.inim_run(m, vals[t][None], P.params(log2_res=9, shape=0.5, max_iters=n, xi_stop=0.0,
+                                                           stall_window=0))
+        np.testing.assert_array_equal(o_ov[t], fx[0], err_msg=str(t))
+        assert fs[0]["iters"] == n and fs[0]["eps"] == s_ov[t]["eps"]
+    assert s_ov[0]["iters"] < 200 and s_ov[0]["eps"] < 0.25 and s_ov[2]["iters"] == 23
+
+
+def test_cumulative_stop_rule_with_overlapped_area_kernel():
+    # a cumulative series with the stop rule, round by round: each step's
+    # vertices and counts as in sequence
+    mesh = synth.voronoi_map(30, 1500, seed=81)
+    vals = synth.random_walk_values(30, 4, seed=82).astype(np.float32)
+    m = P.inim_map_create(mesh)
+    p = P.params(log2_res=8, shape=0.25, max_iters=120, xi_stop=0.02, stall_window=8, mode=P.INIM_CUMULATIVE)
+    (o_ov, s_ov, _), (o_sq, s_sq, _) = _stop_rule_runs(lambda: P.inim_run(m, vals, p))
+    np.testing.assert_array_equal(o_ov, o_sq)
+    for t in range(4):
+        for key in ("iters", "eps", "xi", "foldover"):
+            assert s_ov[t][key] == s_sq[t][key], (t, key)
 
 
 def test_stop_rule_reports_consistent_errors():
