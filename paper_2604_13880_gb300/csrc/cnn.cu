@@ -178,9 +178,9 @@ int ilog2_exact(int v) {
 }
 
 void conv(inim_cnn& c, int B, int res, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, int cin,
-          int cout, int relu, __nv_bfloat16* y, float* yf) {
+          int cout, int relu, __nv_bfloat16* y, float* yf, const __nv_bfloat16* mask = nullptr) {
     ConvArgs a{};
-    a.x = x; a.w = w; a.bias = bias; a.y_bf16 = y; a.y_f32 = yf;
+    a.x = x; a.w = w; a.bias = bias; a.y_bf16 = y; a.y_f32 = yf; a.mask = mask;
     a.B = B; a.H = res; a.W = res; a.Cin = cin; a.Cout = cout; a.relu = relu;
     a.lw = ilog2_exact(res);
     a.lc = ilog2_exact(cin);
@@ -205,8 +205,10 @@ void layer_fwd(inim_cnn& c, int l, int B, const __nv_bfloat16* x, __nv_bfloat16*
 
 // weight / bias gradient of layer l from dz (already masked) and its input x;
 // the data gradient into dx when dx != nullptr
+// dx_mask: the ReLU output whose gradient dx is (dx is zeroed where it is
+// <= 0, in the data-gradient convolution's epilogue), or nullptr
 void layer_bwd(inim_cnn& c, int l, int B, const __nv_bfloat16* dz, const __nv_bfloat16* x, __nv_bfloat16* dx,
-               int res_override = 0) {
+               int res_override = 0, const __nv_bfloat16* dx_mask = nullptr) {
     LayerSpec s = kSpec[l];
     if (res_override) s.res = res_override;
     const int P = B * s.res * s.res;
@@ -227,7 +229,7 @@ void layer_bwd(inim_cnn& c, int l, int B, const __nv_bfloat16* dz, const __nv_bf
         k_bias_grad<<<std::min(1024, (P + lanes - 1) / lanes), lanes * s.cout <= 256 ? lanes * s.cout : 256, 0,
                       c.stream>>>(dz, c.grads + c.b_off[l], P, s.cout);
     }
-    if (dx) conv(c, B, s.res, dz, c.wf[l], nullptr, s.cout, s.cin, 0, dx, nullptr);
+    if (dx) conv(c, B, s.res, dz, c.wf[l], nullptr, s.cout, s.cin, 0, dx, nullptr, dx_mask);
 }
 
 void relu_grad(inim_cnn& c, int t, int B) {
@@ -293,8 +295,7 @@ int backward(inim_cnn& c, const float* y, int B) {
     // the head's output gradient reuses the X0 gradient buffer (B*64*64*2 bf16 fits in U1's)
     __nv_bfloat16* gout = G[U1];
     k_mse<<<grid_for(no), 256, 0, c.stream>>>(c.out, y, gout, c.loss, no);
-    layer_bwd(c, 13, B, gout, A[D1B], G[D1B]);
-    relu_grad(c, D1B, B);
+    layer_bwd(c, 13, B, gout, A[D1B], G[D1B], 0, A[D1B]);
     layer_bwd(c, 12, B, G[D1B], A[D1], G[D1]);             // d1 = z11 + e1
     CK(cudaMemcpyAsync(G[Z11], G[D1], tsize(D1, B) * 2, cudaMemcpyDeviceToDevice, c.stream));
     relu_grad(c, Z11, B);
@@ -317,19 +318,17 @@ int backward(inim_cnn& c, const float* y, int B) {
     k_pool2_grad<<<grid_for(tsize(E3, B)), 256, 0, c.stream>>>(G[E3], G[P3], B, 16, 16, 128);
     k_accum<<<grid_for(tsize(E3, B)), 256, 0, c.stream>>>(G[E3], G[D3], tsize(E3, B));   // skip into d3
     relu_grad(c, E3, B);
-    layer_bwd(c, 5, B, G[E3], A[A4], G[A4]);
-    relu_grad(c, A4, B);
+    layer_bwd(c, 5, B, G[E3], A[A4], G[A4], 0, A[A4]);
     layer_bwd(c, 4, B, G[A4], A[P2], G[P2]);
     k_pool2_grad<<<grid_for(tsize(E2, B)), 256, 0, c.stream>>>(G[E2], G[P2], B, 32, 32, 64);
     k_accum<<<grid_for(tsize(E2, B)), 256, 0, c.stream>>>(G[E2], G[D2], tsize(E2, B));   // skip into d2
     relu_grad(c, E2, B);
-    layer_bwd(c, 3, B, G[E2], A[A2], G[A2]);
-    relu_grad(c, A2, B);
+    layer_bwd(c, 3, B, G[E2], A[A2], G[A2], 0, A[A2]);
     layer_bwd(c, 2, B, G[A2], A[P1], G[P1]);
     k_pool2_grad<<<grid_for(tsize(E1, B)), 256, 0, c.stream>>>(G[E1], G[P1], B, 64, 64, 32);
     k_accum<<<grid_for(tsize(E1, B)), 256, 0, c.stream>>>(G[E1], G[D1], tsize(E1, B));   // skip into d1
     relu_grad(c, E1, B);
-    layer_bwd(c, 1, B, G[E1], A[A0], G[A0]);
+    layer_bwd(c, 1, B, G[E1], A[A0], G[A0], 0, c.stem > 0 ? nullptr : A[A0]);
     if (c.stem > 0) {
         // back through the stem's pools to the first convolution's output,
         // its ReLU mask, and its weights at the input resolution
@@ -344,7 +343,6 @@ int backward(inim_cnn& c, const float* y, int B) {
         k_relu_grad<<<grid_for(n1), 256, 0, c.stream>>>(GS[1], S[1], n1);
         layer_bwd(c, 0, B, GS[1], S[0], nullptr, c.in_res);
     } else {
-        relu_grad(c, A0, B);
         layer_bwd(c, 0, B, G[A0], A[X0], nullptr);
     }
     CK(cudaGetLastError());

@@ -70,6 +70,7 @@ struct ConvArgs {
     float* y_f32;
     int B, H, W, Cin, Cout;
     int relu;
+    const __nv_bfloat16* mask;   // nullable: outputs where mask <= 0 are 0 (a ReLU's gradient)
     int lw;                   // log2 W (W = H, a power of two)
     int lc;                   // log2 Cin, or -1 when Cin is not a power of two
 };
@@ -183,6 +184,10 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_fwd(ConvArgs a) {
                     if (col + 1 < a.Cout) v1 += a.bias[col + 1];
                 }
                 if (a.relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                if (a.mask) {
+                    if (col < a.Cout && !(__bfloat162float(a.mask[(size_t)row * a.Cout + col]) > 0.0f)) v0 = 0.0f;
+                    if (col + 1 < a.Cout && !(__bfloat162float(a.mask[(size_t)row * a.Cout + col + 1]) > 0.0f)) v1 = 0.0f;
+                }
                 if (a.y_f32) {
                     if (col < a.Cout) a.y_f32[(size_t)row * a.Cout + col] = v0;
                     if (col + 1 < a.Cout) a.y_f32[(size_t)row * a.Cout + col + 1] = v1;
@@ -320,6 +325,10 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_fwd_async(ConvArgs a) 
                     if (col + 1 < a.Cout) v1 += a.bias[col + 1];
                 }
                 if (a.relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                if (a.mask) {
+                    if (col < a.Cout && !(__bfloat162float(a.mask[(size_t)row * a.Cout + col]) > 0.0f)) v0 = 0.0f;
+                    if (col + 1 < a.Cout && !(__bfloat162float(a.mask[(size_t)row * a.Cout + col + 1]) > 0.0f)) v1 = 0.0f;
+                }
                 if (a.y_f32) {
                     if (col < a.Cout) a.y_f32[(size_t)row * a.Cout + col] = v0;
                     if (col + 1 < a.Cout) a.y_f32[(size_t)row * a.Cout + col + 1] = v1;
