@@ -220,15 +220,8 @@ void layer_bwd(inim_cnn& c, int l, int B, const __nv_bfloat16* dz, const __nv_bf
     const int splits = std::max(1, std::min(256, P / 2048));
     a.p_per_split = ((P + splits - 1) / splits + kWK - 1) / kWK * kWK;
     dim3 grid((s.cout + kBM - 1) / kBM, (9 * s.cin + kBN - 1) / kBN, (P + a.p_per_split - 1) / a.p_per_split);
+    a.db = c.grads + c.b_off[l];              // the bias gradient rides along (N tile 0)
     k_conv3x3_wgrad<<<grid, kConvThreads, 0, c.stream>>>(a);
-    if (s.cout % 8 == 0 && s.cout <= 256) {
-        const int ppb = 256 / (s.cout / 8);
-        k_bias_grad8<<<std::min(1024, (P + ppb - 1) / ppb), 256, 0, c.stream>>>(dz, c.grads + c.b_off[l], P, s.cout);
-    } else {
-        const int lanes = std::max(1, 256 / s.cout);
-        k_bias_grad<<<std::min(1024, (P + lanes - 1) / lanes), lanes * s.cout <= 256 ? lanes * s.cout : 256, 0,
-                      c.stream>>>(dz, c.grads + c.b_off[l], P, s.cout);
-    }
     if (dx) conv(c, B, s.res, dz, c.wf[l], nullptr, s.cout, s.cin, 0, dx, nullptr, dx_mask);
 }
 

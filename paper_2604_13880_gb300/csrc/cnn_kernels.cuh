@@ -359,6 +359,7 @@ struct WgradArgs {
     const __nv_bfloat16* dz;   // [P][Cout]
     const __nv_bfloat16* x;    // [B][H][W][Cin]
     float* dw;                 // [Cout][9*Cin]
+    float* db;                 // nullable: [Cout] bias gradient (sum of dZ over the pixels), by the blocks of N tile 0
     int B, H, W, Cin, Cout;
     int p_per_split;           // multiple of kWK
     int lw, lc;                // log2 W, log2 Cin (-1: not a power of two)
@@ -416,6 +417,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
     ca.lw = a.lw; ca.lc = a.lc;
     const bool vec_dz = (a.Cout & 7) == 0;
     const bool vec_x = a.lc >= 3;
+    const bool bias_blk = a.db != nullptr && blockIdx.y == 0;     // uniform over the block
+    float db_acc = 0.0f;
     // a thread stages chunks idx = tid + 128 r (r < 4): pixel idx >> 3, 8 channels / k at (idx & 7) * 8;
     // whole 16-byte chunks by asynchronous copies (zero fill outside), the
     // others (the 2-channel head, the 1-channel input) through registers
@@ -462,9 +465,21 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
         cp_async_wait<1>();                   // this stage's copies (the next stage's may be in flight)
         __syncthreads();
         warp_mma_tile_t(At[s & 1], Bt[s & 1], wm, wn, acc);
+        if (bias_blk) {                       // the stage's dZ column sums: two threads a channel
+            const __nv_bfloat16* col = At[s & 1] + (tid & 63);
+#pragma unroll 8
+            for (int p = (tid >> 6); p < kWK; p += 2) db_acc += __bfloat162float(col[p * kWPad]);
+        }
         __syncthreads();
     }
     cp_async_wait<0>();
+    if (bias_blk) {
+        __shared__ float dbs[kConvThreads];
+        dbs[tid] = db_acc;
+        __syncthreads();
+        const int co = m0 + tid;
+        if (tid < 64 && co < a.Cout) atomicAdd(&a.db[co], dbs[tid] + dbs[tid + 64]);
+    }
     const int lane = tid & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
@@ -483,49 +498,6 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3x3_wgrad(WgradArgs a) {
 // ---------------------------------------------------------------------------
 // element-wise, pooling and optimiser kernels
 // ---------------------------------------------------------------------------
-// bias gradient for C a multiple of 8: a thread adds 8 channels of a pixel
-// at a time (16-byte loads), the block's sums meet in shared memory, one
-// global atomic per channel and block
-__global__ void __launch_bounds__(256) k_bias_grad8(const __nv_bfloat16* dz, float* db, int P, int C) {
-    __shared__ float sdb[256];
-    const int tpp = C >> 3;                          // threads per pixel
-    const int ppb = 256 / tpp;                       // pixels per block and round
-    const int gch = threadIdx.x % tpp, sub = threadIdx.x / tpp;
-    for (int c = threadIdx.x; c < C; c += 256) sdb[c] = 0.0f;
-    __syncthreads();
-    float acc[8] = {};
-    if (sub < ppb) {
-        for (int p = blockIdx.x * ppb + sub; p < P; p += gridDim.x * ppb) {
-            const uint4 v = *reinterpret_cast<const uint4*>(dz + (size_t)p * C + gch * 8);
-            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] += __bfloat162float(e[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) atomicAdd(&sdb[gch * 8 + q], acc[q]);
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < C; c += 256) atomicAdd(&db[c], sdb[c]);
-}
-
-// bias gradient: db[c] += sum_p dz[p][c]
-// (any C <= blockDim.x: the block's sums meet in shared memory first)
-__global__ void k_bias_grad(const __nv_bfloat16* dz, float* db, int P, int C) {
-    __shared__ float sdb[256];
-    const int c = threadIdx.x % C;
-    const int lanes = blockDim.x / C;
-    const int sub = threadIdx.x / C;
-    for (int q = threadIdx.x; q < C; q += blockDim.x) sdb[q] = 0.0f;
-    __syncthreads();
-    if (sub < lanes) {
-        float s = 0.0f;
-        for (int p = blockIdx.x * lanes + sub; p < P; p += gridDim.x * lanes) s += __bfloat162float(dz[(size_t)p * C + c]);
-        atomicAdd(&sdb[c], s);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < C; q += blockDim.x) atomicAdd(&db[q], sdb[q]);
-}
-
 // dz = dy * (z > 0), in place on dy (bf16)
 __global__ void k_relu_grad(__nv_bfloat16* dy, const __nv_bfloat16* z, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
