@@ -58,7 +58,7 @@ __device__ __forceinline__ int table_fix_bits(const Job& J, int o, float dbg) {
     return fb < 0 ? 0 : fb;
 }
 
-__device__ inline void table_state(const Job& J, const TableSums& t);
+__device__ inline void table_state(const Job& J, const TableSums& t, int raster_it);
 
 // The table into `table` (R + 1 entries, shared or global memory; the caller
 // synchronises before reading it).  lead: also publish it to J.dens (unless
@@ -71,6 +71,9 @@ __device__ inline TableSums region_table(const Job& J, float* table, bool lead) 
     const int R = J.n_regions;
     const int nt = (int)blockDim.x, tid = (int)threadIdx.x, lane = tid & 31;
     int bad = 0;
+    // the lead's iteration counter, loaded with the regions' data (not after
+    // the table, where a dependent round trip would delay the lead block)
+    const int raster_it = (lead && tid == 0) ? __ldcg(&J.st->raster_it) : 0;
     // with >= 256 threads, thread t holds the first kTableSlots regions of
     // virtual thread t (v = t + 256 q) for the table below
     const bool cache = nt >= 256;
@@ -157,7 +160,7 @@ __device__ inline TableSums region_table(const Job& J, float* table, bool lead) 
     if (tid == 0) {
         table[R] = t.dbg;
         if (publish) J.dens[R] = t.dbg;
-        if (lead) table_state(J, t);
+        if (lead) table_state(J, t, raster_it);
     }
     return t;
 }
@@ -166,18 +169,21 @@ __device__ inline TableSums region_table(const Job& J, float* table, bool lead) 
 // error, background pixel count, d0 and background value, total mass (and
 // its copy by iteration parity, for the area kernel that may run next to the
 // next iteration's table) and the fixed-point bits.
-__device__ inline void table_state(const Job& J, const TableSums& t) {
+__device__ inline void table_state(const Job& J, const TableSums& t, int raster_it) {
     if (t.bad) atomicExch(&J.st->error, INIM_E_VALUE);
     const long long o_bg = (long long)J.n * J.n - t.o;
     J.counts[J.n_regions] = (int)o_bg;
     JobState* st = J.st;
     const bool empty = (t.o == 0);
     const double s = (double)t.hi + (double)t.lo;
-    st->d0 = empty ? 1.0 : s / (double)t.o;
-    st->bdv_abs = J.bdv_value > 0.0f ? (double)J.bdv_value : (double)J.bdv_scale * st->d0;
-    st->mass = empty ? 1.0 : s + st->bdv_abs * (double)o_bg;
-    st->mass_it[st->raster_it & 1] = st->mass;
-    st->raster_it += 1;
+    const double d0 = empty ? 1.0 : s / (double)t.o;
+    const double bdv_abs = J.bdv_value > 0.0f ? (double)J.bdv_value : (double)J.bdv_scale * d0;
+    const double mass = empty ? 1.0 : s + bdv_abs * (double)o_bg;
+    st->d0 = d0;
+    st->bdv_abs = bdv_abs;
+    st->mass = mass;
+    st->mass_it[raster_it & 1] = mass;
+    st->raster_it = raster_it + 1;
     st->fix_bits = t.fix_bits;
 }
 
