@@ -61,8 +61,12 @@ __device__ __forceinline__ int clamped_ceil_div(long long num, long long den, in
 // belongs to the last lane whose exclusive prefix is <= i (found by a binary
 // search over the lanes' prefixes), which supplies its edges through
 // shuffles, and to the slot whose range holds it.  The warp's serial work is
-// total / 32 crossings instead of the longest edge's row count, with one
-// bucket atomic per lane and round for all of the warp's edges.
+// total / 32 crossings instead of the longest edge's row count; the bucket
+// atomics of kCrossPipe rounds go out together, so a warp whose stretched
+// edges cross many rows waits for one atomic round trip per 32 * kCrossPipe
+// crossings.
+constexpr int kCrossPipe = 4;
+
 template <int E>
 __device__ __forceinline__ void emit_crossings_lane(const Job& J, const bool (&valid)[E], const unsigned (&reg)[E],
                                                     const float2 (&p)[E], const float2 (&q)[E]) {
@@ -85,40 +89,56 @@ __device__ __forceinline__ void emit_crossings_lane(const Job& J, const bool (&v
     }
     const int excl = incl - cnt;
     const int total = __shfl_sync(full, incl, 31);
-    for (int base = 0; base < total; base += 32) {
-        const int i = base + lane;
-        int owner = 0;
+    for (int base = 0; base < total; base += 32 * kCrossPipe) {
+        // up to kCrossPipe rounds of 32 crossings, then their bucket atomics
+        // together (one round trip for the batch), then the key stores
+        int jq[kCrossPipe];
+        unsigned kq[kCrossPipe];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int cand = owner + step;
-            if (__shfl_sync(full, excl, cand) <= i) owner = cand;
-        }
-        const int k = i - __shfl_sync(full, excl, owner);     // index among the owner's crossings
-        long long X0 = 0, Y0 = 0, X1 = 0, Y1 = 0;
-        int j = 0;
-        unsigned r = 0;
-        int acc = 0;
+        for (int t = 0; t < kCrossPipe; ++t) {
+            jq[t] = -1;
+            kq[t] = 0;
+            if (base + 32 * t >= total) continue;             // warp-uniform
+            const int i = base + 32 * t + lane;
+            int owner = 0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int ce = __shfl_sync(full, c[e], owner);
-            const long long x0 = __shfl_sync(full, f[e].X0, owner), y0 = __shfl_sync(full, f[e].Y0, owner);
-            const long long x1 = __shfl_sync(full, f[e].X1, owner), y1 = __shfl_sync(full, f[e].Y1, owner);
-            const int jl = __shfl_sync(full, f[e].jlo, owner);
-            const unsigned re = __shfl_sync(full, reg[e], owner);
-            if (k >= acc && k < acc + ce) {
-                X0 = x0; Y0 = y0; X1 = x1; Y1 = y1;
-                j = jl + (k - acc);
-                r = re;
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = owner + step;
+                if (__shfl_sync(full, excl, cand) <= i) owner = cand;
             }
-            acc += ce;
+            const int k = i - __shfl_sync(full, excl, owner);     // index among the owner's crossings
+            long long X0 = 0, Y0 = 0, X1 = 0, Y1 = 0;
+            int j = 0;
+            unsigned r = 0;
+            int acc = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ce = __shfl_sync(full, c[e], owner);
+                const long long x0 = __shfl_sync(full, f[e].X0, owner), y0 = __shfl_sync(full, f[e].Y0, owner);
+                const long long x1 = __shfl_sync(full, f[e].X1, owner), y1 = __shfl_sync(full, f[e].Y1, owner);
+                const int jl = __shfl_sync(full, f[e].jlo, owner);
+                const unsigned re = __shfl_sync(full, reg[e], owner);
+                if (k >= acc && k < acc + ce) {
+                    X0 = x0; Y0 = y0; X1 = x1; Y1 = y1;
+                    j = jl + (k - acc);
+                    r = re;
+                }
+                acc += ce;
+            }
+            if (i < total) {
+                const long long dY = Y1 - Y0, dX = X1 - X0;
+                const long long Yc = 256LL * j + 128;
+                const int col = clamped_ceil_div(dX * (Yc - Y0) + (X0 - 128) * dY, 256 * dY, J.n);
+                jq[t] = j;
+                kq[t] = (r << 16) | (unsigned)col;
+            }
         }
-        if (i < total) {
-            const long long dY = Y1 - Y0, dX = X1 - X0;
-            const long long Yc = 256LL * j + 128;
-            const int col = clamped_ceil_div(dX * (Yc - Y0) + (X0 - 128) * dY, 256 * dY, J.n);
-            const int slot = atomicAdd(&J.row_cnt[j], 1);
-            if (slot < kKeyStride) J.keys[(size_t)j * kKeyStride + slot] = (r << 16) | (unsigned)col;
-        }
+        int slot[kCrossPipe];
+#pragma unroll
+        for (int t = 0; t < kCrossPipe; ++t) slot[t] = jq[t] >= 0 ? atomicAdd(&J.row_cnt[jq[t]], 1) : kKeyStride;
+#pragma unroll
+        for (int t = 0; t < kCrossPipe; ++t)
+            if (slot[t] < kKeyStride) J.keys[(size_t)jq[t] * kKeyStride + slot[t]] = kq[t];
     }
 }
 
