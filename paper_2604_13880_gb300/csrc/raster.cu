@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 5) k_raster_rows(const Jo
                                                                     const int2* __restrict__ bmap) {
     extern __shared__ __align__(16) unsigned rows_smem[];
     __shared__ int big[kWarpsPerBlock];
-    const int2 m = bmap[blockIdx.x];                 // (job, first row)
+    const int2 m = bmap[blockIdx.x];                 // (job, 8 x row item)
     const Job J = jobs[m.x];                         // fixed over a run: read before the wait
     pdl_start(J.pdl_early != 0);
     tl_begin(J.tl, kTlRows);

@@ -407,16 +407,19 @@ __device__ __forceinline__ void raster_row_warp(const Job& J, int j, int cnt, un
     if (lane == 0) J.row_cnt[j] = 0;     // ready for the next iteration
 }
 
-// rows [first_row, first_row + 8) of one job, one warp each; rows_smem holds
-// 8 * row_warp_bytes(N) bytes.  With check_active the job's active flag is
-// read together with the row's count and first key slots (one round trip).
-// A row with more crossings than a warp holds is returned (local_big: the
-// caller's block rasterises it) or appended to the job's big-row list.
-// Returns that row or -1, the same on every lane.
+// Item first_row / 8 = q of one job's n / 8 row items: rows q + w n / 8,
+// w = 0 .. 7, one warp each (rows spread over the texture, so that the rows
+// a stretched region makes long are shared out over the items instead of
+// filling a few); rows_smem holds 8 * row_warp_bytes(N) bytes.  With
+// check_active the job's active flag is read together with the row's count
+// and first key slots (one round trip).  A row with more crossings than a
+// warp holds is returned (local_big: the caller's block rasterises it) or
+// appended to the job's big-row list.  Returns that row or -1, the same on
+// every lane.
 __device__ __forceinline__ int raster_rows_item(const Job& J, int first_row, unsigned* rows_smem,
                                                 bool check_active = false, bool local_big = false) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = first_row + warp;
+    const int j = first_row / kWarpsPerBlock + warp * (J.n / kWarpsPerBlock);
     if (warp >= kWarpsPerBlock || j >= J.n) return -1;
     unsigned* diff = rows_smem + (size_t)warp * (row_warp_bytes(J.n) / 4);
     const uint32_t* bucket = J.keys + (size_t)j * kKeyStride;
