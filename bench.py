@@ -78,7 +78,7 @@ def stage_bytes(n_jobs, N, V, R, E, K, nb):
 # The 3-solve batch's textures stay in L2, so its kernels move far fewer DRAM
 # bytes than their algorithmic bytes.
 TRAFFIC = {
-    ("chain3", "crossings", 8, 0, 256): 2.355e6,
+    ("chain3", "crossings", 8, 0, 256): 2.367e6,
     ("chain3", "raster_rows", 8, 0, 256): 0.876e6,
     ("chain3", "scan_phase1", 8, 0, 256): 6.363e6,
     ("chain3", "scan_carry", 8, 0, 256): 4.750e6,
@@ -577,7 +577,10 @@ def timeline_study(args):
     timeline on: per kernel the median time from its first block's start to
     its last block's end, the median gap to the next kernel's first block,
     and the time per iteration (medians over iterations 5-49).  Scan tiles
-    from --tiles (default: the tiles the sweep uses)."""
+    from --tiles (default: the tiles the sweep uses).  Also the chain's
+    kernel timeline at later rounds of its cumulative series
+    (chain_rounds_timeline) and the step split by series kind
+    (series_split)."""
     import torch
     import paper_2604_13880_gb300 as P
     from paper_2604_13880_gb300 import _lib, synth
@@ -635,8 +638,107 @@ def timeline_study(args):
         res["batches"][name] = {"jobs": len(jobs), "us_per_iteration": float(np.median(np.diff(st[0, lo:hi]))) / 1e3,
                                 "us_per_iteration_timeline_off": plain_us, "kernel_us": kern, "gap_us": gaps}
     P.inim_timeline(False)
+    res["chain3_rounds"] = chain_rounds_timeline(P, _lib, lib, m, mesh, k, vals, names)
+    res["series_split_ms"] = series_split(P, _lib, lib, m, mesh, k, vals)
     print(json.dumps(res))
     return 0
+
+
+def chain_rounds_timeline(P, _lib, lib, m, mesh, k, vals, names, sample=(0, 12, 23)):
+    """The cumulative chain advanced round by round from the initial map (each
+    round starts from the previous round's 50-iteration result), with the
+    kernel timeline of the sampled rounds: their maps stretch, rows hold more
+    crossings and regions fold over.  Per sampled round: median kernel times
+    and time per iteration (iterations 5-49), the mean crossings per row and
+    the flags of the three solves."""
+    import torch
+    xy = [torch.as_tensor(mesh.verts_f32(), device="cuda").contiguous() for _ in SHAPES]
+    out = [torch.empty_like(x) for x in xy]
+    N = 1 << k
+
+    def run_round(t):
+        arr = (P.inim_job * len(SHAPES))()
+        stats = (P.inim_step_stats * len(SHAPES))()
+        for q, sh in enumerate(SHAPES):
+            arr[q].map = m.handle
+            arr[q].values = vals[t].ctypes.data
+            arr[q].init_xy = xy[q].data_ptr()
+            arr[q].out_xy = out[q].data_ptr()
+            arr[q].params = P.params(log2_res=k, shape=sh, max_iters=ITERS, xi_stop=0.0, stall_window=0)
+            arr[q].stats = ctypes.cast(ctypes.byref(stats[q]), ctypes.POINTER(P.inim_step_stats))
+        _lib.check(lib.inim_run_batch(arr, len(arr), None), "chain round")
+        return stats
+
+    rounds = {}
+    for t in range(T_STEPS):
+        if t in sample:
+            P.inim_timeline(True)
+            for _ in range(2):
+                run_round(t)
+            P.inim_timeline_read()
+            stats = run_round(t)
+            st, en = P.inim_timeline_read()
+            P.inim_timeline(False)
+            ran = [q for q in range(len(names)) if st[q, 5] > 0]
+            rows = float(np.mean([crossings_count(mesh_at(mesh, x.cpu().numpy()), N) for x in xy])) / N
+            rounds[str(t)] = {
+                "us_per_iteration": float(np.median(np.diff(st[0, 5:ITERS]))) / 1e3,
+                "kernel_us": {names[q]: float(np.median(en[q, 5:ITERS] - st[q, 5:ITERS])) / 1e3 for q in ran},
+                "crossings_per_row": rows,
+                "foldover": [int(x.foldover) for x in stats], "overlap": [int(x.overlap) for x in stats]}
+        run_round(t)
+        torch.cuda.synchronize()
+        for q in range(len(SHAPES)):
+            xy[q].copy_(out[q])
+    return rounds
+
+
+def mesh_at(mesh, xy):
+    """The mesh with its vertices moved to xy."""
+    from paper_2604_13880_gb300 import synth
+    return synth.Mesh(np.asarray(xy, np.float64), mesh.ring_off, mesh.ring_idx, mesh.ring_region, mesh.n_regions)
+
+
+def series_split(P, _lib, lib, m, mesh, k, vals, reps=5):
+    """One sweep step as inim_run_series calls: both series kinds (the
+    benchmark's step), the 3 direct series alone and the 3 cumulative series
+    alone; median wall ms of `reps` calls after 3 warm-up calls."""
+    import torch
+    V = mesh.n_verts
+    vals_d = torch.as_tensor(vals, device="cuda").contiguous()
+    out_d = torch.empty((len(SHAPES) * T_STEPS, V, 2), device="cuda")
+    out_c = torch.empty((len(SHAPES) * T_STEPS, V, 2), device="cuda")
+
+    def series(kinds):
+        ser = (P.inim_series * (len(kinds) * len(SHAPES)))()
+        for a, (mode, buf) in enumerate(kinds):
+            for b, sh in enumerate(SHAPES):
+                x = ser[a * len(SHAPES) + b]
+                x.map = m.handle
+                x.values = vals_d.data_ptr()
+                x.T = T_STEPS
+                x.init_xy = None
+                x.out_xy = buf.data_ptr() + b * T_STEPS * V * 8
+                x.params = P.params(log2_res=k, shape=sh, max_iters=ITERS, xi_stop=0.0, stall_window=0, mode=mode)
+                x.stats = None
+        return ser
+
+    res = {}
+    for name, kinds in (("both", [(P.INIM_DIRECT, out_d), (P.INIM_CUMULATIVE, out_c)]),
+                        ("direct_only", [(P.INIM_DIRECT, out_d)]),
+                        ("cumulative_only", [(P.INIM_CUMULATIVE, out_c)])):
+        ser = series(kinds)
+        for _ in range(3):
+            _lib.check(lib.inim_run_series(ser, len(ser), None), name)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            _lib.check(lib.inim_run_series(ser, len(ser), None), name)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        res[name] = float(np.median(ts))
+    return res
 
 
 # ---------------------------------------------------------------------------
