@@ -16,22 +16,59 @@ namespace inim {
 
 namespace {
 
+// blocks per SM the register budget aims at: four for FP32 (the sweep's
+// chain launches ~4 blocks per SM in one wave), two for the wider sums
 template <class Acc>
-__global__ void __launch_bounds__(256) k_gather_move(const Job* __restrict__ jobs,
-                                                     const int2* __restrict__ bmap) {
+constexpr int gather_min_blocks() { return sizeof(typename Acc::T) == 4 ? 4 : 2; }
+
+template <class Acc>
+__global__ void __launch_bounds__(256, (gather_min_blocks<Acc>())) k_gather_move(const Job* __restrict__ jobs,
+                                                                              const int2* __restrict__ bmap) {
     const int2 m = bmap[blockIdx.x];
     const Job J = jobs[m.x];                  // fixed over a run: read before the wait
     const int v = m.y * blockDim.x + threadIdx.x;
-    pdl_start(J.pdl_early != 0);
-    if (v >= J.n_verts) return;
-    // the active flag, the vertex and C in one round trip
-    const int act = J.st->active;
-    const float2 p = J.xy[v];
-    const typename Acc::T C = grand_total<Acc>(J);
-    if (!act) return;
-    tl_begin(J.tl, kTlGather);
-    move_vertex<Acc>(J, v, p, C);
-    tl_end(J.tl, kTlGather);
+    if constexpr (sizeof(typename Acc::T) == 4) {
+        // FP32: the vertex before the wait too (only this kernel writes it,
+        // and the previous iteration's move has completed: the kernels in
+        // between have passed their waits), so that its corners are known
+        // when the wait returns and the active flag, C and the corner sums
+        // of the interleaved table go out in one round trip
+        const bool has_v = v < J.n_verts;
+        const float2 p = has_v ? J.xy[v] : make_float2(0.0f, 0.0f);
+        const CornerPos cp = corner_pos(J.n, p);
+        pdl_start(J.pdl_early != 0);
+        if (!has_v) return;
+        if (J.ST) {
+            CornerSums<Acc> q[4];
+            load_corners<Acc>(J, cp.i0, cp.j0, q);
+            const int act = J.st->active;
+            const typename Acc::T C = grand_total<Acc>(J);
+            if (!act) return;
+            tl_begin(J.tl, kTlGather);
+            const float2 dlt = displacement_from<Acc>(J, cp, q, C);
+            J.xy[v] = make_float2(p.x + J.lam * dlt.x, p.y + J.lam * dlt.y);
+            tl_end(J.tl, kTlGather);
+        } else {
+            const int act = J.st->active;
+            const typename Acc::T C = grand_total<Acc>(J);
+            if (!act) return;
+            tl_begin(J.tl, kTlGather);
+            move_vertex<Acc>(J, v, p, C);
+            tl_end(J.tl, kTlGather);
+        }
+    } else {
+        // the wider sums of the other precisions: the active flag, the vertex
+        // and C in one round trip, then the corners
+        pdl_start(J.pdl_early != 0);
+        if (v >= J.n_verts) return;
+        const int act = J.st->active;
+        const float2 p = J.xy[v];
+        const typename Acc::T C = grand_total<Acc>(J);
+        if (!act) return;
+        tl_begin(J.tl, kTlGather);
+        move_vertex<Acc>(J, v, p, C);
+        tl_end(J.tl, kTlGather);
+    }
     pdl_release();
 }
 

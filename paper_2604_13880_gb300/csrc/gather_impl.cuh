@@ -226,41 +226,68 @@ __device__ __forceinline__ void uniform_ratios4(int i0, int j0, int n, float inv
     }
 }
 
+// The pixel (i0, j0) whose centre is the top-left of the four around p (kept
+// inside the texture) and p's bilinear weights (a, b) towards i0 + 1, j0 + 1.
+struct CornerPos {
+    int i0, j0;
+    float a, b;
+};
+
+__device__ __forceinline__ CornerPos corner_pos(int n, float2 p) {
+    const float fx = p.x * (float)n - 0.5f;
+    const float fy = p.y * (float)n - 0.5f;
+    CornerPos c;
+    c.i0 = min(max((int)floorf(fx), 0), n - 2);
+    c.j0 = min(max((int)floorf(fy), 0), n - 2);
+    c.a = fminf(fmaxf(fx - (float)c.i0, 0.0f), 1.0f);
+    c.b = fminf(fmaxf(fy - (float)c.j0, 0.0f), 1.0f);
+    return c;
+}
+
+__device__ __forceinline__ float2 bilinear(const float2 (&f)[4], float a, float b) {
+    const float2 top = make_float2((1.0f - a) * f[0].x + a * f[1].x, (1.0f - a) * f[0].y + a * f[1].y);
+    const float2 bot = make_float2((1.0f - a) * f[2].x + a * f[3].x, (1.0f - a) * f[2].y + a * f[3].y);
+    return make_float2((1.0f - b) * top.x + b * bot.x, (1.0f - b) * top.y + b * bot.y);
+}
+
+// The displacement from the interleaved table's corner sums already loaded.
 template <class Acc>
-__device__ __forceinline__ float2 displacement_at_c(const Job& J, float2 p, typename Acc::T C) {
+__device__ __forceinline__ float2 displacement_from(const Job& J, const CornerPos& cp, const CornerSums<Acc> (&q)[4],
+                                                    typename Acc::T C) {
     const int n = J.n;
     const double inv_c = Acc::inv(C);
     const float inv_n = 1.0f / (float)n;
     const float inv_c0 = ldexpf(1.0f, -2 * J.log2n);
-    const float fx = p.x * (float)n - 0.5f;
-    const float fy = p.y * (float)n - 0.5f;
-    int i0 = (int)floorf(fx), j0 = (int)floorf(fy);
-    i0 = min(max(i0, 0), n - 2);
-    j0 = min(max(j0, 0), n - 2);
-    const float a = fminf(fmaxf(fx - (float)i0, 0.0f), 1.0f);
-    const float b = fminf(fmaxf(fy - (float)j0, 0.0f), 1.0f);
+    Ratios r0[4];
+    uniform_ratios4(cp.i0, cp.j0, n, inv_c0, r0);
     float2 f[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int i = cp.i0 + (c & 1), j = cp.j0 + (c >> 1);
+        f[c] = delta_at_pixel(ratios_from<Acc>(q[c], i - j, C, inv_c), r0[c], i, j, inv_n);
+    }
+    return bilinear(f, cp.a, cp.b);
+}
+
+template <class Acc>
+__device__ __forceinline__ float2 displacement_at_c(const Job& J, float2 p, typename Acc::T C) {
+    const int n = J.n;
+    const CornerPos cp = corner_pos(n, p);
     if (J.ST) {
         CornerSums<Acc> q[4];
-        load_corners<Acc>(J, i0, j0, q);
-        Ratios r0[4];
-        uniform_ratios4(i0, j0, n, inv_c0, r0);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int i = i0 + (c & 1), j = j0 + (c >> 1);
-            f[c] = delta_at_pixel(ratios_from<Acc>(q[c], i - j, C, inv_c), r0[c], i, j, inv_n);
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int i = i0 + (c & 1), j = j0 + (c >> 1);
-            f[c] = delta_at_pixel(corner_ratios<Acc>(J, i, j, C, inv_c), uniform_ratios(i, j, n, inv_c0), i, j,
-                                  inv_n);
-        }
+        load_corners<Acc>(J, cp.i0, cp.j0, q);
+        return displacement_from<Acc>(J, cp, q, C);
     }
-    const float2 top = make_float2((1.0f - a) * f[0].x + a * f[1].x, (1.0f - a) * f[0].y + a * f[1].y);
-    const float2 bot = make_float2((1.0f - a) * f[2].x + a * f[3].x, (1.0f - a) * f[2].y + a * f[3].y);
-    return make_float2((1.0f - b) * top.x + b * bot.x, (1.0f - b) * top.y + b * bot.y);
+    const double inv_c = Acc::inv(C);
+    const float inv_n = 1.0f / (float)n;
+    const float inv_c0 = ldexpf(1.0f, -2 * J.log2n);
+    float2 f[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int i = cp.i0 + (c & 1), j = cp.j0 + (c >> 1);
+        f[c] = delta_at_pixel(corner_ratios<Acc>(J, i, j, C, inv_c), uniform_ratios(i, j, n, inv_c0), i, j, inv_n);
+    }
+    return bilinear(f, cp.a, cp.b);
 }
 
 template <class Acc>

@@ -78,6 +78,12 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     if (tid == 0) {
         for (int q = 0; q <= H; ++q) mbar_init(bars + q, 1);
         mbar_init_fence();
+        // Phase 3's label rows before the wait: the row kernel that wrote
+        // them has completed (phase 1 and the carries, launched after it,
+        // have passed their waits before this grid could start).
+        if (PHASE == 3 && from_labels)
+            for (int q = 0; q < H; ++q)
+                tma_load_1d(ring + q * N, J.labels + (size_t)(j0 + q) * N, 2u * N, bars + q);
     }
     __syncthreads();
     pdl_start(J.pdl_early != 0);
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(kPbThreads, (H <= 8 ? 3 : 1)) k_scan_band_pb(c
     // is read together with the loads of the region table (one round trip);
     // a stopped job's block leaves once its copies have landed.
     // stage: every label row of the band, one bulk copy each
-    if (from_labels && tid == 0)
+    if (PHASE == 1 && from_labels && tid == 0)
         for (int q = 0; q < H; ++q)
             tma_load_1d(ring + q * N, J.labels + (size_t)(j0 + q) * N, 2u * N, bars + q);
     if (PHASE == 3 && tid == 0) {
