@@ -78,7 +78,6 @@ def stage_bytes(n_jobs, N, V, R, E, K, nb):
 # The 3-solve batch's textures stay in L2, so its kernels move far fewer DRAM
 # bytes than their algorithmic bytes.
 TRAFFIC = {
-    ("chain3", "crossings", 8, 0, 256): 2.367e6,
     ("chain3", "raster_rows", 8, 0, 256): 0.876e6,
     ("chain3", "scan_phase1", 8, 0, 256): 6.363e6,
     ("chain3", "scan_carry", 8, 0, 256): 4.750e6,

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256, 5) k_crossings(const Job* __restrict__ jo
     }
     if (!act) return;
     tl_begin(J.tl, kTlCrossings);
-    emit_crossings_lane<kEdgesPerLane>(J, valid, reg, p, q);
+    emit_crossings_warp<kEdgesPerLane>(J, valid, reg, p, q);
     if (m.y == 0) reset_raster_block(J);
     tl_end(J.tl, kTlCrossings);
     pdl_release();

@@ -7,22 +7,33 @@
 
 namespace inim {
 
-struct EdgeFix {
-    long long X0, Y0, X1, Y1;
+// An edge in fixed point (I = long long for any input; I = int when every
+// coordinate is below 512 in magnitude: |X| < 2^29 for textures up to 4096^2,
+// so that the differences the rule needs stay exact in 32 bits).
+template <class I>
+struct EdgeFixT {
+    I X0, Y0, X1, Y1;
     int jlo, jhi;
 };
+using EdgeFix = EdgeFixT<long long>;
 
-__device__ __forceinline__ bool edge_rows_pts(const Job& J, float2 p, float2 q, EdgeFix& f) {
+__device__ __forceinline__ long long snap_t(float x, float scale, long long) { return snap_coord(x, scale); }
+__device__ __forceinline__ int snap_t(float x, float scale, int) { return __float2int_rn(x * scale); }
+__device__ __forceinline__ long long ceil_div256(long long a) { return ceil_div(a, 256); }
+__device__ __forceinline__ int ceil_div256(int a) { return (a + 255) >> 8; }   // |a| < 2^30: exact
+
+template <class I>
+__device__ __forceinline__ bool edge_rows_pts(const Job& J, float2 p, float2 q, EdgeFixT<I>& f) {
     const float scale = (float)(1 << (J.log2n + kSubBits));
-    long long X0 = snap_coord(p.x, scale), Y0 = snap_coord(p.y, scale);
-    long long X1 = snap_coord(q.x, scale), Y1 = snap_coord(q.y, scale);
+    I X0 = snap_t(p.x, scale, I{}), Y0 = snap_t(p.y, scale, I{});
+    I X1 = snap_t(q.x, scale, I{}), Y1 = snap_t(q.y, scale, I{});
     if (Y1 < Y0) {
-        long long t = X0; X0 = X1; X1 = t;
+        I t = X0; X0 = X1; X1 = t;
         t = Y0; Y0 = Y1; Y1 = t;
     }
     if (Y1 == Y0) return false;                       // horizontal: never counted
-    long long jlo = ceil_div(Y0 - 128, 256);
-    long long jhi = ceil_div(Y1 - 128, 256) - 1;
+    I jlo = ceil_div256(Y0 - 128);
+    I jhi = ceil_div256(Y1 - 128) - 1;
     if (jlo < 0) jlo = 0;
     if (jhi > J.n - 1) jhi = J.n - 1;
     if (jlo > jhi) return false;
@@ -67,17 +78,17 @@ __device__ __forceinline__ int clamped_ceil_div(long long num, long long den, in
 // crossings.
 constexpr int kCrossPipe = 4;
 
-template <int E>
+template <int E, class I>
 __device__ __forceinline__ void emit_crossings_lane(const Job& J, const bool (&valid)[E], const unsigned (&reg)[E],
                                                     const float2 (&p)[E], const float2 (&q)[E]) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    EdgeFix f[E];
+    EdgeFixT<I> f[E];
     int c[E];
     int cnt = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        f[e] = EdgeFix{};
+        f[e] = EdgeFixT<I>{};
         c[e] = (valid[e] && edge_rows_pts(J, p[e], q[e], f[e])) ? f[e].jhi - f[e].jlo + 1 : 0;
         cnt += c[e];
     }
@@ -89,13 +100,16 @@ __device__ __forceinline__ void emit_crossings_lane(const Job& J, const bool (&v
     }
     const int excl = incl - cnt;
     const int total = __shfl_sync(full, incl, 31);
-    for (int base = 0; base < total; base += 32 * kCrossPipe) {
-        // up to kCrossPipe rounds of 32 crossings, then their bucket atomics
+    // the 64-bit form (far-away end points only) pipelines two rounds: fewer
+    // registers beside the 32-bit form in one kernel
+    constexpr int PIPE = sizeof(I) == 4 ? kCrossPipe : 2;
+    for (int base = 0; base < total; base += 32 * PIPE) {
+        // up to PIPE rounds of 32 crossings, then their bucket atomics
         // together (one round trip for the batch), then the key stores
-        int jq[kCrossPipe];
-        unsigned kq[kCrossPipe];
+        int jq[PIPE];
+        unsigned kq[PIPE];
 #pragma unroll
-        for (int t = 0; t < kCrossPipe; ++t) {
+        for (int t = 0; t < PIPE; ++t) {
             jq[t] = -1;
             kq[t] = 0;
             if (base + 32 * t >= total) continue;             // warp-uniform
@@ -107,15 +121,15 @@ __device__ __forceinline__ void emit_crossings_lane(const Job& J, const bool (&v
                 if (__shfl_sync(full, excl, cand) <= i) owner = cand;
             }
             const int k = i - __shfl_sync(full, excl, owner);     // index among the owner's crossings
-            long long X0 = 0, Y0 = 0, X1 = 0, Y1 = 0;
+            I X0 = 0, Y0 = 0, X1 = 0, Y1 = 0;
             int j = 0;
             unsigned r = 0;
             int acc = 0;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int ce = __shfl_sync(full, c[e], owner);
-                const long long x0 = __shfl_sync(full, f[e].X0, owner), y0 = __shfl_sync(full, f[e].Y0, owner);
-                const long long x1 = __shfl_sync(full, f[e].X1, owner), y1 = __shfl_sync(full, f[e].Y1, owner);
+                const I x0 = __shfl_sync(full, f[e].X0, owner), y0 = __shfl_sync(full, f[e].Y0, owner);
+                const I x1 = __shfl_sync(full, f[e].X1, owner), y1 = __shfl_sync(full, f[e].Y1, owner);
                 const int jl = __shfl_sync(full, f[e].jlo, owner);
                 const unsigned re = __shfl_sync(full, reg[e], owner);
                 if (k >= acc && k < acc + ce) {
@@ -126,20 +140,36 @@ __device__ __forceinline__ void emit_crossings_lane(const Job& J, const bool (&v
                 acc += ce;
             }
             if (i < total) {
-                const long long dY = Y1 - Y0, dX = X1 - X0;
-                const long long Yc = 256LL * j + 128;
-                const int col = clamped_ceil_div(dX * (Yc - Y0) + (X0 - 128) * dY, 256 * dY, J.n);
+                const I dY = Y1 - Y0, dX = X1 - X0;
+                const I Yc = (I)256 * j + 128;
+                const long long num = (long long)dX * (long long)(Yc - Y0) + (long long)(X0 - 128) * (long long)dY;
+                const int col = clamped_ceil_div(num, 256LL * (long long)dY, J.n);
                 jq[t] = j;
                 kq[t] = (r << 16) | (unsigned)col;
             }
         }
-        int slot[kCrossPipe];
+        int slot[PIPE];
 #pragma unroll
-        for (int t = 0; t < kCrossPipe; ++t) slot[t] = jq[t] >= 0 ? atomicAdd(&J.row_cnt[jq[t]], 1) : kKeyStride;
+        for (int t = 0; t < PIPE; ++t) slot[t] = jq[t] >= 0 ? atomicAdd(&J.row_cnt[jq[t]], 1) : kKeyStride;
 #pragma unroll
-        for (int t = 0; t < kCrossPipe; ++t)
+        for (int t = 0; t < PIPE; ++t)
             if (slot[t] < kKeyStride) J.keys[(size_t)jq[t] * kKeyStride + slot[t]] = kq[t];
     }
+}
+
+// emit_crossings_lane in 32-bit fixed point when every end point of the
+// warp's edges lies within 512 of the origin (the same keys), else in 64 bits.
+template <int E>
+__device__ __forceinline__ void emit_crossings_warp(const Job& J, const bool (&valid)[E], const unsigned (&reg)[E],
+                                                    const float2 (&p)[E], const float2 (&q)[E]) {
+    bool wide = false;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (valid[e])
+            wide |= !(fabsf(p[e].x) < 512.0f && fabsf(p[e].y) < 512.0f && fabsf(q[e].x) < 512.0f &&
+                      fabsf(q[e].y) < 512.0f);
+    if (__any_sync(0xffffffffu, wide)) emit_crossings_lane<E, long long>(J, valid, reg, p, q);
+    else emit_crossings_lane<E, int>(J, valid, reg, p, q);
 }
 
 // One item of kEdgesPerItem edges of a job (a block of 256 threads; lane
@@ -162,7 +192,7 @@ __device__ __forceinline__ void emit_crossings_item(const Job& J, int item) {
             q[s] = J.xy[ab.y];
         }
     }
-    emit_crossings_lane<kEdgesPerLane>(J, valid, reg, p, q);
+    emit_crossings_warp<kEdgesPerLane>(J, valid, reg, p, q);
 }
 
 // Per job, while the keys of an iteration are being emitted (one block):

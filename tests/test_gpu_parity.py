@@ -99,6 +99,30 @@ def test_raster_bit_exact(name, mesh, k):
     assert bool(ov) == oov
 
 
+def test_raster_bit_exact_far_vertices():
+    """End points far outside the unit square (a map's own vertices lie in
+    [-1, 2], but inim_raster takes any positions): the warps holding such
+    edges form the crossing keys in 64-bit fixed point, the others in 32-bit,
+    with the same keys."""
+    base = synth.voronoi_map(40, 2000, seed=5)
+    nb = base.verts.shape[0]
+    tri = [(0.2, 0.2), (0.9, 0.5), (0.2, 0.8), (0.5, 0.9), (0.1, 0.61), (0.5, 0.3)]
+    mesh = synth.Mesh(np.concatenate([base.verts, np.array(tri, np.float64)]),
+                      np.concatenate([base.ring_off, base.ring_off[-1] + np.array([3, 6])]).astype(np.int32),
+                      np.concatenate([base.ring_idx, nb + np.arange(6)]).astype(np.int32),
+                      np.concatenate([base.ring_region, [0, 1]]).astype(np.int32), base.n_regions)
+    m = P.inim_map_create(mesh)
+    xy = mesh.verts_f32()
+    xy[nb + 1] = (700.25, 0.5)          # beyond the 32-bit form's range (512)
+    xy[nb + 4] = (-600.5, 0.61)
+    for k in (9, 12):
+        lab, cnt, ov = gpu_raster(m, xy, k)
+        olab, ocnt, oov = oracle_raster(mesh, xy, k)
+        np.testing.assert_array_equal(lab, olab)
+        np.testing.assert_array_equal(cnt[:-1], ocnt)
+        assert bool(ov) == oov
+
+
 def test_raster_bit_exact_4096():
     w = synth.precision_workload()
     mesh = w["mesh"]
