@@ -69,7 +69,9 @@ def test_roofline_entry_arithmetic():
     r = bench.roofline(batches, "chain3", "scan_phase3", pk)
     assert r["achieved"] == pytest.approx(algo["scan_phase3"] / 0.02e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == bench.TRAFFIC[("chain3", "scan_phase3", 8, 0, 256)]
+    # scan phase 3 of this tile changed after its capture (label copies issued
+    # before the launch wait): no traffic until it is captured again
+    assert r["traffic"] is None
     assert bench.roofline(batches, "chain3", "scan_phase1", pk)["traffic"] == \
         bench.TRAFFIC[("chain3", "scan_phase1", 8, 0, 256)]
     # no capture of this tile: no traffic
