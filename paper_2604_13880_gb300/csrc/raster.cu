@@ -13,8 +13,10 @@
 // Kernels (edge-parallel, then row-parallel; no per-pixel global atomics):
 //   k_crossings    two edges per lane: (region << 16 | c) appended to the
 //                  fixed-stride bucket of every row the edge crosses (no
-//                  histogram or prefix pass: each bucket holds up to 2048 keys)
-//   k_raster_rows  warp per row: sort the row's keys in registers, pair them
+//                  histogram or prefix pass: each bucket holds up to 2048 keys;
+//                  the rule in 32-bit integers where the end points allow)
+//   k_raster_rows  warp per row (a block's 8 rows spread over the texture):
+//                  sort the row's keys in registers, pair them
 //                  into spans, enter the spans into a shared-memory difference
 //                  array and build every label by one striped prefix pass
 //                  (pixels inside two spans resolved to the smallest region);
