@@ -75,7 +75,7 @@ __device__ __forceinline__ int clamped_ceil_div(long long num, long long den, in
 // total / 32 crossings instead of the longest edge's row count; the bucket
 // atomics of kCrossPipe rounds go out together, so a warp whose stretched
 // edges cross many rows waits for one atomic round trip per 32 * kCrossPipe
-// crossings.
+// crossings.  I is the fixed-point type of the end points (EdgeFixT).
 constexpr int kCrossPipe = 4;
 
 template <int E, class I>
