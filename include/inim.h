@@ -541,9 +541,10 @@ int inim_autotune_scan(const inim_job* jobs, int32_t n_jobs, int32_t reps);
  * stores) and the rows get the pairs' time minus that; the buckets are
  * emptied afterwards.  For batches whose maps have at most 2047 regions the
  * density table is built by scan_phase1 (there is no density_table kernel in
- * the iteration) and ms[2] = 0.  Large batches (at least 2^23 pixels per
- * resolution) scan in one pass: scan_fused holds that kernel and the three
- * scan phases read 0 (and the other way round for small batches).  The
+ * the iteration) and ms[2] = 0.  With inim_set_single_pass_scan(1), large
+ * batches (at least 2^23 pixels per resolution) scan in one pass: scan_fused
+ * holds that kernel and the three scan phases read 0 (otherwise scan_fused
+ * reads 0).  The
  * batch's vertices move while it runs; the next run resets them.  ms must
  * hold >= 9 floats; *n_stages receives 9.  INIM_E_STATE if no map batch ran
  * yet.

@@ -2012,6 +2012,10 @@ int inim_profile_stages(int32_t reps, float* ms, int32_t max_stages, int32_t* n_
                 }
                 return e;
             }
+            // back-to-back moves: each reads its vertices before its launch
+            // wait, so it may see the previous replay's moves half done (the
+            // values only feed this timing run; every run restarts from its
+            // start positions)
             case 6: return launch_gather(B.d_jobs, B.vert_blocks, B.precision, B.stream);
             default: return launch_areas_errors(B.d_jobs, B.region_blocks, 0, B.stream);
         }
